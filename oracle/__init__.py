@@ -1,0 +1,171 @@
+"""Plain FP64 CPU oracle of the online DMN evaluation (arXiv 2109.14403, Sec. 3.3,
+Algorithm 1) plus an FP64 reference of the warm-start MLP.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the library under
+``paper_2109_14403_gb300`` never does.  The C source (``dmn_oracle.c``) is
+compiled with gcc on first use (or by ``build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dmn_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+OUT_WORDS = 57
+PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_build/liboracle.so``."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+                               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i, i64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
+            p = ctypes.c_void_p
+            lib.oracle_state_words.restype = i64
+            lib.oracle_state_words.argtypes = [i, p, p, p, p, i]
+            lib.oracle_eval_batch.restype = i
+            lib.oracle_eval_batch.argtypes = [i, p, p, p, p, i, d, i, i, d, d, i, i64, p, p, d,
+                                              p, p, p, p, p, i]
+            lib.oracle_eval_point_trace.restype = i
+            lib.oracle_eval_point_trace.argtypes = [i, p, p, p, p, i, d, i, i, d, d, i, p, d, d,
+                                                    p, p, p, p, p, p, i]
+            lib.oracle_leaf.restype = None
+            lib.oracle_leaf.argtypes = [p, p, d, p, d, d, p]
+            lib.oracle_leaf_strains.restype = i
+            lib.oracle_leaf_strains.argtypes = [i, p, p, p, p, p]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Tree:
+    """DMN description: depth K, leaf weights (2^K), normals ((2^K-1) x 3 in the
+    paper's order: bottom level first, root last), phase map (2^K) and a material
+    table (n_mats x 8: kind, E, nu, alpha, theta0, sy0, dsy_dT, H)."""
+
+    def __init__(self, K, w, normals, phase, mats):
+        self.K = int(K)
+        self.w = _c(w, np.float64)
+        self.normals = _c(normals, np.float64).reshape(-1, 3)
+        self.phase = _c(phase, np.uint8)
+        self.mats = _c(mats, np.float64).reshape(-1, 8)
+        n = _load().oracle_state_words(self.K, _ptr(self.w), _ptr(self.normals), _ptr(self.phase),
+                                       _ptr(self.mats), self.mats.shape[0])
+        if n < 0:
+            raise ValueError(f"oracle rejected the tree (code {n})")
+        self.state_words = int(n)
+        self.nnode = (1 << self.K) - 1
+
+    def init_state(self, n_points, theta0):
+        s = np.zeros((n_points, self.state_words), np.float64)
+        s[:, 6] = theta0
+        return s
+
+
+def eval_batch(tree: Tree, deps, theta, dt, state_in, *, tol=1e-12, maxit=50, maxbacktrack=8,
+               gamma=0.5, res_floor=None, dense=False, threads=None):
+    """Algorithm 1 at every point.  Returns (state_out, out[n,57], status, iters)."""
+    deps = _c(deps, np.float64).reshape(-1, 6)
+    n = deps.shape[0]
+    theta = _c(np.broadcast_to(np.asarray(theta, np.float64), (n,)), np.float64)
+    sin = _c(state_in, np.float64).reshape(n, tree.state_words)
+    sout = np.zeros_like(sin)
+    out = np.zeros((n, OUT_WORDS), np.float64)
+    status = np.zeros(n, np.int32)
+    iters = np.zeros(n, np.int32)
+    if res_floor is None:
+        res_floor = 1e-8 * float(tree.mats[:, 1].max())
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = _load().oracle_eval_batch(tree.K, _ptr(tree.w), _ptr(tree.normals), _ptr(tree.phase),
+                                   _ptr(tree.mats), tree.mats.shape[0], tol, maxit, maxbacktrack,
+                                   gamma, res_floor, int(bool(dense)), n, _ptr(deps), _ptr(theta),
+                                   float(dt), _ptr(sin), _ptr(sout), _ptr(out), _ptr(status),
+                                   _ptr(iters), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_eval_batch failed (code {rc})")
+    return sout, out, status, iters
+
+
+def eval_point_trace(tree: Tree, deps, theta, dt, state_in, *, tol=1e-12, maxit=50,
+                     maxbacktrack=8, gamma=0.5, res_floor=None, dense=False):
+    """One point; also returns the residual history of Algorithm 1."""
+    deps = _c(deps, np.float64).reshape(6)
+    sin = _c(state_in, np.float64).reshape(tree.state_words)
+    sout = np.zeros_like(sin)
+    out = np.zeros(OUT_WORDS, np.float64)
+    st = np.zeros(1, np.int32)
+    it = np.zeros(1, np.int32)
+    hist = np.full(maxit + 1, np.nan)
+    if res_floor is None:
+        res_floor = 1e-8 * float(tree.mats[:, 1].max())
+    rc = _load().oracle_eval_point_trace(tree.K, _ptr(tree.w), _ptr(tree.normals),
+                                         _ptr(tree.phase), _ptr(tree.mats), tree.mats.shape[0],
+                                         tol, maxit, maxbacktrack, gamma, res_floor,
+                                         int(bool(dense)), _ptr(deps), float(theta), float(dt),
+                                         _ptr(sin), _ptr(sout), _ptr(out), _ptr(st), _ptr(it),
+                                         _ptr(hist), maxit + 1)
+    if rc != 0:
+        raise ValueError(f"oracle_eval_point_trace failed (code {rc})")
+    return sout, out, int(st[0]), int(it[0]), hist[~np.isnan(hist)]
+
+
+def leaf(mat_row, eps, theta, zn=None, trn=0.0, dt=1.0):
+    """One phase-law evaluation.  Returns a dict with sig, C, tau, D, d, g, diss, znew."""
+    m = _c(mat_row, np.float64).reshape(8)
+    e = _c(eps, np.float64).reshape(6)
+    z = _c(np.zeros(7) if zn is None else zn, np.float64).reshape(7)
+    o = np.zeros(64, np.float64)
+    _load().oracle_leaf(_ptr(m), _ptr(e), float(theta), _ptr(z), float(trn), float(dt), _ptr(o))
+    return {"sig": o[0:6].copy(), "C": o[6:42].reshape(6, 6).copy(), "tau": o[42:48].copy(),
+            "D": float(o[48]), "d": o[49:55].copy(), "g": float(o[55]), "diss": float(o[56]),
+            "znew": o[57:64].copy()}
+
+
+def leaf_strains(tree: Tree, eps_bar, a):
+    """eps_j = eps_bar + A a for every leaf j (explicit kinematic operator)."""
+    eb = _c(eps_bar, np.float64).reshape(6)
+    av = _c(a, np.float64).reshape(3 * tree.nnode)
+    out = np.zeros((1 << tree.K, 6), np.float64)
+    rc = _load().oracle_leaf_strains(tree.K, _ptr(tree.w), _ptr(tree.normals), _ptr(eb),
+                                     _ptr(av), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_leaf_strains failed")
+    return out
+
+
+def split_out(out):
+    """Named views of the 57 output words."""
+    out = np.asarray(out)
+    return {"sig": out[..., 0:6], "C": out[..., 6:42].reshape(out.shape[:-1] + (6, 6)),
+            "C_theta": out[..., 42:48], "D": out[..., 48], "D_eps": out[..., 49:55],
+            "D_theta": out[..., 55], "diss": out[..., 56]}

@@ -1,0 +1,72 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds no arithmetic of the method: it only draws random trees and
+load paths and lists material parameters.  Both the CUDA path and the CPU oracle
+consume what it returns.
+
+Workloads (the paper's own trained DMN and FFT data are not available, so these
+stand in for its strain-controlled virtual experiments, Sec. 5.4):
+  * tree: leaf weights ~ Dirichlet(1) over 2^K leaves, lamination directions
+    uniform on the unit sphere, phases alternating (odd leaves phase 1 = fiber,
+    even leaves phase 2 = matrix, as in Sec. 3.3), seed 1234 + K;
+  * fiber: isotropic linear thermoelastic E = 72 GPa, nu = 0.22, alpha = 5e-6/K;
+  * matrix: J2 elastoplastic, linear isotropic hardening 300 MPa,
+    E = 2.5 GPa, nu = 0.38, alpha = 8e-5/K, yield 50 MPa at 293 K falling
+    0.3 MPa/K;
+  * K=4 ramp: 64 points, 20 increments of 0.1 % in the 11 component plus
+    N(0, 1e-4) on all six Mandel components, temperature 293 -> 353 K;
+  * K=8 random walk: 65,536 points, 50 increments with N(0, 2e-4) on every
+    Mandel component and temperature steps U(0, 1) K from 293 K.
+Units: MPa, K, s.  Symmetric tensors are Mandel 6-vectors.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# material table rows: kind, E, nu, alpha, theta0, sy0, dsy_dT, H
+KIND_THERMOELASTIC = 0
+KIND_J2_LINEAR = 1
+FIBER = (KIND_THERMOELASTIC, 72000.0, 0.22, 5e-6, 293.0, 0.0, 0.0, 0.0)
+MATRIX = (KIND_J2_LINEAR, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0)
+THETA_START = 293.0
+
+
+def materials():
+    return np.array([FIBER, MATRIX], dtype=np.float64)
+
+
+def tree(K: int, seed: int | None = None):
+    """Random DMN parameters: (w, normals in paper order, phase map)."""
+    rng = np.random.default_rng(1234 + K if seed is None else seed)
+    g = rng.gamma(1.0, 1.0, size=1 << K)
+    w = g / g.sum()
+    v = rng.standard_normal(((1 << K) - 1, 3))
+    normals = v / np.linalg.norm(v, axis=1, keepdims=True)
+    phase = (np.arange(1 << K) % 2).astype(np.uint8)  # leaf 1 (odd) -> fiber
+    return w, normals, phase
+
+
+def ramp_k4(n_points=64, n_incr=20, seed=42):
+    """Uniaxial 2 % ramp with noise; returns (deps[n_incr, n, 6], theta[n_incr, n])."""
+    rng = np.random.default_rng(seed)
+    deps = rng.normal(0.0, 1e-4, size=(n_incr, n_points, 6))
+    deps[:, :, 0] += 1e-3
+    theta = THETA_START + 3.0 * np.arange(1, n_incr + 1)[:, None] * np.ones((1, n_points))
+    return deps, theta
+
+
+def random_walk_k8(n_points=65536, n_incr=50, seed=42):
+    """Random-walk strain path; returns (deps[n_incr, n, 6], theta[n_incr, n])."""
+    rng = np.random.default_rng(seed)
+    deps = rng.normal(0.0, 2e-4, size=(n_incr, n_points, 6))
+    dth = rng.uniform(0.0, 1.0, size=(n_incr, n_points))
+    theta = THETA_START + np.cumsum(dth, axis=0)
+    return deps, theta
+
+
+def single_increment(n_points, seed=7, scale=2e-4, theta=300.0):
+    """One increment of N(0, scale) strain on every component at a fixed temperature."""
+    rng = np.random.default_rng(seed)
+    deps = rng.normal(0.0, scale, size=(n_points, 6))
+    th = np.full(n_points, theta)
+    return deps, th
