@@ -1,0 +1,321 @@
+"""Benchmark: Gauss-point DMN evaluations per second at K=8.
+
+Workload (one step = one load increment of the whole hot path, Algorithm 1 at
+every point): a depth-8 DMN (256 leaves, 765 jump unknowns; fiber/matrix
+alternating; w ~ Dirichlet(1), normals uniform on the sphere, seed 1242),
+65,536 Gauss points per GPU, consecutive increments of the random-walk load
+(N(0, 2e-4) on every Mandel strain component, temperature steps U(0, 1) K from
+293 K).  Device-resident state (~0.9 GB per batch, larger than L2), so no L2
+flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                       [--impl ours|reference]
+--impl reference times the FP64 CPU oracle on the host cores (a bounded
+sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+K_DEPTH = 8
+N_POINTS = 65536
+METRIC = "Gauss-pt DMN evals/s (K=8, to 1e-8 rel) FP64 vs mixed+warm-start; %HBM roof"
+UNIT = "GP-evals/s"
+TOL = 1e-10
+
+
+def state_words(K, n_j2):
+    w = 8 + 3 * ((1 << K) - 1) + 7 * n_j2
+    return w + (w & 1)
+
+
+def algorithmic_bytes_per_eval(K):
+    """State in + state out + inputs (deps 6, theta 1) + outputs (57) + status + iters."""
+    sw = state_words(K, (1 << K) // 2)
+    return 8 * (2 * sw + 7 + 57) + 8
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(n_points=1024, n_incr=2, threads=None):
+    """FP64 oracle on the host cores: the first n_incr increments of the same
+    K=8 random walk on n_points points (its own trajectory)."""
+    import oracle
+    from paper_2109_14403_gb300 import synthetic as syn
+    threads = threads or os.cpu_count() or 1
+    w, nrm, ph = syn.tree(K_DEPTH)
+    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials())
+    deps, theta = syn.random_walk_k8(n_points=n_points, n_incr=n_incr)
+    s = tree.init_state(n_points, syn.THETA_START)
+    t0 = time.perf_counter()
+    for k in range(n_incr):
+        s, out, st, it = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n_points * n_incr / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 random walk, tol {TOL}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2109_14403_gb300 import synthetic as syn
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = 512
+    w, nrm, ph = syn.tree(K_DEPTH)
+    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials())
+    deps, theta = syn.random_walk_k8(n_points=n, n_incr=args.warmup + args.steps)
+    s = tree.init_state(n, syn.THETA_START)
+    for k in range(args.warmup):
+        s, *_ = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        s, *_ = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
+    el = time.perf_counter() - t0
+    v = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"K={K_DEPTH} DMN random walk, {n} of {N_POINTS} points per step (oracle sample)",
+                       "precision": "fp64", "tol": TOL},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} points per increment, {args.steps} increments after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-variant", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    from paper_2109_14403_gb300 import DMN, synthetic as syn
+    n = args.points
+    w, nrm, ph = syn.tree(K_DEPTH)
+    mats = syn.materials()
+    steps, warm = args.steps, args.warmup
+    n_incr = warm + 2 * steps
+    deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=n_incr, seed=42 + rank)
+    deps_d = torch.tensor(deps_h, device=dev)
+    theta_d = torch.tensor(theta_h, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def device_run(prec):
+        d = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision=prec)
+        s_a = d.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+        s_b = torch.empty_like(s_a)
+        out = torch.empty((n, 57), dtype=torch.float64, device=dev)
+        st = torch.empty(n, dtype=torch.int32, device=dev)
+        it = torch.empty(n, dtype=torch.int32, device=dev)
+        for k in range(warm):
+            d.eval(deps_d[k], theta_d[k], 1.0, s_a, s_b, out, st, it)
+            s_a, s_b = s_b, s_a
+        barrier()
+        stream = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        iters = []
+        with ClockSampler(local) as clk:
+            ev[0].record(stream)
+            for k in range(steps):
+                d.eval(deps_d[warm + k], theta_d[warm + k], 1.0, s_a, s_b, out, st, it)
+                ev[k + 1].record(stream)
+                s_a, s_b = s_b, s_a
+                iters.append(it)
+                it = torch.empty_like(it)
+            barrier()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        total_ms = ev[0].elapsed_time(ev[steps])
+        nonconv = int((st != 0).sum().item())
+        hist = torch.bincount(torch.cat(iters).cpu().long()).tolist()
+        return d, s_a, s_b, total_ms, per, clk.summary(), hist, nonconv
+
+    d, s_a, s_b, total_ms, per, clocks, hist, nonconv = device_run(args.precision)
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * steps / (t_max / 1e3)
+
+    # end to end through the public API: pinned host inputs in, results out
+    deps_p = torch.tensor(deps_h[warm + steps:warm + 2 * steps]).pin_memory()
+    theta_p = torch.tensor(theta_h[warm + steps:warm + 2 * steps]).pin_memory()
+    out_p = torch.empty((n, 57), dtype=torch.float64).pin_memory()
+    st_p = torch.empty(n, dtype=torch.int32).pin_memory()
+    it_p = torch.empty(n, dtype=torch.int32).pin_memory()
+    dd = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    th = torch.empty(n, dtype=torch.float64, device=dev)
+    out = torch.empty((n, 57), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    it = torch.empty(n, dtype=torch.int32, device=dev)
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        dd.copy_(deps_p[k], non_blocking=True)
+        th.copy_(theta_p[k], non_blocking=True)
+        d.eval(dd, th, 1.0, s_a, s_b, out, st, it)
+        out_p.copy_(out, non_blocking=True)
+        st_p.copy_(st, non_blocking=True)
+        it_p.copy_(it, non_blocking=True)
+        s_a, s_b = s_b, s_a
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": world * n * steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": n * 7 * 8, "d2h_bytes_per_step": n * (57 * 8 + 8)}
+    d.close()
+    del s_a, s_b
+
+    fp64_variant = None
+    if not args.no_fp64_variant and args.precision != "fp64":
+        d2, a2, b2, ms2, per2, clk2, hist2, nc2 = device_run("fp64")
+        fp64_variant = {"value": n * steps / (ms2 / 1e3), "ms_per_step": ms2 / steps,
+                        "iter_hist": hist2, "not_converged": nc2}
+        d2.close()
+        del a2, b2
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    bpe = algorithmic_bytes_per_eval(K_DEPTH)
+    kern_ms = statistics.mean(per)
+    achieved = bpe * n / (kern_ms / 1e3) / 1e9
+    peak, how = measured_peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": how,
+            "kernel": "dmn_solve_kernel", "bytes_per_eval": bpe}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": t_max / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"K={K_DEPTH} DMN, {n} Gauss points per GPU, random-walk increments",
+                       "precision": args.precision, "tol": TOL, "points_per_gpu": n,
+                       "l2": "inputs larger than L2 (device state ~0.9 GB)",
+                       "parallelism": f"replicas x{world} (independent points)"},
+            "iter_hist": hist, "not_converged": nonconv,
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": steps}
+    if fp64_variant:
+        line["fp64_path"] = fp64_variant
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * dmn.h -- C ABI of the GB300 (sm_103a) library for the online evaluation of a
+ * thermomechanical direct deep material network (DMN) at a batch of
+ * macroscopic Gauss points.
+ *
+ * Method: Gajek, Schneider, Boehlke, "An FE-DMN method for the multiscale
+ * analysis of thermomechanical composites", arXiv 2109.14403.
+ *   - tree, weights, volume fractions, normals ............ Sec. 3.1
+ *   - kinematics eps = eps_bar + A a, balance A^T W sigma = 0, Newton
+ *     system, effective stress / coupling term / dissipation, the four
+ *     algorithmic tangents ................................ Sec. 3.3
+ *   - the driver (warm start, Residual, Newton, Backtracking) Algorithm 1
+ *   - phase laws (linear thermoelastic; J2 flow) ........... Sec. 4
+ *
+ * Conventions
+ *   - Units MPa, K, s.
+ *   - Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13,
+ *     sqrt2*12); a fourth-order tangent is a 6x6 row-major matrix
+ *     T[i][j] = d out_i / d in_j in that basis.
+ *   - Tree nodes are numbered as the paper orders its lamination directions:
+ *     bottom level first, left to right, root last (Sec. 3.1).  Leaf j
+ *     (0-based) lies under child 1 of its parent laminate when j is even.
+ *   - Kinematic operator A (the paper defers its form to Gajek et al. 2020):
+ *     every leaf under child 1 of node p receives +c_{p,2} sym(a_p (x) n_p),
+ *     every leaf under child 2 receives -c_{p,1} sym(a_p (x) n_p).  The
+ *     converged stress and tangents do not depend on this choice; the scale
+ *     of the Algorithm 1 residual does.
+ *
+ * Ownership: every d_* pointer is device memory owned by the caller.  A
+ * handle owns only device copies of the tree and material constants.
+ * Streams: every call that takes a stream is stream-ordered and does not
+ * synchronise the device.  Errors: a non-zero dmn_status; the message of the
+ * last error of the calling thread is returned by dmn_last_error().
+ * Argument errors are detected before any launch.  Numerical failures are
+ * reported per point in the status array, never as a call error.
+ */
+#ifndef DMN_H_
+#define DMN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmn_handle_s *dmn_handle;
+typedef void *dmn_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  DMN_OK = 0,
+  DMN_ERR_ARG = 1,      /* invalid argument (checked before any launch)  */
+  DMN_ERR_CUDA = 2,     /* a CUDA runtime call failed                    */
+  DMN_ERR_OOM = 3,      /* device allocation failed                      */
+  DMN_ERR_STATE = 4,    /* state buffer too small / wrong tree           */
+  DMN_ERR_INTERNAL = 5
+} dmn_status;
+
+/* per-point status codes written by dmn_eval */
+enum {
+  DMN_PT_OK = 0,            /* residual < tol                              */
+  DMN_PT_NOT_CONVERGED = 1, /* maxit Newton iterations without res < tol   */
+  DMN_PT_NONFINITE = 2      /* a residual or an output was NaN or Inf      */
+};
+
+/* phase laws (Sec. 4) */
+enum {
+  DMN_MAT_THERMOELASTIC = 0, /* sigma = C[eps - alpha (theta - theta0) I] */
+  DMN_MAT_J2_LINEAR = 1      /* J2 plasticity, linear isotropic hardening  */
+};
+
+typedef struct {
+  int32_t kind;   /* DMN_MAT_*                                              */
+  int32_t pad_;
+  double E;       /* Young's modulus (MPa), > 0                             */
+  double nu;      /* Poisson's ratio, (-1, 0.5)                             */
+  double alpha;   /* isotropic thermal expansion coefficient (1/K)          */
+  double theta0;  /* reference temperature (K), > 0                         */
+  double sy0;     /* J2: yield stress at theta0 (MPa), > 0                  */
+  double dsy_dT;  /* J2: yield-stress slope (MPa/K); sigma_Y is floored at
+                     1e-6 MPa                                               */
+  double H;       /* J2: linear isotropic hardening modulus (MPa), >= 0     */
+} dmn_material;
+
+enum { DMN_PREC_FP64 = 0, DMN_PREC_MIXED = 1 };
+
+typedef struct {
+  double tol;           /* relative residual tolerance of Algorithm 1 (1e-10) */
+  double gamma;         /* backtracking factor, step gamma^{i+1} (0.5)        */
+  double res_floor;     /* floor of |sigma_bar|_F in the residual's
+                           denominator (MPa); <= 0 selects 1e-8 * max E       */
+  int32_t maxit;        /* Newton iterations (50), >= 1                       */
+  int32_t maxbacktrack; /* backtracking steps per iteration (8), >= 0         */
+  int32_t precision;    /* DMN_PREC_FP64: every step in FP64.  DMN_PREC_MIXED:
+                           leaf tangents, condensation and the Newton
+                           correction in FP32; strains, leaf stresses, the
+                           residual, the convergence test and every output
+                           accumulation in FP64                                */
+  int32_t reserved_;
+} dmn_options;
+
+/* Fill *opt with the defaults listed above. */
+void dmn_default_options(dmn_options *opt);
+
+/*
+ * Create a DMN handle (Sec. 3.1 tree; Sec. 4 phase laws).
+ *   K          tree depth, 1..10 (2^K leaves, 2^K - 1 laminates).
+ *   leaf_w     host, 2^K weights w_{K+1}^i, each > 0, summing to 1 within
+ *              1e-12 (Sec. 3.1 constraint; zero weights are rejected).
+ *   normals    host, (2^K - 1) x 3 lamination directions in the paper's
+ *              order; normalised on create, zero vectors rejected.
+ *   phase_map  host, 2^K indices into mats (the paper alternates two phases;
+ *              any map is accepted).
+ *   mats       host, n_mats materials, 1 <= n_mats <= 16.
+ *   opt        host options; NULL selects the defaults.
+ * Copies everything to device memory of the current device.
+ */
+dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_w, const double *normals,
+                      const uint8_t *phase_map, const dmn_material *mats, int32_t n_mats,
+                      const dmn_options *opt);
+
+dmn_status dmn_destroy(dmn_handle h);
+
+/*
+ * Device state of one Gauss point: state_words() doubles, 16-byte aligned.
+ *   [0..5]   eps_bar^n  (macro strain, Mandel)
+ *   [6]      theta^n    (K)
+ *   [7]      reserved (0)
+ *   [8 .. 8+3(2^K-1))  jump vectors a^n, node order as above, (x, y, z) each
+ *   then, for every leaf j in order whose material is DMN_MAT_J2_LINEAR:
+ *            plastic strain (6, Mandel) and accumulated plastic strain p (1)
+ *   padded to an even number of words.
+ * A batch is n_points such blocks back to back.
+ */
+int64_t dmn_state_words(dmn_handle h);
+
+/* Initial state: eps_bar = 0, a = 0, internal variables 0, theta^n =
+   d_theta0[i] (device, n_points doubles). */
+dmn_status dmn_state_init(dmn_handle h, double *d_state, int64_t n_points, const double *d_theta0,
+                          dmn_stream stream);
+
+/*
+ * One load increment at every point (Algorithm 1).
+ *   d_deps     n x 6 macro strain increments (eps_bar^{n+1} = eps_bar^n + deps)
+ *   d_theta    n absolute temperatures theta^{n+1} (K), > 0
+ *   dt         time increment (s), > 0: rates in D and Diss are (x^{n+1}-x^n)/dt
+ *   d_state_in   n x state_words: z^n, a^n, eps_bar^n, theta^n (read only)
+ *   d_state_out  n x state_words: written with the converged state; may not
+ *                alias d_state_in (a macro solver re-calls with the same
+ *                state_in until its global iteration converges)
+ *   d_out      n x 57 doubles, per point:
+ *                [0..5]   sigma_bar                     (eq. effective stress)
+ *                [6..41]  C_algo = d sigma_bar/d eps_bar (eq. ddsdde), 6x6
+ *                [42..47] d sigma_bar / d theta          (eq. ddsddt)
+ *                [48]     coupling term D_bar            (eq. effective coupling)
+ *                [49..54] d D_bar / d eps_bar            (eq. drplde)
+ *                [55]     d D_bar / d theta              (eq. drpldt)
+ *                [56]     dissipation                    (eq. effective dissipation)
+ *   d_status   n int32 per-point codes (DMN_PT_*)
+ *   d_iters    n int32 Newton iterations taken
+ * The phase coupling term of a J2 leaf is
+ *   D = [-3 K alpha theta tr(eps - eps^n) + sigma_Y(theta) dp] / dt
+ * and its dissipation sigma_Y(theta) dp / dt (discrete form of Sec. 4).
+ */
+dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points, const double *d_deps,
+                    const double *d_theta, double dt, const double *d_state_in,
+                    double *d_state_out, double *d_out, int32_t *d_status, int32_t *d_iters);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dmn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMN_H_ */

@@ -1,0 +1,290 @@
+// dmn_api.cu -- the C ABI declared in include/dmn.h: handle creation (tree
+// setup of arXiv 2109.14403 Sec. 3.1), state initialisation and the batched
+// evaluation launch (Sec. 3.3, Algorithm 1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/dmn.h"
+#include "dmn_internal.h"
+
+using namespace dmn;
+
+struct dmn_handle_s {
+  int K, N, nleaf, SW, zend, n_mats;
+  dmn_options opt;
+  int device, num_sms;
+  int blocks_per_sm[2];  // FP64, mixed
+  double *d_node;        // [N][6]
+  uint8_t *d_phase;      // [nleaf]
+  int *d_zoff;           // [nleaf]
+  double *d_mat;         // [n_mats][8]
+};
+
+static thread_local char g_err[512] = "";
+
+static dmn_status fail(dmn_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+static dmn_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? DMN_ERR_OOM : DMN_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+extern "C" const char *dmn_last_error(void) { return g_err; }
+
+extern "C" void dmn_default_options(dmn_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->gamma = 0.5;
+  o->res_floor = 0.0;
+  o->maxit = 50;
+  o->maxbacktrack = 8;
+  o->precision = DMN_PREC_FP64;
+}
+
+static void free_handle(dmn_handle h) {
+  if (!h) return;
+  cudaFree(h->d_node);
+  cudaFree(h->d_phase);
+  cudaFree(h->d_zoff);
+  cudaFree(h->d_mat);
+  delete h;
+}
+
+extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_w,
+                                 const double *normals, const uint8_t *phase_map,
+                                 const dmn_material *mats, int32_t n_mats, const dmn_options *opt) {
+  g_err[0] = 0;
+  if (!out) return fail(DMN_ERR_ARG, "dmn_create: out is NULL");
+  *out = nullptr;
+  if (K < 1 || K > 10) return fail(DMN_ERR_ARG, "dmn_create: K=%d outside 1..10", K);
+  if (!leaf_w || !normals || !phase_map || !mats)
+    return fail(DMN_ERR_ARG, "dmn_create: NULL array argument");
+  if (n_mats < 1 || n_mats > kMaxMats)
+    return fail(DMN_ERR_ARG, "dmn_create: n_mats=%d outside 1..%d", n_mats, kMaxMats);
+  dmn_options o;
+  if (opt) o = *opt; else dmn_default_options(&o);
+  if (!(o.tol > 0.0) || !(o.gamma > 0.0 && o.gamma < 1.0) || o.maxit < 1 || o.maxbacktrack < 0 ||
+      (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED))
+    return fail(DMN_ERR_ARG, "dmn_create: invalid options");
+  const int nleaf = 1 << K, N = nleaf - 1;
+
+  // materials: derived bulk and shear moduli (Sec. 4: K = E/(3(1-2nu)), G = E/(2(1+nu)))
+  std::vector<double> mat(8 * n_mats);
+  double Emax = 0.0;
+  for (int i = 0; i < n_mats; ++i) {
+    const dmn_material &m = mats[i];
+    if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR)
+      return fail(DMN_ERR_ARG, "dmn_create: material %d has unknown kind %d", i, m.kind);
+    if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
+      return fail(DMN_ERR_ARG, "dmn_create: material %d has invalid elastic constants", i);
+    if (m.kind == DMN_MAT_J2_LINEAR &&
+        (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
+      return fail(DMN_ERR_ARG, "dmn_create: material %d has invalid J2 constants", i);
+    double *r = &mat[8 * i];
+    r[0] = m.kind;
+    r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+    r[2] = m.E / (2.0 * (1.0 + m.nu));
+    r[3] = m.alpha;
+    r[4] = m.theta0;
+    r[5] = m.kind == DMN_MAT_J2_LINEAR ? m.sy0 : 0.0;
+    r[6] = m.kind == DMN_MAT_J2_LINEAR ? m.dsy_dT : 0.0;
+    r[7] = m.kind == DMN_MAT_J2_LINEAR ? m.H : 0.0;
+    if (m.E > Emax) Emax = m.E;
+  }
+  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
+
+  // weights (Sec. 3.1): w > 0, sum 1
+  double ws = 0.0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (!(leaf_w[j] > 0.0) || !isfinite(leaf_w[j]))
+      return fail(DMN_ERR_ARG, "dmn_create: leaf weight %d is not positive", j);
+    if (phase_map[j] >= n_mats)
+      return fail(DMN_ERR_ARG, "dmn_create: phase_map[%d]=%d >= n_mats", j, phase_map[j]);
+    ws += leaf_w[j];
+  }
+  if (fabs(ws - 1.0) > 1e-12) return fail(DMN_ERR_ARG, "dmn_create: weights sum to %.17g", ws);
+
+  // node table: n (normalised), c1, c2, w c1 c2; weight propagation bottom-up
+  std::vector<double> node(6 * N);
+  std::vector<double> wl(leaf_w, leaf_w + nleaf), wn;
+  for (int k = K; k >= 1; --k) {
+    const int cnt = 1 << (k - 1);
+    wn.assign(cnt, 0.0);
+    for (int i = 0; i < cnt; ++i) {
+      const double wa = wl[2 * i], wb = wl[2 * i + 1], w = wa + wb;
+      const int p = nleaf - (1 << k) + i;
+      const double *nv = normals + 3 * p;
+      const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (!(nn > 0.0) || !isfinite(nn))
+        return fail(DMN_ERR_ARG, "dmn_create: normal %d is zero or not finite", p);
+      double *r = &node[6 * p];
+      r[0] = nv[0] / nn;
+      r[1] = nv[1] / nn;
+      r[2] = nv[2] / nn;
+      r[3] = wa / w;
+      r[4] = 1.0 - r[3];
+      r[5] = w * r[3] * r[4];
+      wn[i] = w;
+    }
+    wl.swap(wn);
+  }
+  // z offsets in a state block
+  std::vector<int> zoff(nleaf);
+  int off = 8 + 3 * N;
+  for (int j = 0; j < nleaf; ++j) {
+    if (mats[phase_map[j]].kind == DMN_MAT_J2_LINEAR) {
+      zoff[j] = off;
+      off += 7;
+    } else {
+      zoff[j] = -1;
+    }
+  }
+  const int zend = off;
+  if (off & 1) off += 1;
+
+  dmn_handle h = new dmn_handle_s();
+  memset(h, 0, sizeof(*h));
+  h->K = K;
+  h->N = N;
+  h->nleaf = nleaf;
+  h->SW = off;
+  h->zend = zend;
+  h->n_mats = n_mats;
+  h->opt = o;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { free_handle(h); return cuda_fail(e, "cudaGetDevice"); }
+  if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  for (int mixed = 0; mixed < 2; ++mixed) {
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (solve_smem_bytes(K, mixed) > (size_t)smem_optin) {
+      h->blocks_per_sm[mixed] = 0;  // this precision does not fit at this depth
+      continue;
+    }
+    if ((e = prepare_solve(K, mixed != 0, &h->blocks_per_sm[mixed])) != cudaSuccess) {
+      free_handle(h);
+      return cuda_fail(e, "prepare_solve");
+    }
+  }
+  if (h->blocks_per_sm[o.precision == DMN_PREC_MIXED] < 1) {
+    free_handle(h);
+    return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
+  }
+  if ((e = cudaMalloc(&h->d_node, sizeof(double) * 6 * N)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(e, "cudaMalloc");
+  }
+  if ((e = cudaMemcpy(h->d_node, node.data(), sizeof(double) * 6 * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_phase, phase_map, nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_zoff, zoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * 8 * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    free_handle(h);
+    return cuda_fail(e, "cudaMemcpy");
+  }
+  *out = h;
+  return DMN_OK;
+}
+
+extern "C" dmn_status dmn_destroy(dmn_handle h) {
+  g_err[0] = 0;
+  if (!h) return fail(DMN_ERR_ARG, "dmn_destroy: NULL handle");
+  free_handle(h);
+  return DMN_OK;
+}
+
+extern "C" int64_t dmn_state_words(dmn_handle h) { return h ? h->SW : -1; }
+
+__global__ void dmn_state_init_kernel(double *s, int64_t n, int SW, const double *theta0) {
+  const int64_t total = n * (int64_t)SW;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pt = i / SW;
+    const int w = int(i - pt * SW);
+    s[i] = (w == 6) ? theta0[pt] : 0.0;
+  }
+}
+
+extern "C" dmn_status dmn_state_init(dmn_handle h, double *d_state, int64_t n_points,
+                                     const double *d_theta0, dmn_stream stream) {
+  g_err[0] = 0;
+  if (!h) return fail(DMN_ERR_ARG, "dmn_state_init: NULL handle");
+  if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_state_init: n_points < 0");
+  if (n_points == 0) return DMN_OK;
+  if (!d_state || !d_theta0) return fail(DMN_ERR_ARG, "dmn_state_init: NULL pointer");
+  if (((uintptr_t)d_state & 15) != 0) return fail(DMN_ERR_ARG, "dmn_state_init: state not 16-byte aligned");
+  const int64_t total = n_points * h->SW;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 8 * h->num_sms * 8) grid = 8 * h->num_sms * 8;
+  dmn_state_init_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_state, n_points, h->SW, d_theta0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "dmn_state_init launch");
+  return DMN_OK;
+}
+
+extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points,
+                               const double *d_deps, const double *d_theta, double dt,
+                               const double *d_state_in, double *d_state_out, double *d_out,
+                               int32_t *d_status, int32_t *d_iters) {
+  g_err[0] = 0;
+  if (!h) return fail(DMN_ERR_ARG, "dmn_eval: NULL handle");
+  if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_eval: n_points < 0");
+  if (n_points == 0) return DMN_OK;
+  if (!d_deps || !d_theta || !d_state_in || !d_state_out || !d_out || !d_status || !d_iters)
+    return fail(DMN_ERR_ARG, "dmn_eval: NULL pointer");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(DMN_ERR_ARG, "dmn_eval: dt must be > 0");
+  if (d_state_in == d_state_out) return fail(DMN_ERR_ARG, "dmn_eval: state_in aliases state_out");
+  const size_t sbytes = sizeof(double) * (size_t)h->SW * (size_t)n_points;
+  const char *a = (const char *)d_state_in, *b = (const char *)d_state_out;
+  if (a < b + sbytes && b < a + sbytes) return fail(DMN_ERR_ARG, "dmn_eval: state_in overlaps state_out");
+  if ((((uintptr_t)d_state_in) & 15) || (((uintptr_t)d_state_out) & 15))
+    return fail(DMN_ERR_ARG, "dmn_eval: state buffers must be 16-byte aligned");
+  const bool mixed = h->opt.precision == DMN_PREC_MIXED;
+  SolveParams P;
+  memset(&P, 0, sizeof(P));
+  P.K = h->K;
+  P.N = h->N;
+  P.G = 1 << (h->K - 1);
+  P.SW = h->SW;
+  P.zend = h->zend;
+  P.n_mats = h->n_mats;
+  P.maxit = h->opt.maxit;
+  P.maxbt = h->opt.maxbacktrack;
+  P.tol = h->opt.tol;
+  P.gamma = h->opt.gamma;
+  P.res_floor = h->opt.res_floor;
+  P.dt = dt;
+  P.node = h->d_node;
+  P.phase = h->d_phase;
+  P.zoff = h->d_zoff;
+  P.mat = h->d_mat;
+  P.n_points = n_points;
+  P.deps = d_deps;
+  P.theta = d_theta;
+  P.sin = d_state_in;
+  P.sout = d_state_out;
+  P.out = d_out;
+  P.status = d_status;
+  P.iters = d_iters;
+  int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm[mixed];
+  if (grid > n_points) grid = n_points;
+  cudaError_t e = launch_solve(P, mixed, (int)grid, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dmn_eval launch");
+  return DMN_OK;
+}

@@ -1,0 +1,12 @@
+// dmn_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "dmn_kernels.cuh"
+
+namespace dmn {
+size_t solve_smem_bytes(int K, bool mixed);
+cudaError_t prepare_solve(int K, bool mixed, int *blocks_per_sm);
+cudaError_t launch_solve(const SolveParams &P, bool mixed, int grid, cudaStream_t s);
+}  // namespace dmn

@@ -1,0 +1,383 @@
+// dmn_kernels.cuh -- device code of the DMN online evaluation (arXiv 2109.14403,
+// Sec. 3.3, Algorithm 1) for sm_103a.
+//
+// Mapping: one CTA per Gauss point (grid-stride over points), G = 2^(K-1)
+// threads; thread t owns the bottom laminate t (paper index t) and its two
+// leaves 2t, 2t+1.  A node (level k, position i) is owned by thread
+// i * 2^(K-k), the owner of its leftmost bottom laminate.
+//
+// Newton system (eq. Newton) by exact hierarchical condensation.  For a fixed
+// strain perturbation e of a node, the minimum of the quadratic Newton model of
+// its subtree is 1/2 e.C_hat e + s_hat.e, with
+//   K_p   = B^T (c2 C_L + c1 C_R) B                     (3x3, SPD)
+//   a_p   = -K_p^{-1} B^T (dC e + ds),   dC = C_L - C_R, ds = s_L - s_R
+//   C_hat = c1 C_L + c2 C_R - c1 c2 dC B K_p^{-1} B^T dC
+//   s_hat = c1 s_L + c2 s_R - c1 c2 dC B K_p^{-1} B^T ds
+// where B a = sym(a (x) n_p).  This is the block elimination of
+// A^T W dsigma/deps A in postorder; with e = 0 at the root a top-down sweep
+// gives the Newton increment exactly.  The same recursion applied to
+// dsigma/dtheta, dD/deps and dD/dtheta gives the four algorithmic tangents at
+// the root (eqs. ddsdde, ddsddt, drplde, drpldt) without extra right-hand
+// sides.  The residual A^T W sigma of Algorithm 1 is, node by node,
+//   r_p = w_p c1 c2 B^T (sigma_bar_L - sigma_bar_R)
+// with sigma_bar the plain weighted mean stress of a subtree (FP64).
+//
+// Precision: TF = double (every step FP64) or float (mixed).  In mixed mode
+// the condensed stress is carried as sigma_bar (FP64) + a TF correction, so
+// the Newton right-hand side is formed from FP64 stress differences and only
+// the O(residual) correction is rounded to FP32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmn {
+
+constexpr double kRsq2 = 0.70710678118654752440;
+constexpr int kMaxMats = 16;
+constexpr int kOutWords = 57;
+
+struct MatDev {
+  double kind, Kb, G, alpha, theta0, sy0, dsy, H;
+};
+
+struct SolveParams {
+  int K, N, G, SW;         // depth, nodes, threads per point, state words
+  int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
+  double tol, gamma, res_floor, dt;
+  const double *node;      // [N][6]: n0 n1 n2 c1 c2 w*c1*c2 (paper order)
+  const uint8_t *phase;    // [2^K]
+  const int *zoff;         // [2^K]: offset of the leaf's z in a state block, -1 none
+  const double *mat;       // [n_mats][8] as MatDev
+  int64_t n_points;
+  const double *deps, *theta, *sin;
+  double *sout, *out;
+  int *status, *iters;
+};
+
+// ------------------------------------------------------------------ helpers
+__host__ __device__ constexpr int sidx(int i, int j) {
+  // packed upper triangle of a symmetric 6x6, i <= j
+  return i * 6 - (i * (i - 1)) / 2 + (j - i);
+}
+template <typename T>
+__device__ __forceinline__ T sget(const T *S, int i, int j) {
+  return i <= j ? S[sidx(i, j)] : S[sidx(j, i)];
+}
+
+// B a = sym(a (x) n) as a Mandel vector
+template <typename T>
+__device__ __forceinline__ void bvec(const T n[3], const T a[3], T out[6]) {
+  const T r = T(kRsq2);
+  out[0] = a[0] * n[0];
+  out[1] = a[1] * n[1];
+  out[2] = a[2] * n[2];
+  out[3] = r * (a[1] * n[2] + a[2] * n[1]);
+  out[4] = r * (a[0] * n[2] + a[2] * n[0]);
+  out[5] = r * (a[0] * n[1] + a[1] * n[0]);
+}
+// B^T s = s n (traction)
+template <typename T>
+__device__ __forceinline__ void btvec(const T n[3], const T s[6], T out[3]) {
+  const T r = T(kRsq2);
+  out[0] = s[0] * n[0] + r * (s[5] * n[1] + s[4] * n[2]);
+  out[1] = s[1] * n[1] + r * (s[5] * n[0] + s[3] * n[2]);
+  out[2] = s[2] * n[2] + r * (s[4] * n[0] + s[3] * n[1]);
+}
+
+// condensed record of a subtree (or a leaf)
+template <typename TF>
+struct Rec {
+  double sb[6];   // weighted mean stress (FP64)
+  double Ds, Xs;  // weighted mean coupling term and dissipation (FP64)
+  TF C[21];       // condensed tangent
+  TF ds[6];       // correction of the condensed stress (s_hat = sb + ds)
+  TF tau[6];      // condensed d sigma / d theta
+  TF dd[6];       // condensed d D / d eps
+  TF gg;          // condensed d D / d theta
+};
+constexpr int kRecWords = 8 + 40;  // exchange slot in doubles
+
+// ------------------------------------------------------------------ phase laws
+// Leaf update at strain eps (FP64) and temperature theta.  Stress, D and the
+// dissipation in FP64; derivatives in TF.  zn = internal variables at t^n
+// (J2 only), trn = trace of the leaf strain at t^n.
+template <typename TF>
+__device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], double theta,
+                                          const double *zn, double trn, double dt, Rec<TF> &R,
+                                          double znew[7]) {
+  const double Kb = m.Kb, G = m.G;
+  const double dth = theta - m.theta0;
+  double ee[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) ee[c] = eps[c] - (c < 3 ? m.alpha * dth : 0.0);
+  const bool j2 = m.kind > 0.5;
+  if (j2) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ee[c] -= zn[c];
+  }
+  const double tr = ee[0] + ee[1] + ee[2];
+  double s[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = 2.0 * G * (ee[c] - (c < 3 ? tr / 3.0 : 0.0));
+#pragma unroll
+  for (int c = 0; c < 6; ++c) R.sb[c] = (c < 3 ? Kb * tr : 0.0) + s[c];
+  const double treps = eps[0] + eps[1] + eps[2];
+  const double a3K = 3.0 * Kb * m.alpha;
+  R.Ds = -a3K * theta * (treps - trn) / dt;
+  R.Xs = 0.0;
+  double gg = -a3K * (treps - trn) / dt;
+  double th1 = 1.0, thb = 0.0, kd = 0.0, ktau = 0.0;
+  double N[6] = {0, 0, 0, 0, 0, 0};
+  if (j2) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) znew[c] = zn[c];
+    double sy = m.sy0 + m.dsy * dth, dsy = m.dsy;
+    if (sy < 1e-6) { sy = 1e-6; dsy = 0.0; }
+    double sn2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sn2 += s[c] * s[c];
+    const double sn = sqrt(sn2);
+    const double qtr = 1.2247448713915890491 * sn;
+    const double f = qtr - sy - m.H * zn[6];
+    if (f > 0.0) {
+      const double den = 3.0 * G + m.H;
+      const double dp = f / den;
+      const double isn = 1.0 / sn;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) N[c] = s[c] * isn;
+      const double kr = 2.0 * G * 1.2247448713915890491 * dp;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        R.sb[c] -= kr * N[c];
+        znew[c] = zn[c] + 1.2247448713915890491 * dp * N[c];
+      }
+      znew[6] = zn[6] + dp;
+      const double g3 = 3.0 * G * dp / qtr;
+      th1 = 1.0 - g3;
+      thb = 3.0 * G / den - g3;
+      const double ddp_dth = -dsy / den;
+      ktau = -2.0 * G * 1.2247448713915890491 * ddp_dth;
+      kd = sy * 1.2247448713915890491 * 2.0 * G / den / dt;
+      R.Ds += sy * dp / dt;
+      R.Xs = sy * dp / dt;
+      gg += (dsy * dp + sy * ddp_dth) / dt;
+    }
+  }
+  // tangent C = 3K P1 + 2G th1 P2 - 2G thb N (x) N
+  const TF cP1 = TF(Kb - 2.0 * G * th1 / 3.0);  // coefficient of m m^T
+  const TF cI = TF(2.0 * G * th1);
+  const TF cN = TF(2.0 * G * thb);
+  TF Nf[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) Nf[c] = TF(N[c]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j)
+      R.C[sidx(i, j)] = (i < 3 && j < 3 ? cP1 : TF(0)) + (i == j ? cI : TF(0)) - cN * Nf[i] * Nf[j];
+  const TF ta = TF(-a3K), tn = TF(ktau);
+  const TF da_ = TF(-a3K * theta / dt), dn = TF(kd);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    R.tau[c] = (c < 3 ? ta : TF(0)) + tn * Nf[c];
+    R.dd[c] = (c < 3 ? da_ : TF(0)) + dn * Nf[c];
+    R.ds[c] = TF(0);
+  }
+  R.gg = TF(gg);
+}
+
+// ------------------------------------------------------------------ condensation
+// Combine children L (in/out) and R of node p.  Writes G_p (3x6) and h_p (3)
+// for the back-substitution, and returns |r_p|^2 of the Algorithm 1 residual.
+template <typename TF>
+__device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const double *nodep,
+                                          TF *gh) {
+  const double nd[3] = {nodep[0], nodep[1], nodep[2]};
+  const double c1d = nodep[3], c2d = nodep[4], wcc = nodep[5];
+  const TF n[3] = {TF(nd[0]), TF(nd[1]), TF(nd[2])};
+  const TF c1 = TF(c1d), c2 = TF(c2d), cc = TF(c1d * c2d);
+  // residual and plain sums (FP64)
+  double dsb[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dsb[c] = L.sb[c] - R.sb[c];
+  double rb[3];
+  btvec(nd, dsb, rb);
+  double r2 = 0.0;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r2 += (wcc * rb[e]) * (wcc * rb[e]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) L.sb[c] = c1d * L.sb[c] + c2d * R.sb[c];
+  L.Ds = c1d * L.Ds + c2d * R.Ds;
+  L.Xs = c1d * L.Xs + c2d * R.Xs;
+  // M = c2 C_L + c1 C_R, dC = C_L - C_R (dC in place of L.C)
+  TF M[21];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) {
+    M[q] = c2 * L.C[q] + c1 * R.C[q];
+    L.C[q] = L.C[q] - R.C[q];
+  }
+  // K = B^T M B
+  TF MB[6][3];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    TF row[6];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) row[b] = sget(M, a, b);
+    btvec(n, row, MB[a]);
+  }
+  TF Kk[3][3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    TF col[6], t3[3];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) col[a] = MB[a][f];
+    btvec(n, col, t3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) Kk[e][f] = t3[e];
+  }
+  // K^{-1} by the adjugate (K is SPD 3x3)
+  const TF k00 = Kk[0][0], k11 = Kk[1][1], k22 = Kk[2][2];
+  const TF k01 = TF(0.5) * (Kk[0][1] + Kk[1][0]);
+  const TF k02 = TF(0.5) * (Kk[0][2] + Kk[2][0]);
+  const TF k12 = TF(0.5) * (Kk[1][2] + Kk[2][1]);
+  const TF a00 = k11 * k22 - k12 * k12, a01 = k02 * k12 - k01 * k22, a02 = k01 * k12 - k02 * k11;
+  const TF a11 = k00 * k22 - k02 * k02, a12 = k01 * k02 - k00 * k12, a22 = k00 * k11 - k01 * k01;
+  const TF idet = TF(1) / (k00 * a00 + k01 * a01 + k02 * a02);
+  const TF Ki[3][3] = {{a00 * idet, a01 * idet, a02 * idet},
+                       {a01 * idet, a11 * idet, a12 * idet},
+                       {a02 * idet, a12 * idet, a22 * idet}};
+  // U = dC B (6x3), G = K^{-1} U^T (3x6)
+  TF U[6][3];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    TF row[6];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) row[b] = sget(L.C, a, b);
+    btvec(n, row, U[a]);
+  }
+  TF Gm[3][6];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Gm[e][a] = Ki[e][0] * U[a][0] + Ki[e][1] * U[a][1] + Ki[e][2] * U[a][2];
+  // condensed stress correction: B^T ds = B^T (sb_L - sb_R) + B^T (ds_L - ds_R)
+  TF hs[3];
+  {
+    TF dds[6], t3[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dds[c] = L.ds[c] - R.ds[c];
+    btvec(n, dds, t3);
+    TF b3[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) b3[e] = TF(rb[e]) + t3[e];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) hs[e] = Ki[e][0] * b3[0] + Ki[e][1] * b3[1] + Ki[e][2] * b3[2];
+  }
+  // store G_p, h_p
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+#pragma unroll
+    for (int a = 0; a < 6; ++a) gh[6 * e + a] = Gm[e][a];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) gh[18 + e] = hs[e];
+  // vectors: tau, dd (and their h), ds
+  TF ht[3];
+  {
+    TF dv[6], t3[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) dv[c] = L.tau[c] - R.tau[c];
+    btvec(n, dv, t3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) ht[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
+  }
+  TF hd[3], ddiff[6];
+  {
+    TF t3[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ddiff[c] = L.dd[c] - R.dd[c];
+    btvec(n, ddiff, t3);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) hd[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
+  }
+  // g_hat = c1 g_L + c2 g_R - c1 c2 (B^T d_diff) . h_tau
+  {
+    TF bd[3];
+    btvec(n, ddiff, bd);
+    L.gg = c1 * L.gg + c2 * R.gg - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const TF Uhs = U[a][0] * hs[0] + U[a][1] * hs[1] + U[a][2] * hs[2];
+    const TF Uht = U[a][0] * ht[0] + U[a][1] * ht[1] + U[a][2] * ht[2];
+    const TF Uhd = U[a][0] * hd[0] + U[a][1] * hd[1] + U[a][2] * hd[2];
+    L.ds[a] = c1 * L.ds[a] + c2 * R.ds[a] - cc * Uhs;
+    L.tau[a] = c1 * L.tau[a] + c2 * R.tau[a] - cc * Uht;
+    L.dd[a] = c1 * L.dd[a] + c2 * R.dd[a] - cc * Uhd;
+  }
+  // C_hat = c1 C_L + c2 C_R - c1 c2 U G  with c1 C_L + c2 C_R = M + (c1 - c2) dC
+  const TF cm = c1 - c2;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j) {
+      const int q = sidx(i, j);
+      const TF ug = U[i][0] * Gm[0][j] + U[i][1] * Gm[1][j] + U[i][2] * Gm[2][j];
+      L.C[q] = M[q] + cm * L.C[q] - cc * ug;
+    }
+  return r2;
+}
+
+// ------------------------------------------------------------------ record exchange
+template <typename TF>
+__device__ __forceinline__ void rec_shfl_down(Rec<TF> &dst, const Rec<TF> &src, int off,
+                                              unsigned mask, int W) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) dst.sb[c] = __shfl_down_sync(mask, src.sb[c], off, W);
+  dst.Ds = __shfl_down_sync(mask, src.Ds, off, W);
+  dst.Xs = __shfl_down_sync(mask, src.Xs, off, W);
+#pragma unroll
+  for (int q = 0; q < 21; ++q) dst.C[q] = __shfl_down_sync(mask, src.C[q], off, W);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    dst.ds[c] = __shfl_down_sync(mask, src.ds[c], off, W);
+    dst.tau[c] = __shfl_down_sync(mask, src.tau[c], off, W);
+    dst.dd[c] = __shfl_down_sync(mask, src.dd[c], off, W);
+  }
+  dst.gg = __shfl_down_sync(mask, src.gg, off, W);
+}
+
+template <typename TF>
+__device__ __forceinline__ void rec_store(double *slot, const Rec<TF> &r) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) slot[c] = r.sb[c];
+  slot[6] = r.Ds;
+  slot[7] = r.Xs;
+#pragma unroll
+  for (int q = 0; q < 21; ++q) slot[8 + q] = double(r.C[q]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    slot[29 + c] = double(r.ds[c]);
+    slot[35 + c] = double(r.tau[c]);
+    slot[41 + c] = double(r.dd[c]);
+  }
+  slot[47] = double(r.gg);
+}
+
+template <typename TF>
+__device__ __forceinline__ void rec_load(Rec<TF> &r, const double *slot) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) r.sb[c] = slot[c];
+  r.Ds = slot[6];
+  r.Xs = slot[7];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) r.C[q] = TF(slot[8 + q]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    r.ds[c] = TF(slot[29 + c]);
+    r.tau[c] = TF(slot[35 + c]);
+    r.dd[c] = TF(slot[41 + c]);
+  }
+  r.gg = TF(slot[47]);
+}
+
+}  // namespace dmn

@@ -1,0 +1,177 @@
+"""Thin ctypes binding of the C ABI in ``include/dmn.h``.
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  PyTorch tensors provide device memory and streams.  If the library
+is missing the import fails; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+DMN_OK = 0
+PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+OUT_WORDS = 57
+
+_lib = None
+
+
+class dmn_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("E", ctypes.c_double),
+                ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("theta0", ctypes.c_double),
+                ("sy0", ctypes.c_double), ("dsy_dT", ctypes.c_double), ("H", ctypes.c_double)]
+
+
+class dmn_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("res_floor", ctypes.c_double), ("maxit", ctypes.c_int32),
+                ("maxbacktrack", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+# every symbol the header declares, with its signature
+_P, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "dmn_default_options": (None, [_P]),
+    "dmn_create": (_I32, [_P, _I32, _P, _P, _P, _P, _I32, _P]),
+    "dmn_destroy": (_I32, [_P]),
+    "dmn_state_words": (_I64, [_P]),
+    "dmn_state_init": (_I32, [_P, _P, _I64, _P, _P]),
+    "dmn_eval": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P]),
+    "dmn_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libdmn.so`` (building it with nvcc if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise ImportError(f"DMN CUDA library not built: {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc, what):
+    if rc != DMN_OK:
+        msg = _lib.dmn_last_error().decode(errors="replace")
+        raise RuntimeError(f"{what} failed with status {rc}: {msg}")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def materials_from_rows(rows):
+    """Material table rows (kind, E, nu, alpha, theta0, sy0, dsy_dT, H) -> ctypes array."""
+    rows = np.asarray(rows, np.float64).reshape(-1, 8)
+    arr = (dmn_material * rows.shape[0])()
+    for i, r in enumerate(rows):
+        arr[i].kind = int(r[0])
+        arr[i].E, arr[i].nu, arr[i].alpha, arr[i].theta0 = r[1], r[2], r[3], r[4]
+        arr[i].sy0, arr[i].dsy_dT, arr[i].H = r[5], r[6], r[7]
+    return arr
+
+
+class DMN:
+    """A DMN handle on the current CUDA device (``dmn_create``)."""
+
+    def __init__(self, K, w, normals, phase, mats, *, tol=1e-10, maxit=50, maxbacktrack=8,
+                 gamma=0.5, precision="fp64", res_floor=0.0):
+        lib = load()
+        self.K = int(K)
+        w = np.ascontiguousarray(w, np.float64)
+        normals = np.ascontiguousarray(normals, np.float64)
+        phase = np.ascontiguousarray(phase, np.uint8)
+        mt = materials_from_rows(mats)
+        opt = dmn_options()
+        lib.dmn_default_options(ctypes.byref(opt))
+        opt.tol, opt.maxit, opt.maxbacktrack, opt.gamma = tol, maxit, maxbacktrack, gamma
+        opt.res_floor = res_floor
+        opt.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(lib.dmn_create(ctypes.byref(h), self.K, w.ctypes.data_as(_P),
+                              normals.ctypes.data_as(_P), phase.ctypes.data_as(_P),
+                              ctypes.cast(mt, _P), len(mt), ctypes.byref(opt)), "dmn_create")
+        self._h = h
+        self.state_words = int(lib.dmn_state_words(h))
+        self.nnode = (1 << self.K) - 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_lib.dmn_destroy(self._h), "dmn_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_state(self, theta0, stream=None):
+        """Allocate and initialise a state batch for ``theta0`` (CUDA float64, n)."""
+        import torch
+        n = theta0.numel()
+        s = torch.empty((n, self.state_words), dtype=torch.float64, device=theta0.device)
+        _check(_lib.dmn_state_init(self._h, _dev(s, torch.float64, None, "state"), n,
+                                   _dev(theta0, torch.float64, (n,), "theta0"),
+                                   _stream_ptr(stream)), "dmn_state_init")
+        return s
+
+    def eval(self, deps, theta, dt, state_in, state_out=None, out=None, status=None, iters=None,
+             stream=None):
+        """One increment at every point (``dmn_eval``).  Returns (state_out, out, status, iters)."""
+        import torch
+        n = deps.shape[0]
+        dev = deps.device
+        if state_out is None:
+            state_out = torch.empty_like(state_in)
+        if out is None:
+            out = torch.empty((n, OUT_WORDS), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=dev)
+        if iters is None:
+            iters = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(_lib.dmn_eval(self._h, _stream_ptr(stream), n,
+                             _dev(deps, torch.float64, (n, 6), "deps"),
+                             _dev(theta, torch.float64, (n,), "theta"), float(dt),
+                             _dev(state_in, torch.float64, (n, self.state_words), "state_in"),
+                             _dev(state_out, torch.float64, (n, self.state_words), "state_out"),
+                             _dev(out, torch.float64, (n, OUT_WORDS), "out"),
+                             _dev(status, torch.int32, (n,), "status"),
+                             _dev(iters, torch.int32, (n,), "iters")), "dmn_eval")
+        return state_out, out, status, iters
