@@ -18,7 +18,8 @@ struct dmn_handle_s {
   dmn_options opt;
   int device, num_sms;
   int blocks_per_sm[2];  // FP64, mixed
-  double *d_node;        // [N][6]
+  double *d_node;        // [N][kNodeWords]
+  double *d_leafw;       // [nleaf]
   uint8_t *d_phase;      // [nleaf]
   int *d_zoff;           // [nleaf]
   double *d_mat;         // [n_mats][8]
@@ -55,6 +56,7 @@ extern "C" void dmn_default_options(dmn_options *o) {
 static void free_handle(dmn_handle h) {
   if (!h) return;
   cudaFree(h->d_node);
+  cudaFree(h->d_leafw);
   cudaFree(h->d_phase);
   cudaFree(h->d_zoff);
   cudaFree(h->d_mat);
@@ -115,8 +117,9 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   }
   if (fabs(ws - 1.0) > 1e-12) return fail(DMN_ERR_ARG, "dmn_create: weights sum to %.17g", ws);
 
-  // node table: n (normalised), c1, c2, w c1 c2; weight propagation bottom-up
-  std::vector<double> node(6 * N);
+  // node table: n (normalised), c1, c2, w, w c1 c2, 1/(w c1 c2); weight
+  // propagation bottom-up (Sec. 3.1)
+  std::vector<double> node(kNodeWords * N);
   std::vector<double> wl(leaf_w, leaf_w + nleaf), wn;
   for (int k = K; k >= 1; --k) {
     const int cnt = 1 << (k - 1);
@@ -128,13 +131,15 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
       if (!(nn > 0.0) || !isfinite(nn))
         return fail(DMN_ERR_ARG, "dmn_create: normal %d is zero or not finite", p);
-      double *r = &node[6 * p];
+      double *r = &node[kNodeWords * p];
       r[0] = nv[0] / nn;
       r[1] = nv[1] / nn;
       r[2] = nv[2] / nn;
       r[3] = wa / w;
       r[4] = 1.0 - r[3];
-      r[5] = w * r[3] * r[4];
+      r[5] = w;
+      r[6] = w * r[3] * r[4];
+      r[7] = 1.0 / r[6];
       wn[i] = w;
     }
     wl.swap(wn);
@@ -184,14 +189,16 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
     free_handle(h);
     return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
   }
-  if ((e = cudaMalloc(&h->d_node, sizeof(double) * 6 * N)) != cudaSuccess ||
+  if ((e = cudaMalloc(&h->d_node, sizeof(double) * kNodeWords * N)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_leafw, sizeof(double) * nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMalloc");
   }
-  if ((e = cudaMemcpy(h->d_node, node.data(), sizeof(double) * 6 * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e = cudaMemcpy(h->d_node, node.data(), sizeof(double) * kNodeWords * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_leafw, leaf_w, sizeof(double) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_phase, phase_map, nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_zoff, zoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * 8 * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -271,6 +278,7 @@ extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points
   P.res_floor = h->opt.res_floor;
   P.dt = dt;
   P.node = h->d_node;
+  P.leafw = h->d_leafw;
   P.phase = h->d_phase;
   P.zoff = h->d_zoff;
   P.mat = h->d_mat;

@@ -35,6 +35,7 @@ namespace dmn {
 constexpr double kRsq2 = 0.70710678118654752440;
 constexpr int kMaxMats = 16;
 constexpr int kOutWords = 57;
+constexpr int kNodeWords = 8;
 
 struct MatDev {
   double kind, Kb, G, alpha, theta0, sy0, dsy, H;
@@ -44,7 +45,8 @@ struct SolveParams {
   int K, N, G, SW;         // depth, nodes, threads per point, state words
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
   double tol, gamma, res_floor, dt;
-  const double *node;      // [N][6]: n0 n1 n2 c1 c2 w*c1*c2 (paper order)
+  const double *node;      // [N][kNodeWords]: n0 n1 n2 c1 c2 w w*c1*c2 1/(w*c1*c2)
+  const double *leafw;     // [2^K] leaf weights
   const uint8_t *phase;    // [2^K]
   const int *zoff;         // [2^K]: offset of the leaf's z in a state block, -1 none
   const double *mat;       // [n_mats][8] as MatDev
@@ -84,48 +86,47 @@ __device__ __forceinline__ void btvec(const T n[3], const T s[6], T out[3]) {
   out[2] = s[2] * n[2] + r * (s[4] * n[0] + s[3] * n[1]);
 }
 
-// condensed record of a subtree (or a leaf)
+// condensed record of a subtree (or a leaf), condensation precision TF
 template <typename TF>
 struct Rec {
-  double sb[6];   // weighted mean stress (FP64)
-  double Ds, Xs;  // weighted mean coupling term and dissipation (FP64)
   TF C[21];       // condensed tangent
-  TF ds[6];       // correction of the condensed stress (s_hat = sb + ds)
+  TF ds[6];       // condensed stress minus the plain weighted mean stress
   TF tau[6];      // condensed d sigma / d theta
   TF dd[6];       // condensed d D / d eps
   TF gg;          // condensed d D / d theta
 };
-constexpr int kRecWords = 8 + 40;  // exchange slot in doubles
+constexpr int kRecWords = 40;  // exchange slot in doubles
 
 // ------------------------------------------------------------------ phase laws
-// Leaf update at strain eps (FP64) and temperature theta.  Stress, D and the
-// dissipation in FP64; derivatives in TF.  zn = internal variables at t^n
-// (J2 only), trn = trace of the leaf strain at t^n.
+// Leaf update at strain eps (FP64) and temperature theta (Sec. 4).  Stress,
+// coupling term D and dissipation X in FP64; derivatives into the TF record.
+// zn = internal variables at t^n (J2 only), trn = trace of the leaf strain at
+// t^n.  The yield test compares squares, so elastic leaves take no square root.
 template <typename TF>
 __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], double theta,
-                                          const double *zn, double trn, double dt, Rec<TF> &R,
-                                          double znew[7]) {
+                                          const double *zn, double trn, double dt, double sig[6],
+                                          double &D, double &X, Rec<TF> &R, double znew[7]) {
   const double Kb = m.Kb, G = m.G;
   const double dth = theta - m.theta0;
+  const double ath = m.alpha * dth;
+  const bool j2 = m.kind > 0.5;
   double ee[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) ee[c] = eps[c] - (c < 3 ? m.alpha * dth : 0.0);
-  const bool j2 = m.kind > 0.5;
-  if (j2) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) ee[c] -= zn[c];
-  }
-  const double tr = ee[0] + ee[1] + ee[2];
+  for (int c = 0; c < 6; ++c) ee[c] = eps[c] - (c < 3 ? ath : 0.0) - (j2 ? zn[c] : 0.0);
+  const double tr3 = (ee[0] + ee[1] + ee[2]) * (1.0 / 3.0);
+  const double G2 = 2.0 * G;
   double s[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s[c] = 2.0 * G * (ee[c] - (c < 3 ? tr / 3.0 : 0.0));
+  for (int c = 0; c < 6; ++c) s[c] = G2 * (c < 3 ? ee[c] - tr3 : ee[c]);
+  const double p3 = 3.0 * Kb * tr3;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) R.sb[c] = (c < 3 ? Kb * tr : 0.0) + s[c];
+  for (int c = 0; c < 6; ++c) sig[c] = (c < 3 ? p3 + s[c] : s[c]);
   const double treps = eps[0] + eps[1] + eps[2];
   const double a3K = 3.0 * Kb * m.alpha;
-  R.Ds = -a3K * theta * (treps - trn) / dt;
-  R.Xs = 0.0;
-  double gg = -a3K * (treps - trn) / dt;
+  const double idt = 1.0 / dt;
+  D = -a3K * theta * (treps - trn) * idt;
+  X = 0.0;
+  double gg = -a3K * (treps - trn) * idt;
   double th1 = 1.0, thb = 0.0, kd = 0.0, ktau = 0.0;
   double N[6] = {0, 0, 0, 0, 0, 0};
   if (j2) {
@@ -136,19 +137,19 @@ __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], 
     double sn2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 6; ++c) sn2 += s[c] * s[c];
-    const double sn = sqrt(sn2);
-    const double qtr = 1.2247448713915890491 * sn;
-    const double f = qtr - sy - m.H * zn[6];
-    if (f > 0.0) {
+    const double yr = sy + m.H * zn[6];
+    if (1.5 * sn2 > yr * yr) {
+      const double sn = sqrt(sn2);
+      const double qtr = 1.2247448713915890491 * sn;
       const double den = 3.0 * G + m.H;
-      const double dp = f / den;
+      const double dp = (qtr - yr) / den;
       const double isn = 1.0 / sn;
 #pragma unroll
       for (int c = 0; c < 6; ++c) N[c] = s[c] * isn;
-      const double kr = 2.0 * G * 1.2247448713915890491 * dp;
+      const double kr = G2 * 1.2247448713915890491 * dp;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        R.sb[c] -= kr * N[c];
+        sig[c] -= kr * N[c];
         znew[c] = zn[c] + 1.2247448713915890491 * dp * N[c];
       }
       znew[6] = zn[6] + dp;
@@ -156,17 +157,17 @@ __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], 
       th1 = 1.0 - g3;
       thb = 3.0 * G / den - g3;
       const double ddp_dth = -dsy / den;
-      ktau = -2.0 * G * 1.2247448713915890491 * ddp_dth;
-      kd = sy * 1.2247448713915890491 * 2.0 * G / den / dt;
-      R.Ds += sy * dp / dt;
-      R.Xs = sy * dp / dt;
-      gg += (dsy * dp + sy * ddp_dth) / dt;
+      ktau = -G2 * 1.2247448713915890491 * ddp_dth;
+      kd = sy * 1.2247448713915890491 * G2 / den * idt;
+      D += sy * dp * idt;
+      X = sy * dp * idt;
+      gg += (dsy * dp + sy * ddp_dth) * idt;
     }
   }
   // tangent C = 3K P1 + 2G th1 P2 - 2G thb N (x) N
-  const TF cP1 = TF(Kb - 2.0 * G * th1 / 3.0);  // coefficient of m m^T
-  const TF cI = TF(2.0 * G * th1);
-  const TF cN = TF(2.0 * G * thb);
+  const TF cP1 = TF(Kb - G2 * th1 / 3.0);  // coefficient of m m^T
+  const TF cI = TF(G2 * th1);
+  const TF cN = TF(G2 * thb);
   TF Nf[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) Nf[c] = TF(N[c]);
@@ -176,7 +177,7 @@ __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], 
     for (int j = i; j < 6; ++j)
       R.C[sidx(i, j)] = (i < 3 && j < 3 ? cP1 : TF(0)) + (i == j ? cI : TF(0)) - cN * Nf[i] * Nf[j];
   const TF ta = TF(-a3K), tn = TF(ktau);
-  const TF da_ = TF(-a3K * theta / dt), dn = TF(kd);
+  const TF da_ = TF(-a3K * theta * idt), dn = TF(kd);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     R.tau[c] = (c < 3 ? ta : TF(0)) + tn * Nf[c];
@@ -187,28 +188,16 @@ __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], 
 }
 
 // ------------------------------------------------------------------ condensation
-// Combine children L (in/out) and R of node p.  Writes G_p (3x6) and h_p (3)
-// for the back-substitution, and returns |r_p|^2 of the Algorithm 1 residual.
+// Combine children L (in/out) and R of node p in precision TF.  rbv =
+// B^T (sigma_bar_L - sigma_bar_R), the node's residual divided by w c1 c2
+// (formed in FP64 by the caller).  Writes G_p (3x6) and h_p (3) for the
+// back-substitution.
 template <typename TF>
-__device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const double *nodep,
-                                          TF *gh) {
-  const double nd[3] = {nodep[0], nodep[1], nodep[2]};
-  const double c1d = nodep[3], c2d = nodep[4], wcc = nodep[5];
-  const TF n[3] = {TF(nd[0]), TF(nd[1]), TF(nd[2])};
-  const TF c1 = TF(c1d), c2 = TF(c2d), cc = TF(c1d * c2d);
-  // residual and plain sums (FP64)
-  double dsb[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) dsb[c] = L.sb[c] - R.sb[c];
-  double rb[3];
-  btvec(nd, dsb, rb);
-  double r2 = 0.0;
-#pragma unroll
-  for (int e = 0; e < 3; ++e) r2 += (wcc * rb[e]) * (wcc * rb[e]);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) L.sb[c] = c1d * L.sb[c] + c2d * R.sb[c];
-  L.Ds = c1d * L.Ds + c2d * R.Ds;
-  L.Xs = c1d * L.Xs + c2d * R.Xs;
+__device__ __forceinline__ void combine(Rec<TF> &L, const Rec<TF> &R, const double *nodep,
+                                        const TF rbv[3], TF *gh) {
+  const TF n[3] = {TF(nodep[0]), TF(nodep[1]), TF(nodep[2])};
+  const TF c1 = TF(nodep[3]), c2 = TF(nodep[4]);
+  const TF cc = c1 * c2;
   // M = c2 C_L + c1 C_R, dC = C_L - C_R (dC in place of L.C)
   TF M[21];
 #pragma unroll
@@ -260,7 +249,7 @@ __device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const do
   for (int e = 0; e < 3; ++e)
 #pragma unroll
     for (int a = 0; a < 6; ++a) Gm[e][a] = Ki[e][0] * U[a][0] + Ki[e][1] * U[a][1] + Ki[e][2] * U[a][2];
-  // condensed stress correction: B^T ds = B^T (sb_L - sb_R) + B^T (ds_L - ds_R)
+  // condensed stress: B^T ds_hat = rb + B^T (ds_L - ds_R)
   TF hs[3];
   {
     TF dds[6], t3[3];
@@ -269,18 +258,16 @@ __device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const do
     btvec(n, dds, t3);
     TF b3[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) b3[e] = TF(rb[e]) + t3[e];
+    for (int e = 0; e < 3; ++e) b3[e] = rbv[e] + t3[e];
 #pragma unroll
     for (int e = 0; e < 3; ++e) hs[e] = Ki[e][0] * b3[0] + Ki[e][1] * b3[1] + Ki[e][2] * b3[2];
   }
-  // store G_p, h_p
 #pragma unroll
   for (int e = 0; e < 3; ++e)
 #pragma unroll
     for (int a = 0; a < 6; ++a) gh[6 * e + a] = Gm[e][a];
 #pragma unroll
   for (int e = 0; e < 3; ++e) gh[18 + e] = hs[e];
-  // vectors: tau, dd (and their h), ds
   TF ht[3];
   {
     TF dv[6], t3[3];
@@ -290,21 +277,17 @@ __device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const do
 #pragma unroll
     for (int e = 0; e < 3; ++e) ht[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
   }
-  TF hd[3], ddiff[6];
+  TF hd[3], bd[3];
   {
-    TF t3[3];
+    TF ddiff[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) ddiff[c] = L.dd[c] - R.dd[c];
-    btvec(n, ddiff, t3);
+    btvec(n, ddiff, bd);
 #pragma unroll
-    for (int e = 0; e < 3; ++e) hd[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
+    for (int e = 0; e < 3; ++e) hd[e] = Ki[e][0] * bd[0] + Ki[e][1] * bd[1] + Ki[e][2] * bd[2];
   }
   // g_hat = c1 g_L + c2 g_R - c1 c2 (B^T d_diff) . h_tau
-  {
-    TF bd[3];
-    btvec(n, ddiff, bd);
-    L.gg = c1 * L.gg + c2 * R.gg - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
-  }
+  L.gg = c1 * L.gg + c2 * R.gg - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     const TF Uhs = U[a][0] * hs[0] + U[a][1] * hs[1] + U[a][2] * hs[2];
@@ -324,17 +307,12 @@ __device__ __forceinline__ double combine(Rec<TF> &L, const Rec<TF> &R, const do
       const TF ug = U[i][0] * Gm[0][j] + U[i][1] * Gm[1][j] + U[i][2] * Gm[2][j];
       L.C[q] = M[q] + cm * L.C[q] - cc * ug;
     }
-  return r2;
 }
 
 // ------------------------------------------------------------------ record exchange
 template <typename TF>
 __device__ __forceinline__ void rec_shfl_down(Rec<TF> &dst, const Rec<TF> &src, int off,
                                               unsigned mask, int W) {
-#pragma unroll
-  for (int c = 0; c < 6; ++c) dst.sb[c] = __shfl_down_sync(mask, src.sb[c], off, W);
-  dst.Ds = __shfl_down_sync(mask, src.Ds, off, W);
-  dst.Xs = __shfl_down_sync(mask, src.Xs, off, W);
 #pragma unroll
   for (int q = 0; q < 21; ++q) dst.C[q] = __shfl_down_sync(mask, src.C[q], off, W);
 #pragma unroll
@@ -349,35 +327,27 @@ __device__ __forceinline__ void rec_shfl_down(Rec<TF> &dst, const Rec<TF> &src, 
 template <typename TF>
 __device__ __forceinline__ void rec_store(double *slot, const Rec<TF> &r) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) slot[c] = r.sb[c];
-  slot[6] = r.Ds;
-  slot[7] = r.Xs;
-#pragma unroll
-  for (int q = 0; q < 21; ++q) slot[8 + q] = double(r.C[q]);
+  for (int q = 0; q < 21; ++q) slot[q] = double(r.C[q]);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    slot[29 + c] = double(r.ds[c]);
-    slot[35 + c] = double(r.tau[c]);
-    slot[41 + c] = double(r.dd[c]);
+    slot[21 + c] = double(r.ds[c]);
+    slot[27 + c] = double(r.tau[c]);
+    slot[33 + c] = double(r.dd[c]);
   }
-  slot[47] = double(r.gg);
+  slot[39] = double(r.gg);
 }
 
 template <typename TF>
 __device__ __forceinline__ void rec_load(Rec<TF> &r, const double *slot) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) r.sb[c] = slot[c];
-  r.Ds = slot[6];
-  r.Xs = slot[7];
-#pragma unroll
-  for (int q = 0; q < 21; ++q) r.C[q] = TF(slot[8 + q]);
+  for (int q = 0; q < 21; ++q) r.C[q] = TF(slot[q]);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    r.ds[c] = TF(slot[29 + c]);
-    r.tau[c] = TF(slot[35 + c]);
-    r.dd[c] = TF(slot[41 + c]);
+    r.ds[c] = TF(slot[21 + c]);
+    r.tau[c] = TF(slot[27 + c]);
+    r.dd[c] = TF(slot[33 + c]);
   }
-  r.gg = TF(slot[47]);
+  r.gg = TF(slot[39]);
 }
 
 }  // namespace dmn
