@@ -1,0 +1,120 @@
+// dfl.cuh -- float-float ("double-single") arithmetic on the FP32 pipe.
+//
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits (relative rounding ~2^-46 per operation).  GB300's
+// FP64 pipe issues at 1/61 of the FP32 rate, so the mixed-precision solve
+// carries its high-precision quantities (strains, leaf stresses, subtree
+// stress sums, residual) in this form.
+//
+// Building blocks (error-free transformations):
+//   two_sum   Knuth, TAOCP vol. 2, 4.2.2: s + e = a + b exactly, any a, b;
+//   fast_two  Dekker (1971): the same when |a| >= |b| (or a == 0);
+//   two_prod  with a fused multiply-add: p + e = a * b exactly.
+// Sums and products below follow Dekker's double-length algorithms (add,
+// mul); the square root and the quotient take the CUDA single-precision
+// result as a first approximation and apply one Newton correction computed
+// in float-float (Karp and Markstein's refinement).
+//
+// These sequences must not be re-associated: the library is compiled without
+// fast-math flags, so the compiler keeps every rounding as written.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dmn {
+
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ dfl fast_two(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ dfl operator+(dfl x, dfl y) {
+  const dfl s = two_sum(x.hi, y.hi);
+  return fast_two(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ dfl operator-(dfl x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfl operator-(dfl x, dfl y) { return x + (-y); }
+__device__ __forceinline__ dfl operator*(dfl x, dfl y) {
+  dfl p = two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+  return fast_two(p.hi, p.lo);
+}
+__device__ __forceinline__ dfl operator*(dfl x, float c) {
+  dfl p = two_prod(x.hi, c);
+  p.lo = fmaf(x.lo, c, p.lo);
+  return fast_two(p.hi, p.lo);
+}
+__device__ __forceinline__ dfl &operator+=(dfl &x, dfl y) { return x = x + y; }
+__device__ __forceinline__ dfl &operator-=(dfl &x, dfl y) { return x = x - y; }
+
+// exact split of a double (FP64 conversions: used at loads only)
+__device__ __forceinline__ dfl dfl_from(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - double(h))};
+}
+__device__ __forceinline__ double dfl_to(dfl x) { return double(x.hi) + double(x.lo); }
+
+__device__ __forceinline__ dfl dfl_sqrt(dfl x) {
+  if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+  const float y = sqrtf(x.hi);
+  const dfl y2 = two_prod(y, y);
+  const float r = ((x.hi - y2.hi) - y2.lo) + x.lo;  // x - y^2 (leading part exact)
+  return fast_two(y, r / (y + y));
+}
+__device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
+  const float q1 = a.hi / b.hi;
+  const dfl r = a - b * q1;
+  return fast_two(q1, r.hi / b.hi);
+}
+
+// ---------------------------------------------------------------- generic
+// The solve is written once for the high-precision type HP = double (every
+// step FP64) or HP = dfl (mixed).  These overloads give both the same names.
+__device__ __forceinline__ double hp_from(double d, double *) { return d; }
+__device__ __forceinline__ dfl hp_from(double d, dfl *) { return dfl_from(d); }
+__device__ __forceinline__ double hp_to(double x) { return x; }
+__device__ __forceinline__ double hp_to(dfl x) { return dfl_to(x); }
+__device__ __forceinline__ double hp_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ dfl hp_sqrt(dfl x) { return dfl_sqrt(x); }
+__device__ __forceinline__ double hp_div(double a, double b) { return a / b; }
+__device__ __forceinline__ dfl hp_div(dfl a, dfl b) { return dfl_div(a, b); }
+// leading part as a float (for quantities needed only to FP32 accuracy)
+__device__ __forceinline__ float hp_f(double x) { return float(x); }
+__device__ __forceinline__ float hp_f(dfl x) { return x.hi; }
+// value in the condensation precision TF (double for HP = double, float for dfl)
+__device__ __forceinline__ double tf_of(double x, double *) { return x; }
+__device__ __forceinline__ float tf_of(dfl x, float *) { return x.hi; }
+__device__ __forceinline__ double hp_d(double x) { return x; }
+__device__ __forceinline__ double hp_d(dfl x) { return double(x.hi); }
+__device__ __forceinline__ double hp_zero(double *) { return 0.0; }
+__device__ __forceinline__ dfl hp_zero(dfl *) { return {0.0f, 0.0f}; }
+// x > y exactly (hi dominates lo)
+__device__ __forceinline__ bool hp_gt(double x, double y) { return x > y; }
+__device__ __forceinline__ bool hp_gt(dfl x, dfl y) {
+  return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo);
+}
+// shuffles
+__device__ __forceinline__ float hp_shfl_down(unsigned m, float v, int o, int w) {
+  return __shfl_down_sync(m, v, o, w);
+}
+__device__ __forceinline__ double hp_shfl_down(unsigned m, double v, int o, int w) {
+  return __shfl_down_sync(m, v, o, w);
+}
+__device__ __forceinline__ dfl hp_shfl_down(unsigned m, dfl v, int o, int w) {
+  return {__shfl_down_sync(m, v.hi, o, w), __shfl_down_sync(m, v.lo, o, w)};
+}
+
+}  // namespace dmn

@@ -19,7 +19,9 @@ struct dmn_handle_s {
   int device, num_sms;
   int blocks_per_sm[2];  // FP64, mixed
   double *d_node;        // [N][kNodeWords]
+  float *d_node_df;      // [N][kNodeDfl]
   double *d_leafw;       // [nleaf]
+  int nz;                // leaves with internal variables
   uint8_t *d_phase;      // [nleaf]
   int *d_zoff;           // [nleaf]
   double *d_mat;         // [n_mats][8]
@@ -57,6 +59,7 @@ static void free_handle(dmn_handle h) {
   if (!h) return;
   cudaFree(h->d_node);
   cudaFree(h->d_leafw);
+  cudaFree(h->d_node_df);
   cudaFree(h->d_phase);
   cudaFree(h->d_zoff);
   cudaFree(h->d_mat);
@@ -140,9 +143,25 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       r[5] = w;
       r[6] = w * r[3] * r[4];
       r[7] = 1.0 / r[6];
+      for (int c = 0; c < 3; ++c) r[8 + c] = r[c] / sqrt(2.0);
+      r[11] = 0.0;
       wn[i] = w;
     }
     wl.swap(wn);
+  }
+  // float-float node table: (hi, lo) of n, n/sqrt2, c1, c2; then 1/(w c1 c2), w c1 c2
+  std::vector<float> node_df(kNodeDfl * N, 0.0f);
+  for (int p = 0; p < N; ++p) {
+    const double *r = &node[kNodeWords * p];
+    const double v[8] = {r[0], r[1], r[2], r[8], r[9], r[10], r[3], r[4]};
+    float *o = &node_df[kNodeDfl * p];
+    for (int i = 0; i < 8; ++i) {
+      const float hi = (float)v[i];
+      o[2 * i] = hi;
+      o[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    o[16] = (float)r[7];
+    o[17] = (float)r[6];
   }
   // z offsets in a state block
   std::vector<int> zoff(nleaf);
@@ -156,6 +175,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
     }
   }
   const int zend = off;
+  const int nz = (zend - (8 + 3 * N)) / 7;
   if (off & 1) off += 1;
 
   dmn_handle h = new dmn_handle_s();
@@ -166,6 +186,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   h->SW = off;
   h->zend = zend;
   h->n_mats = n_mats;
+  h->nz = nz;
   h->opt = o;
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { free_handle(h); return cuda_fail(e, "cudaGetDevice"); }
@@ -176,11 +197,11 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   for (int mixed = 0; mixed < 2; ++mixed) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (solve_smem_bytes(K, mixed) > (size_t)smem_optin) {
+    if (solve_smem_bytes(K, nz, mixed) > (size_t)smem_optin) {
       h->blocks_per_sm[mixed] = 0;  // this precision does not fit at this depth
       continue;
     }
-    if ((e = prepare_solve(K, mixed != 0, &h->blocks_per_sm[mixed])) != cudaSuccess) {
+    if ((e = prepare_solve(K, nz, mixed != 0, &h->blocks_per_sm[mixed])) != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "prepare_solve");
     }
@@ -191,6 +212,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   }
   if ((e = cudaMalloc(&h->d_node, sizeof(double) * kNodeWords * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_leafw, sizeof(double) * nleaf)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_node_df, sizeof(float) * kNodeDfl * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess) {
@@ -199,6 +221,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   }
   if ((e = cudaMemcpy(h->d_node, node.data(), sizeof(double) * kNodeWords * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_leafw, leaf_w, sizeof(double) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_node_df, node_df.data(), sizeof(float) * kNodeDfl * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_phase, phase_map, nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_zoff, zoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * 8 * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -279,6 +302,8 @@ extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points
   P.dt = dt;
   P.node = h->d_node;
   P.leafw = h->d_leafw;
+  P.node_df = h->d_node_df;
+  P.nz = h->nz;
   P.phase = h->d_phase;
   P.zoff = h->d_zoff;
   P.mat = h->d_mat;

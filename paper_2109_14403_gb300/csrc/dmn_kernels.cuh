@@ -30,12 +30,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfl.cuh"
+
 namespace dmn {
 
 constexpr double kRsq2 = 0.70710678118654752440;
 constexpr int kMaxMats = 16;
 constexpr int kOutWords = 57;
-constexpr int kNodeWords = 8;
+constexpr int kNodeWords = 12;  // FP64 node table row
+constexpr int kNodeDfl = 20;    // float-float node table row (floats)
 
 struct MatDev {
   double kind, Kb, G, alpha, theta0, sy0, dsy, H;
@@ -44,8 +47,12 @@ struct MatDev {
 struct SolveParams {
   int K, N, G, SW;         // depth, nodes, threads per point, state words
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
+  int nz, pad2_;                   // number of leaves with internal variables
   double tol, gamma, res_floor, dt;
   const double *node;      // [N][kNodeWords]: n0 n1 n2 c1 c2 w w*c1*c2 1/(w*c1*c2)
+                           //   n0/sqrt2 n1/sqrt2 n2/sqrt2 0
+  const float *node_df;    // [N][kNodeDfl]: (hi, lo) of n0 n1 n2 n0/sqrt2 n1/sqrt2
+                           //   n2/sqrt2 c1 c2, then 1/(w c1 c2) and padding
   const double *leafw;     // [2^K] leaf weights
   const uint8_t *phase;    // [2^K]
   const int *zoff;         // [2^K]: offset of the leaf's z in a state block, -1 none
@@ -98,93 +105,141 @@ struct Rec {
 constexpr int kRecWords = 40;  // exchange slot in doubles
 
 // ------------------------------------------------------------------ phase laws
-// Leaf update at strain eps (FP64) and temperature theta (Sec. 4).  Stress,
-// coupling term D and dissipation X in FP64; derivatives into the TF record.
-// zn = internal variables at t^n (J2 only), trn = trace of the leaf strain at
-// t^n.  The yield test compares squares, so elastic leaves take no square root.
-template <typename TF>
-__device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], double theta,
-                                          const double *zn, double trn, double dt, double sig[6],
-                                          double &D, double &X, Rec<TF> &R, double znew[7]) {
-  const double Kb = m.Kb, G = m.G;
+// Constants of one material at the current point (temperature theta, time
+// increment dt), high-precision type HP where they enter the stress, TF where
+// they enter only derivatives.
+template <typename TF, typename HP>
+struct MatPt {
+  HP ath;        // alpha (theta - theta0)
+  HP Kb, G2;     // bulk modulus, 2G
+  HP a3Kth_idt;  // 3 K alpha theta / dt
+  HP sy, syidt;  // sigma_Y(theta) (floored at 1e-6), sigma_Y / dt
+  HP H, G3, iden, third, c15, one;  // H, 3G, 1/(3G+H), 1/3, 3/2, 1
+  TF a3K_f, a3K_idt_f, dsy_f, G2_f, G3_f, Kb_f, iden_f, sy_f, idt_f;
+  int j2;
+};
+
+template <typename TF, typename HP>
+__device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, const MatDev &m, double theta,
+                                          double dt) {
+  HP *tag = nullptr;
   const double dth = theta - m.theta0;
-  const double ath = m.alpha * dth;
-  const bool j2 = m.kind > 0.5;
-  double ee[6];
+  double sy = m.sy0 + m.dsy * dth, dsy = m.dsy;
+  if (sy < 1e-6) { sy = 1e-6; dsy = 0.0; }
+  const double a3K = 3.0 * m.Kb * m.alpha;
+  const double den = 3.0 * m.G + m.H;
+  o.ath = hp_from(m.alpha * dth, tag);
+  o.Kb = hp_from(m.Kb, tag);
+  o.G2 = hp_from(2.0 * m.G, tag);
+  o.a3Kth_idt = hp_from(a3K * theta / dt, tag);
+  o.sy = hp_from(sy, tag);
+  o.syidt = hp_from(sy / dt, tag);
+  o.H = hp_from(m.H, tag);
+  o.G3 = hp_from(3.0 * m.G, tag);
+  o.iden = hp_from(1.0 / den, tag);
+  o.third = hp_from(1.0 / 3.0, tag);
+  o.c15 = hp_from(1.5, tag);
+  o.one = hp_from(1.0, tag);
+  o.a3K_f = TF(a3K);
+  o.a3K_idt_f = TF(a3K / dt);
+  o.dsy_f = TF(dsy);
+  o.G2_f = TF(2.0 * m.G);
+  o.G3_f = TF(3.0 * m.G);
+  o.Kb_f = TF(m.Kb);
+  o.iden_f = TF(1.0 / den);
+  o.sy_f = TF(sy);
+  o.idt_f = TF(1.0 / dt);
+  o.j2 = m.kind > 0.5;
+}
+
+// Leaf update at strain eps and the point's temperature (Sec. 4).  Stress,
+// coupling term D and dissipation X in HP; derivatives into the TF record.
+// zn = internal variables at t^n (J2 only; eps_p Mandel 6, p), trn = trace of
+// the leaf strain at t^n.  J2 radial return with linear hardening, written as
+// sigma = K tr(ee) I + th1 s_tr, d eps_p = (3/2)(dp/q_tr) s_tr, th1 = 1 - 3G dp/q_tr;
+// the yield test compares squares, so elastic leaves take no square root.
+template <typename TF, typename HP>
+__device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6], const HP *zn,
+                                          HP trn, HP sig[6], HP &D, HP &X, Rec<TF> &R, HP *znew) {
+  const bool j2 = m.j2;
+  HP ee[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) ee[c] = eps[c] - (c < 3 ? ath : 0.0) - (j2 ? zn[c] : 0.0);
-  const double tr3 = (ee[0] + ee[1] + ee[2]) * (1.0 / 3.0);
-  const double G2 = 2.0 * G;
-  double s[6];
+  for (int c = 0; c < 6; ++c) {
+    ee[c] = c < 3 ? eps[c] - m.ath : eps[c];
+    if (j2) ee[c] = ee[c] - zn[c];
+  }
+  const HP tr = ee[0] + ee[1] + ee[2];
+  const HP tr3 = tr * m.third;
+  HP s[6];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s[c] = G2 * (c < 3 ? ee[c] - tr3 : ee[c]);
-  const double p3 = 3.0 * Kb * tr3;
-#pragma unroll
-  for (int c = 0; c < 6; ++c) sig[c] = (c < 3 ? p3 + s[c] : s[c]);
-  const double treps = eps[0] + eps[1] + eps[2];
-  const double a3K = 3.0 * Kb * m.alpha;
-  const double idt = 1.0 / dt;
-  D = -a3K * theta * (treps - trn) * idt;
-  X = 0.0;
-  double gg = -a3K * (treps - trn) * idt;
-  double th1 = 1.0, thb = 0.0, kd = 0.0, ktau = 0.0;
-  double N[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < 6; ++c) s[c] = m.G2 * (c < 3 ? ee[c] - tr3 : ee[c]);
+  const HP pk = m.Kb * tr;
+  const HP treps = eps[0] + eps[1] + eps[2];
+  const HP dtr = treps - trn;
+  D = -(m.a3Kth_idt * dtr);
+  X = hp_zero((HP *)nullptr);
+  TF gg = -m.a3K_idt_f * tf_of(dtr, (TF *)nullptr);
+  TF th1 = TF(1), thb = TF(0), kd = TF(0), ktau = TF(0);
+  TF Nf[6] = {TF(0), TF(0), TF(0), TF(0), TF(0), TF(0)};
+  bool plastic = false;
   if (j2) {
+    HP sn2 = s[0] * s[0];
 #pragma unroll
-    for (int c = 0; c < 7; ++c) znew[c] = zn[c];
-    double sy = m.sy0 + m.dsy * dth, dsy = m.dsy;
-    if (sy < 1e-6) { sy = 1e-6; dsy = 0.0; }
-    double sn2 = 0.0;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sn2 += s[c] * s[c];
-    const double yr = sy + m.H * zn[6];
-    if (1.5 * sn2 > yr * yr) {
-      const double sn = sqrt(sn2);
-      const double qtr = 1.2247448713915890491 * sn;
-      const double den = 3.0 * G + m.H;
-      const double dp = (qtr - yr) / den;
-      const double isn = 1.0 / sn;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) N[c] = s[c] * isn;
-      const double kr = G2 * 1.2247448713915890491 * dp;
+    for (int c = 1; c < 6; ++c) sn2 = sn2 + s[c] * s[c];
+    const HP yr = m.sy + m.H * zn[6];
+    const HP q2 = m.c15 * sn2;
+    plastic = hp_gt(q2, yr * yr);
+    if (plastic) {
+      const HP q = hp_sqrt(q2);                // q_tr = sqrt(3/2) |s_tr|
+      const HP dp = (q - yr) * m.iden;         // closed-form plastic multiplier
+      const HP kap = hp_div(dp, q);            // dp / q_tr
+      const HP th1h = m.one - m.G3 * kap;
+      const HP kz = m.c15 * kap;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        sig[c] -= kr * N[c];
-        znew[c] = zn[c] + 1.2247448713915890491 * dp * N[c];
+        sig[c] = c < 3 ? pk + th1h * s[c] : th1h * s[c];
+        znew[c] = zn[c] + kz * s[c];
       }
       znew[6] = zn[6] + dp;
-      const double g3 = 3.0 * G * dp / qtr;
-      th1 = 1.0 - g3;
-      thb = 3.0 * G / den - g3;
-      const double ddp_dth = -dsy / den;
-      ktau = -G2 * 1.2247448713915890491 * ddp_dth;
-      kd = sy * 1.2247448713915890491 * G2 / den * idt;
-      D += sy * dp * idt;
-      X = sy * dp * idt;
-      gg += (dsy * dp + sy * ddp_dth) * idt;
+      const HP dis = m.syidt * dp;
+      D = D + dis;
+      X = dis;
+      const TF kapf = tf_of(kap, (TF *)nullptr), dpf = tf_of(dp, (TF *)nullptr);
+      th1 = TF(1) - m.G3_f * kapf;
+      thb = m.G3_f * m.iden_f - m.G3_f * kapf;
+      const TF isn = TF(1) / sqrt(tf_of(sn2, (TF *)nullptr));
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Nf[c] = tf_of(s[c], (TF *)nullptr) * isn;
+      ktau = m.G2_f * TF(1.2247448713915890491) * m.dsy_f * m.iden_f;
+      kd = m.sy_f * TF(1.2247448713915890491) * m.G2_f * m.iden_f * m.idt_f;
+      gg += (m.dsy_f * dpf - m.sy_f * m.dsy_f * m.iden_f) * m.idt_f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) znew[c] = zn[c];
     }
   }
-  // tangent C = 3K P1 + 2G th1 P2 - 2G thb N (x) N
-  const TF cP1 = TF(Kb - G2 * th1 / 3.0);  // coefficient of m m^T
-  const TF cI = TF(G2 * th1);
-  const TF cN = TF(G2 * thb);
-  TF Nf[6];
+  if (!plastic) {
 #pragma unroll
-  for (int c = 0; c < 6; ++c) Nf[c] = TF(N[c]);
+    for (int c = 0; c < 6; ++c) sig[c] = c < 3 ? pk + s[c] : s[c];
+  }
+  // tangent C = 3K P1 + 2G th1 P2 - 2G thb N (x) N
+  const TF cP1 = m.Kb_f - m.G2_f * th1 / TF(3);  // coefficient of m m^T
+  const TF cI = m.G2_f * th1;
+  const TF cN = m.G2_f * thb;
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = i; j < 6; ++j)
       R.C[sidx(i, j)] = (i < 3 && j < 3 ? cP1 : TF(0)) + (i == j ? cI : TF(0)) - cN * Nf[i] * Nf[j];
-  const TF ta = TF(-a3K), tn = TF(ktau);
-  const TF da_ = TF(-a3K * theta * idt), dn = TF(kd);
+  const TF ta = -m.a3K_f;
+  const TF da_ = -tf_of(m.a3Kth_idt, (TF *)nullptr);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    R.tau[c] = (c < 3 ? ta : TF(0)) + tn * Nf[c];
-    R.dd[c] = (c < 3 ? da_ : TF(0)) + dn * Nf[c];
+    R.tau[c] = (c < 3 ? ta : TF(0)) + ktau * Nf[c];
+    R.dd[c] = (c < 3 ? da_ : TF(0)) + kd * Nf[c];
     R.ds[c] = TF(0);
   }
-  R.gg = TF(gg);
+  R.gg = gg;
 }
 
 // ------------------------------------------------------------------ condensation
@@ -193,10 +248,8 @@ __device__ __forceinline__ void leaf_eval(const MatDev &m, const double eps[6], 
 // (formed in FP64 by the caller).  Writes G_p (3x6) and h_p (3) for the
 // back-substitution.
 template <typename TF>
-__device__ __forceinline__ void combine(Rec<TF> &L, const Rec<TF> &R, const double *nodep,
+__device__ __forceinline__ void combine(Rec<TF> &L, const Rec<TF> &R, const TF n[3], TF c1, TF c2,
                                         const TF rbv[3], TF *gh) {
-  const TF n[3] = {TF(nodep[0]), TF(nodep[1]), TF(nodep[2])};
-  const TF c1 = TF(nodep[3]), c2 = TF(nodep[4]);
   const TF cc = c1 * c2;
   // M = c2 C_L + c1 C_R, dC = C_L - C_R (dC in place of L.C)
   TF M[21];

@@ -19,6 +19,79 @@ __device__ __forceinline__ unsigned group_mask(int G) {
 // shuffle segment width: a point with fewer than 32 threads is one segment
 __device__ __forceinline__ int group_width(int G) { return G >= 32 ? 32 : G; }
 
+// ------------------------------------------------------------------ node constants
+template <typename HP>
+struct NodeHP {
+  HP n[3], ns[3], c1, c2;  // normal, normal / sqrt2, volume fractions
+};
+__device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<double> &o) {
+  const double *r = P.node + kNodeWords * p;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    o.n[i] = __ldg(r + i);
+    o.ns[i] = __ldg(r + 8 + i);
+  }
+  o.c1 = __ldg(r + 3);
+  o.c2 = __ldg(r + 4);
+}
+__device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<dfl> &o) {
+  const float4 *r = reinterpret_cast<const float4 *>(P.node_df + kNodeDfl * p);
+  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+  o.n[0] = {a.x, a.y};
+  o.n[1] = {a.z, a.w};
+  o.n[2] = {b.x, b.y};
+  o.ns[0] = {b.z, b.w};
+  o.ns[1] = {c.x, c.y};
+  o.ns[2] = {c.z, c.w};
+  o.c1 = {d.x, d.y};
+  o.c2 = {d.z, d.w};
+}
+// normal, c1, c2, 1/(w c1 c2), w c1 c2 in the condensation precision
+__device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, double n[3], double &c1,
+                                             double &c2, double &iwcc, double &wcc) {
+  const double *r = P.node + kNodeWords * p;
+  n[0] = __ldg(r);
+  n[1] = __ldg(r + 1);
+  n[2] = __ldg(r + 2);
+  c1 = __ldg(r + 3);
+  c2 = __ldg(r + 4);
+  wcc = __ldg(r + 6);
+  iwcc = __ldg(r + 7);
+}
+__device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, float n[3], float &c1,
+                                             float &c2, float &iwcc, float &wcc) {
+  const float *r = P.node_df + kNodeDfl * p;
+  n[0] = __ldg(r);
+  n[1] = __ldg(r + 2);
+  n[2] = __ldg(r + 4);
+  c1 = __ldg(r + 12);
+  c2 = __ldg(r + 14);
+  iwcc = __ldg(r + 16);
+  wcc = __ldg(r + 17);
+}
+__device__ __forceinline__ double hp_add_tf(double a, double d) { return a + d; }
+__device__ __forceinline__ dfl hp_add_tf(dfl a, float d) { return a + dfl{d, 0.0f}; }
+
+// B a = sym(a (x) n) with the pre-scaled normal ns = n / sqrt2
+template <typename HP>
+__device__ __forceinline__ void bvec_hp(const NodeHP<HP> &nd, const HP a[3], HP out[6]) {
+  out[0] = a[0] * nd.n[0];
+  out[1] = a[1] * nd.n[1];
+  out[2] = a[2] * nd.n[2];
+  out[3] = a[1] * nd.ns[2] + a[2] * nd.ns[1];
+  out[4] = a[0] * nd.ns[2] + a[2] * nd.ns[0];
+  out[5] = a[0] * nd.ns[1] + a[1] * nd.ns[0];
+}
+
+// B^T s = s n (traction) in HP; the cancellation of the residual happens
+// here, so it must run in the high precision before any rounding to TF
+template <typename HP>
+__device__ __forceinline__ void btvec_hp(const NodeHP<HP> &nd, const HP s[6], HP out[3]) {
+  out[0] = s[0] * nd.n[0] + s[5] * nd.ns[1] + s[4] * nd.ns[2];
+  out[1] = s[1] * nd.n[1] + s[5] * nd.ns[0] + s[3] * nd.ns[2];
+  out[2] = s[2] * nd.n[2] + s[4] * nd.ns[0] + s[3] * nd.ns[1];
+}
+
 // Top-down back-substitution of the Newton increment (owner mapping):
 // da_p = -(G_p de_p + h_p); children de_1 = de + c2 B da, de_2 = de - c1 B da.
 template <typename TF>
@@ -47,9 +120,8 @@ __device__ __forceinline__ void back_substitute(const SolveParams &P, TF *da_s, 
 #pragma unroll
       for (int r = 0; r < 3; ++r) da_s[3 * p + r] = da[r];
       if (k < K) {
-        const double *nd = P.node + kNodeWords * p;
-        const TF n[3] = {TF(__ldg(nd)), TF(__ldg(nd + 1)), TF(__ldg(nd + 2))};
-        const TF c1 = TF(__ldg(nd + 3)), c2 = TF(__ldg(nd + 4));
+        TF n[3], c1, c2, iw, w;
+        load_node_tf(P, p, n, c1, c2, iw, w);
         TF ba[6];
         bvec(n, da, ba);
 #pragma unroll
@@ -82,61 +154,72 @@ __device__ __forceinline__ void back_substitute(const SolveParams &P, TF *da_s, 
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v, unsigned mask, int W) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v, unsigned mask, int W) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
-    if (o < W) v += __shfl_down_sync(mask, v, o, W);
+    if (o < W) v = v + hp_shfl_down(mask, v, o, W);
   return v;
 }
 
 // One Newton pass ("Residual" of Algorithm 1 plus the condensation):
-//  R1  compact top-down FP64 strain scatter: node j of level k on thread j;
-//  R2  thread t: leaves 2t, 2t+1 (FP64 stress, TF record) and laminate t;
-//  R3  per level, bottom-up: compact FP64 subtree stress sums and residual
+//  R1  compact top-down strain scatter in HP: node j of level k on thread j;
+//  R2  thread t: leaves 2t, 2t+1 (HP stress, TF record) and laminate t;
+//  R3  per level, bottom-up: compact HP subtree stress sums S and residual
 //      r_p = B^T (c2 S_L - c1 S_R), then the owner-mapped TF condensation.
+// HP = double (FP64 path) or float-float (mixed path); TF = double or float.
 // MAXT bounds the threads per CTA (2^(K-1)); the 128-thread instance (K <= 8)
 // lets the compiler use up to 255 registers per thread.
-template <typename TF, int MAXT>
+template <typename TF, typename HP, int MAXT>
 __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = P.K, N = P.N, G = P.G;
+  const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
   const int t = threadIdx.x;
   const int nslot = G >= 64 ? G / 64 : 1;
-  double *a_s = reinterpret_cast<double *>(smem_raw);  // 3N  jump vectors
-  double *es = a_s + 3 * N;                            // 6N  node strains, then subtree sums
-  double *slots = es + 6 * N;                          // nslot * kRecWords
-  double *red = slots + nslot * kRecWords;             // 96  warp partial sums
-  double *mats_s = red + 96;                           // kMaxMats * 8
-  double *eb = mats_s + kMaxMats * 8;                  // 12: eps_bar^{n+1}, deps
-  Ctrl *ctrl = reinterpret_cast<Ctrl *>(eb + 12);
-  TF *da_s = reinterpret_cast<TF *>(ctrl + 1);         // 3N  Newton increment
-  TF *gh_s = da_s + 3 * N;                             // 21N G_p, h_p
-  TF *rb_s = gh_s + 21 * N;                            // 3N  residual / (w c1 c2)
+  HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
+  // node strains (top-down) and subtree stress sums (bottom-up) of two
+  // consecutive levels: level k lives in the buffer of its parity
+  HP *esK = a_s + 3 * N;                       // 6G   levels K, K-2, ...
+  HP *esO = esK + 6 * G;                       // 3G   levels K-1, K-3, ...
+  HP *zn_s = esO + 3 * G;                      // 7 NZ internal variables at t^n
+  HP *zw_s = zn_s + 7 * NZ;                    // 7 NZ internal variables of the last pass
+  HP *eb = zw_s + 7 * NZ;                      // 12: eps_bar^{n+1}, deps
+  HP *redD = eb + 12;                          // 32
+  HP *redX = redD + 32;                        // 32
+  double *red = reinterpret_cast<double *>(redX + 32);  // 32
+  double *slots = red + 32;                    // nslot * kRecWords
+  MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(slots + nslot * kRecWords);
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(mp_s + kMaxMats);
+  TF *da_s = reinterpret_cast<TF *>(ctrl + 1);  // 3N  Newton increment
+  TF *gh_s = da_s + 3 * N;                      // 21N G_p, h_p
+  TF *rb_s = gh_s + 21 * N;                     // 3 max(1, G/2): residual / (w c1 c2), one level
+  HP *tag = nullptr;
 
-  for (int i = t; i < P.n_mats * 8; i += G) mats_s[i] = P.mat[i];
   const unsigned mask = group_mask(G);
   const int W = group_width(G);
   const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
+  auto lev = [&](int k) { return ((k ^ K) & 1) ? esO : esK; };  // buffer of level k
+  HP *const es1 = lev(1);  // root: strain, then sigma_bar
 
   // per-thread constants: laminate t and its leaves 2t, 2t+1
-  const double *nb = P.node + kNodeWords * t;
-  const double nbv[3] = {__ldg(nb), __ldg(nb + 1), __ldg(nb + 2)};
-  const double c1b = __ldg(nb + 3), c2b = __ldg(nb + 4);
-  const TF iwccb = TF(__ldg(nb + 7));
-  const double wL = __ldg(P.leafw + 2 * t), wR = __ldg(P.leafw + 2 * t + 1);
-  const int j0 = 2 * t, j1 = 2 * t + 1;
-  const int zo0 = P.zoff[j0], zo1 = P.zoff[j1];
-  const int ph0 = P.phase[j0], ph1 = P.phase[j1];
+  const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
+  const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
+  const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
+  const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
   for (int64_t pt = blockIdx.x; pt < P.n_points; pt += gridDim.x) {
     const double *sin = P.sin + pt * P.SW;
     double *sout = P.sout + pt * P.SW;
-    for (int i = t; i < 3 * N; i += G) a_s[i] = sin[8 + i];
+    const double theta = P.theta[pt];
+    for (int i = t; i < 3 * N; i += G) a_s[i] = hp_from(sin[8 + i], tag);
+    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_from(sin[8 + 3 * N + i], tag);
     for (int c = t; c < 6; c += G) {  // a point may have fewer than 6 threads
       const double d = P.deps[pt * 6 + c];
-      eb[c] = sin[c] + d;
-      eb[6 + c] = d;
+      eb[c] = hp_from(sin[c] + d, tag);
+      eb[6 + c] = hp_from(d, tag);
     }
+    for (int i = t; i < P.n_mats; i += G)
+      mat_point<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i), theta, P.dt);
     if (t == 0) {
       ctrl->first = 1;
       ctrl->it = 0;
@@ -145,98 +228,106 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
       ctrl->res_old = 0.0;
       ctrl->status = 0;
     }
-    const double theta = P.theta[pt];
     __syncthreads();
-    const MatDev &m0 = *reinterpret_cast<const MatDev *>(mats_s + 8 * ph0);
-    const MatDev &m1 = *reinterpret_cast<const MatDev *>(mats_s + 8 * ph1);
-    const double *zn0 = zo0 >= 0 ? sin + zo0 : nullptr;
-    const double *zn1 = zo1 >= 0 ? sin + zo1 : nullptr;
+    const HP *zn0 = zq0 >= 0 ? zn_s + zq0 : nullptr;
+    const HP *zn1 = zq1 >= 0 ? zn_s + zq1 : nullptr;
+    HP *zw0 = zq0 >= 0 ? zw_s + zq0 : nullptr;
+    HP *zw1 = zq1 >= 0 ? zw_s + zq1 : nullptr;
 
-    double trn0 = 0.0, trn1 = 0.0;
+    HP trn0 = hp_zero(tag), trn1 = hp_zero(tag);
     bool first = true;
-    double znew0[7] = {0, 0, 0, 0, 0, 0, 0}, znew1[7] = {0, 0, 0, 0, 0, 0, 0};
-    double Dsum = 0.0, Xsum = 0.0;
+    HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
     Rec<TF> rec;
     for (;;) {
       // ---- R1: strains, top-down (eq. DMN kinematics) ----
-      for (int c = t; c < 6; c += G) es[6 * (N - 1) + c] = eb[c];
+      for (int c = t; c < 6; c += G) es1[c] = eb[c];
       __syncthreads();
       for (int k = 1; k <= K - 1; ++k) {
         if (t < (1 << (k - 1))) {
           const int p = (1 << K) - (1 << k) + t;
-          const int ch = (1 << K) - (1 << (k + 1)) + 2 * t;
-          const double *nd = P.node + kNodeWords * p;
-          const double n[3] = {__ldg(nd), __ldg(nd + 1), __ldg(nd + 2)};
-          const double c1 = __ldg(nd + 3), c2 = __ldg(nd + 4);
-          const double av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
-          double J[6];
-          bvec(n, av, J);
+          HP *ep = lev(k) + 6 * t, *ec = lev(k + 1) + 12 * t;
+          NodeHP<HP> nd;
+          load_node(P, p, nd);
+          const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
+          HP J[6];
+          bvec_hp(nd, av, J);
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
-            const double e = es[6 * p + c];
-            es[6 * ch + c] = e + c2 * J[c];
-            es[6 * ch + 6 + c] = e - c1 * J[c];
+            const HP e = ep[c];
+            ec[c] = e + nd.c2 * J[c];
+            ec[6 + c] = e - nd.c1 * J[c];
           }
         }
         __syncthreads();
       }
       // ---- R2: leaves and laminate t ----
-      double r2;
+      TF r2;
       {
-        double e[6], J[6], el[6], er[6];
+        NodeHP<HP> nd;
+        load_node(P, t, nd);
+        HP el[6], er[6];
+        {
+          const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
+          HP J[6];
+          bvec_hp(nd, av, J);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = es[6 * t + c];
-        const double av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
-        bvec(nbv, av, J);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          el[c] = e[c] + c2b * J[c];
-          er[c] = e[c] - c1b * J[c];
+          for (int c = 0; c < 6; ++c) {
+            const HP e = esK[6 * t + c];
+            el[c] = e + nd.c2 * J[c];
+            er[c] = e - nd.c1 * J[c];
+          }
         }
         if (first) {  // at a = a^n: eps^n = eps - deps
-          const double trd = eb[6] + eb[7] + eb[8];
+          const HP trd = eb[6] + eb[7] + eb[8];
           trn0 = (el[0] + el[1] + el[2]) - trd;
           trn1 = (er[0] + er[1] + er[2]) - trd;
         }
-        double sl[6], sr[6], DL, DR, XL, XR;
+        HP sl[6], sr[6], DL, DR, XL, XR;
         Rec<TF> rr;
-        leaf_eval<TF>(m0, el, theta, zn0, trn0, P.dt, sl, DL, XL, rec, znew0);
-        leaf_eval<TF>(m1, er, theta, zn1, trn1, P.dt, sr, DR, XR, rr, znew1);
+        leaf_eval<TF, HP>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+        leaf_eval<TF, HP>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
         Dsum = wL * DL + wR * DR;
         Xsum = wL * XL + wR * XR;
-        double d[6], rv[3];
+        HP dsh[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-          const double SL = wL * sl[c], SR = wR * sr[c];
-          es[6 * t + c] = SL + SR;
-          d[c] = c2b * SL - c1b * SR;
+          esK[6 * t + c] = wL * sl[c] + wR * sr[c];
+          dsh[c] = sl[c] - sr[c];
         }
-        btvec(nbv, d, rv);
-        r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-        const TF rbv[3] = {TF(rv[0]) * iwccb, TF(rv[1]) * iwccb, TF(rv[2]) * iwccb};
-        combine<TF>(rec, rr, nb, rbv, gh_s + 21 * t);
+        HP rbh[3];
+        btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_t / (w c1 c2)
+        TF n[3], c1, c2, iwcc, wcc;
+        load_node_tf(P, t, n, c1, c2, iwcc, wcc);
+        const TF rbv[3] = {tf_of(rbh[0], (TF *)nullptr), tf_of(rbh[1], (TF *)nullptr),
+                           tf_of(rbh[2], (TF *)nullptr)};
+        r2 = wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
+        combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t);
       }
       // ---- R3: bottom-up ----
       for (int k = K - 1; k >= 1; --k) {
         __syncthreads();
         if (t < (1 << (k - 1))) {
           const int p = (1 << K) - (1 << k) + t;
-          const int ch = (1 << K) - (1 << (k + 1)) + 2 * t;
-          const double *nd = P.node + kNodeWords * p;
-          const double n[3] = {__ldg(nd), __ldg(nd + 1), __ldg(nd + 2)};
-          const double c1 = __ldg(nd + 3), c2 = __ldg(nd + 4);
-          const TF iwcc = TF(__ldg(nd + 7));
-          double d[6], rv[3];
+          HP *sp = lev(k) + 6 * t;
+          const HP *sc = lev(k + 1) + 12 * t;
+          NodeHP<HP> nd;
+          load_node(P, p, nd);
+          HP dh[6];
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
-            const double SL = es[6 * ch + c], SR = es[6 * ch + 6 + c];
-            es[6 * p + c] = SL + SR;
-            d[c] = c2 * SL - c1 * SR;
+            const HP SL = sc[c], SR = sc[6 + c];
+            sp[c] = SL + SR;
+            dh[c] = nd.c2 * SL - nd.c1 * SR;
           }
-          btvec(n, d, rv);
+          HP rh[3];
+          btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
+          TF n_[3], c1_, c2_, iwcc, wcc_;
+          load_node_tf(P, p, n_, c1_, c2_, iwcc, wcc_);
+          const TF rv[3] = {tf_of(rh[0], (TF *)nullptr), tf_of(rh[1], (TF *)nullptr),
+                            tf_of(rh[2], (TF *)nullptr)};
           r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
 #pragma unroll
-          for (int e = 0; e < 3; ++e) rb_s[3 * p + e] = TF(rv[e]) * iwcc;
+          for (int e = 0; e < 3; ++e) rb_s[3 * t + e] = rv[e] * iwcc;
         }
         __syncthreads();
         const int span = 1 << (K - k);
@@ -253,17 +344,20 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
         }
         if (owner) {
           const int p = (1 << K) - (1 << k) + (t >> (K - k));
-          const TF rbv[3] = {rb_s[3 * p], rb_s[3 * p + 1], rb_s[3 * p + 2]};
-          combine<TF>(rec, other, P.node + kNodeWords * p, rbv, gh_s + 21 * p);
+          TF n[3], c1, c2, iwcc, wcc;
+          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+          const int i = t >> (K - k);  // position of node p in its level
+          const TF rbv[3] = {rb_s[3 * i], rb_s[3 * i + 1], rb_s[3 * i + 2]};
+          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
         }
       }
       // ---- residual norm, decision (Algorithm 1) ----
       r2 = warp_sum(r2, mask, W);
-      const double ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
+      const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
       if (lane == 0) {
-        red[warp] = r2;
-        red[32 + warp] = ds_;
-        red[64 + warp] = xs_;
+        red[warp] = double(r2);
+        redD[warp] = ds_;
+        redX[warp] = xs_;
       }
       __syncthreads();
       if (t == 0) {
@@ -271,7 +365,10 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
         for (int w = 0; w < nwarp; ++w) s += red[w];
         double sn = 0.0;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sn += es[6 * (N - 1) + c] * es[6 * (N - 1) + c];
+        for (int c = 0; c < 6; ++c) {
+          const double v = hp_d(es1[c]);
+          sn += v * v;
+        }
         double den = sqrt(sn);
         if (den < P.res_floor) den = P.res_floor;
         const double res = sqrt(s) / (double(N) * den);
@@ -309,10 +406,10 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
       if (action == ACT_STEP) {
         back_substitute<TF>(P, da_s, gh_s, slots, t);
         __syncthreads();
-        for (int i = t; i < 3 * N; i += G) a_s[i] += double(da_s[i]);
+        for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], da_s[i]);
       } else {
-        const double f = ctrl->gi * (1.0 - P.gamma);
-        for (int i = t; i < 3 * N; i += G) a_s[i] -= f * double(da_s[i]);
+        const TF f = TF(ctrl->gi * (1.0 - P.gamma));
+        for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
       }
       __syncthreads();
       if (t == 0 && action == ACT_BACK) {
@@ -327,23 +424,23 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
       int st = ctrl->status;
       double v[kOutWords];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[c] = es[6 * (N - 1) + c];
+      for (int c = 0; c < 6; ++c) v[c] = hp_to(es1[c]);
 #pragma unroll
       for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < 6; ++j) v[6 + 6 * i + j] = double(sget(rec.C, i, j));
 #pragma unroll
       for (int c = 0; c < 6; ++c) v[42 + c] = double(rec.tau[c]);
-      double Db = 0.0, Xb = 0.0;
-      for (int w = 0; w < nwarp; ++w) {
-        Db += red[32 + w];
-        Xb += red[64 + w];
+      HP Db = redD[0], Xb = redX[0];
+      for (int w = 1; w < nwarp; ++w) {
+        Db = Db + redD[w];
+        Xb = Xb + redX[w];
       }
-      v[48] = Db;
+      v[48] = hp_to(Db);
 #pragma unroll
       for (int c = 0; c < 6; ++c) v[49 + c] = double(rec.dd[c]);
       v[55] = double(rec.gg);
-      v[56] = Xb;
+      v[56] = hp_to(Xb);
       for (int c = 0; c < kOutWords; ++c) {
         if (!isfinite(v[c])) st = 2;
         o[c] = v[c];
@@ -351,53 +448,52 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
       P.status[pt] = st;
       P.iters[pt] = ctrl->it;
     }
-    for (int c = t; c < 8; c += G) sout[c] = c < 6 ? eb[c] : (c == 6 ? theta : 0.0);
-    for (int i = t; i < 3 * N; i += G) sout[8 + i] = a_s[i];
-    if (zo0 >= 0) {
-#pragma unroll
-      for (int c = 0; c < 7; ++c) sout[zo0 + c] = znew0[c];
-    }
-    if (zo1 >= 0) {
-#pragma unroll
-      for (int c = 0; c < 7; ++c) sout[zo1 + c] = znew1[c];
-    }
+    for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
+      sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);
+    for (int i = t; i < 3 * N; i += G) sout[8 + i] = hp_to(a_s[i]);
+    for (int i = t; i < 7 * NZ; i += G) sout[8 + 3 * N + i] = hp_to(zw_s[i]);
     for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
     __syncthreads();
   }
 }
 
-size_t solve_smem_bytes(int K, bool mixed) {
+size_t solve_smem_bytes(int K, int nz, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const int nslot = G >= 64 ? G / 64 : 1;
-  size_t b = sizeof(double) * (9 * N + nslot * kRecWords + 96 + kMaxMats * 8 + 12) + sizeof(Ctrl);
-  b += (mixed ? sizeof(float) : sizeof(double)) * (27 * N);
+  const size_t hp = 8;  // double or float-float
+  size_t b = hp * (3 * N + 9 * G + 14 * nz + 12 + 64) + sizeof(double) * (32 + nslot * kRecWords);
+  b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * kMaxMats;
+  b += sizeof(Ctrl);
+  b += (mixed ? sizeof(float) : sizeof(double)) * (24 * N + 3 * (G >= 2 ? G / 2 : 1));
   return (b + 15) & ~size_t(15);
 }
 
-template <typename TF, int MAXT>
-static cudaError_t prepare_t(int K, int *blocks_per_sm) {
-  const size_t smem = solve_smem_bytes(K, sizeof(TF) == 4);
-  cudaError_t e = cudaFuncSetAttribute(dmn_solve_kernel<TF, MAXT>,
+template <typename TF, typename HP, int MAXT>
+static cudaError_t prepare_t(int K, int nz, int *blocks_per_sm) {
+  const size_t smem = solve_smem_bytes(K, nz, sizeof(TF) == 4);
+  cudaError_t e = cudaFuncSetAttribute(dmn_solve_kernel<TF, HP, MAXT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, dmn_solve_kernel<TF, MAXT>,
-                                                       1 << (K - 1), smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, dmn_solve_kernel<TF, HP, MAXT>, 1 << (K - 1), smem);
 }
 
-cudaError_t prepare_solve(int K, bool mixed, int *blocks_per_sm) {
+cudaError_t prepare_solve(int K, int nz, bool mixed, int *blocks_per_sm) {
   if (K <= 8)
-    return mixed ? prepare_t<float, 128>(K, blocks_per_sm) : prepare_t<double, 128>(K, blocks_per_sm);
-  return mixed ? prepare_t<float, 512>(K, blocks_per_sm) : prepare_t<double, 512>(K, blocks_per_sm);
+    return mixed ? prepare_t<float, dfl, 128>(K, nz, blocks_per_sm)
+                 : prepare_t<double, double, 128>(K, nz, blocks_per_sm);
+  return mixed ? prepare_t<float, dfl, 512>(K, nz, blocks_per_sm)
+               : prepare_t<double, double, 512>(K, nz, blocks_per_sm);
 }
 
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int grid, cudaStream_t s) {
-  const size_t smem = solve_smem_bytes(P.K, mixed);
+  const size_t smem = solve_smem_bytes(P.K, P.nz, mixed);
   if (P.K <= 8) {
-    if (mixed) dmn_solve_kernel<float, 128><<<grid, P.G, smem, s>>>(P);
-    else dmn_solve_kernel<double, 128><<<grid, P.G, smem, s>>>(P);
+    if (mixed) dmn_solve_kernel<float, dfl, 128><<<grid, P.G, smem, s>>>(P);
+    else dmn_solve_kernel<double, double, 128><<<grid, P.G, smem, s>>>(P);
   } else {
-    if (mixed) dmn_solve_kernel<float, 512><<<grid, P.G, smem, s>>>(P);
-    else dmn_solve_kernel<double, 512><<<grid, P.G, smem, s>>>(P);
+    if (mixed) dmn_solve_kernel<float, dfl, 512><<<grid, P.G, smem, s>>>(P);
+    else dmn_solve_kernel<double, double, 512><<<grid, P.G, smem, s>>>(P);
   }
   return cudaGetLastError();
 }
