@@ -67,6 +67,23 @@ __device__ __forceinline__ dfl dfl_from(double d) {
 }
 __device__ __forceinline__ double dfl_to(dfl x) { return double(x.hi) + double(x.lo); }
 
+// The same split by integer operations only (no FP64 pipe): hi keeps the
+// leading 24 significand bits of d (truncated), lo the next 29 bits rounded
+// to a float; a final fast_two renormalises.  Zero, and magnitudes outside
+// [2^-74, 2^127), take the FP64 conversion.
+__device__ __forceinline__ dfl dfl_split(double d) {
+  const long long b = __double_as_longlong(d);
+  const int E = int((b >> 52) & 0x7ff);
+  if (E < 949 || E >= 1150) return E == 0 ? dfl{0.0f, 0.0f} : dfl_from(d);
+  const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+  const long long mant = b & ((1ll << 52) - 1);
+  const float hi = __uint_as_float(sign | (unsigned(E - 1023 + 127) << 23) | unsigned(mant >> 29));
+  const float scale = __uint_as_float(unsigned(E - 1075 + 127) << 23);  // 2^(E-1075)
+  float lo = float(int(mant & ((1ll << 29) - 1))) * scale;
+  if (sign) lo = -lo;
+  return fast_two(hi, lo);
+}
+
 __device__ __forceinline__ dfl dfl_sqrt(dfl x) {
   if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
   const float y = sqrtf(x.hi);
@@ -85,6 +102,9 @@ __device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
 // step FP64) or HP = dfl (mixed).  These overloads give both the same names.
 __device__ __forceinline__ double hp_from(double d, double *) { return d; }
 __device__ __forceinline__ dfl hp_from(double d, dfl *) { return dfl_from(d); }
+// load-path conversion (integer split for float-float)
+__device__ __forceinline__ double hp_load(double d, double *) { return d; }
+__device__ __forceinline__ dfl hp_load(double d, dfl *) { return dfl_split(d); }
 __device__ __forceinline__ double hp_to(double x) { return x; }
 __device__ __forceinline__ double hp_to(dfl x) { return dfl_to(x); }
 __device__ __forceinline__ double hp_sqrt(double x) { return sqrt(x); }

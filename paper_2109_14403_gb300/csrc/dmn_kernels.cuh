@@ -105,51 +105,66 @@ struct Rec {
 constexpr int kRecWords = 40;  // exchange slot in doubles
 
 // ------------------------------------------------------------------ phase laws
-// Constants of one material at the current point (temperature theta, time
-// increment dt), high-precision type HP where they enter the stress, TF where
-// they enter only derivatives.
+// Constants of one material.  The static part is built once per CTA (FP64 is
+// fine there); the part that depends on the point's temperature theta is
+// formed per point in the high-precision type HP, so the mixed path stays on
+// the FP32 pipe.
 template <typename TF, typename HP>
 struct MatPt {
-  HP ath;        // alpha (theta - theta0)
-  HP Kb, G2;     // bulk modulus, 2G
-  HP a3Kth_idt;  // 3 K alpha theta / dt
-  HP sy, syidt;  // sigma_Y(theta) (floored at 1e-6), sigma_Y / dt
-  HP H, G3, iden, third, c15, one;  // H, 3G, 1/(3G+H), 1/3, 3/2, 1
-  TF a3K_f, a3K_idt_f, dsy_f, G2_f, G3_f, Kb_f, iden_f, sy_f, idt_f;
+  HP Kb, G2, G3, iden, H, a3K, alpha, theta0, sy0, dsy, symin, third, c15, one;
+  TF a3K_f, G2_f, G3_f, Kb_f, iden_f, dsy0_f;
   int j2;
+  // per point
+  HP ath;        // alpha (theta - theta0)
+  HP a3Kth_idt;  // 3 K alpha theta / dt
+  HP sy, syidt;  // sigma_Y(theta) (floored at 1e-6 MPa), sigma_Y / dt
+  TF a3K_idt_f, dsy_f, sy_f, idt_f;
 };
 
 template <typename TF, typename HP>
-__device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, const MatDev &m, double theta,
-                                          double dt) {
+__device__ __forceinline__ void mat_static(MatPt<TF, HP> &o, const MatDev &m) {
   HP *tag = nullptr;
-  const double dth = theta - m.theta0;
-  double sy = m.sy0 + m.dsy * dth, dsy = m.dsy;
-  if (sy < 1e-6) { sy = 1e-6; dsy = 0.0; }
-  const double a3K = 3.0 * m.Kb * m.alpha;
   const double den = 3.0 * m.G + m.H;
-  o.ath = hp_from(m.alpha * dth, tag);
   o.Kb = hp_from(m.Kb, tag);
   o.G2 = hp_from(2.0 * m.G, tag);
-  o.a3Kth_idt = hp_from(a3K * theta / dt, tag);
-  o.sy = hp_from(sy, tag);
-  o.syidt = hp_from(sy / dt, tag);
-  o.H = hp_from(m.H, tag);
   o.G3 = hp_from(3.0 * m.G, tag);
   o.iden = hp_from(1.0 / den, tag);
+  o.H = hp_from(m.H, tag);
+  o.a3K = hp_from(3.0 * m.Kb * m.alpha, tag);
+  o.alpha = hp_from(m.alpha, tag);
+  o.theta0 = hp_from(m.theta0, tag);
+  o.sy0 = hp_from(m.sy0, tag);
+  o.dsy = hp_from(m.dsy, tag);
+  o.symin = hp_from(1e-6, tag);
   o.third = hp_from(1.0 / 3.0, tag);
   o.c15 = hp_from(1.5, tag);
   o.one = hp_from(1.0, tag);
-  o.a3K_f = TF(a3K);
-  o.a3K_idt_f = TF(a3K / dt);
-  o.dsy_f = TF(dsy);
+  o.a3K_f = TF(3.0 * m.Kb * m.alpha);
   o.G2_f = TF(2.0 * m.G);
   o.G3_f = TF(3.0 * m.G);
   o.Kb_f = TF(m.Kb);
   o.iden_f = TF(1.0 / den);
-  o.sy_f = TF(sy);
-  o.idt_f = TF(1.0 / dt);
+  o.dsy0_f = TF(m.dsy);
   o.j2 = m.kind > 0.5;
+}
+
+template <typename TF, typename HP>
+__device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, HP theta, HP idt, TF idt_f) {
+  const HP dth = theta - o.theta0;
+  o.ath = o.alpha * dth;
+  o.a3Kth_idt = o.a3K * theta * idt;
+  HP sy = o.sy0 + o.dsy * dth;
+  TF dsy = o.dsy0_f;
+  if (tf_of(sy, (TF *)nullptr) < TF(1e-6)) {
+    sy = o.symin;
+    dsy = TF(0);
+  }
+  o.sy = sy;
+  o.syidt = sy * idt;
+  o.a3K_idt_f = o.a3K_f * idt_f;
+  o.dsy_f = dsy;
+  o.sy_f = tf_of(sy, (TF *)nullptr);
+  o.idt_f = idt_f;
 }
 
 // Leaf update at strain eps and the point's temperature (Sec. 4).  Stress,

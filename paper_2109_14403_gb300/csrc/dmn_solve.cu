@@ -8,9 +8,10 @@ namespace dmn {
 
 enum { ACT_STEP = 0, ACT_BACK = 1, ACT_DONE = 2 };
 
+template <typename TF>
 struct Ctrl {
-  double res, res_old, gi, r2;
-  int action, it, bt, status, first, pad_[3];
+  TF res, res_old, gi, pad0_;
+  int action, it, bt, status, first, nonfinite, pad_[2];
 };
 
 __device__ __forceinline__ unsigned group_mask(int G) {
@@ -186,11 +187,13 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   HP *eb = zw_s + 7 * NZ;                      // 12: eps_bar^{n+1}, deps
   HP *redD = eb + 12;                          // 32
   HP *redX = redD + 32;                        // 32
-  double *red = reinterpret_cast<double *>(redX + 32);  // 32
-  double *slots = red + 32;                    // nslot * kRecWords
+  HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
+  double *slots = reinterpret_cast<double *>(misc + 4);  // nslot * kRecWords
   MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(slots + nslot * kRecWords);
-  Ctrl *ctrl = reinterpret_cast<Ctrl *>(mp_s + kMaxMats);
-  TF *da_s = reinterpret_cast<TF *>(ctrl + 1);  // 3N  Newton increment
+  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(mp_s + kMaxMats);
+  TF *red = reinterpret_cast<TF *>(ctrl + 1);   // 32  warp partial sums of |r|^2
+  TF *orec = red + 32;                          // 40  root record for the outputs
+  TF *da_s = orec + 40;                         // 3N  Newton increment
   TF *gh_s = da_s + 3 * N;                      // 21N G_p, h_p
   TF *rb_s = gh_s + 21 * N;                     // 3 max(1, G/2): residual / (w c1 c2), one level
   HP *tag = nullptr;
@@ -200,6 +203,12 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
   auto lev = [&](int k) { return ((k ^ K) & 1) ? esO : esK; };  // buffer of level k
   HP *const es1 = lev(1);  // root: strain, then sigma_bar
+
+  for (int i = t; i < P.n_mats; i += G)
+    mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
+  if (t == 0) misc[0] = hp_from(1.0 / P.dt, tag);
+  const TF idt_f = TF(1.0 / P.dt);
+  const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
 
   // per-thread constants: laminate t and its leaves 2t, 2t+1
   const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
@@ -211,21 +220,21 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
     const double *sin = P.sin + pt * P.SW;
     double *sout = P.sout + pt * P.SW;
     const double theta = P.theta[pt];
-    for (int i = t; i < 3 * N; i += G) a_s[i] = hp_from(sin[8 + i], tag);
-    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_from(sin[8 + 3 * N + i], tag);
+    for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
+    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_load(sin[8 + 3 * N + i], tag);
     for (int c = t; c < 6; c += G) {  // a point may have fewer than 6 threads
       const double d = P.deps[pt * 6 + c];
-      eb[c] = hp_from(sin[c] + d, tag);
-      eb[6 + c] = hp_from(d, tag);
+      eb[c] = hp_load(sin[c] + d, tag);
+      eb[6 + c] = hp_load(d, tag);
     }
-    for (int i = t; i < P.n_mats; i += G)
-      mat_point<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i), theta, P.dt);
+    __syncthreads();  // misc[0] (first point) and the static material part
+    for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
     if (t == 0) {
       ctrl->first = 1;
       ctrl->it = 0;
       ctrl->bt = 0;
-      ctrl->gi = 1.0;
-      ctrl->res_old = 0.0;
+      ctrl->gi = TF(1);
+      ctrl->res_old = TF(0);
       ctrl->status = 0;
     }
     __syncthreads();
@@ -355,31 +364,31 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
       r2 = warp_sum(r2, mask, W);
       const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
       if (lane == 0) {
-        red[warp] = double(r2);
+        red[warp] = r2;
         redD[warp] = ds_;
         redX[warp] = xs_;
       }
       __syncthreads();
-      if (t == 0) {
-        double s = 0.0;
+      if (t == 0) {  // in TF: the norm needs no more than a few digits
+        TF s = TF(0);
         for (int w = 0; w < nwarp; ++w) s += red[w];
-        double sn = 0.0;
+        TF sn = TF(0);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-          const double v = hp_d(es1[c]);
+          const TF v = tf_of(es1[c], (TF *)nullptr);
           sn += v * v;
         }
-        double den = sqrt(sn);
-        if (den < P.res_floor) den = P.res_floor;
-        const double res = sqrt(s) / (double(N) * den);
-        Ctrl &c = *ctrl;
+        TF den = sqrt(sn);
+        if (den < res_floor) den = res_floor;
+        const TF res = sqrt(s) / (TF(N) * den);
+        Ctrl<TF> &c = *ctrl;
         const bool accept = c.first || (res < c.res_old) || (c.bt >= P.maxbt);
         int action;
         if (accept) {
           if (!isfinite(res)) {
             c.status = 2;
             action = ACT_DONE;
-          } else if (!c.first && res < P.tol) {
+          } else if (!c.first && res < tol) {
             c.status = 0;
             action = ACT_DONE;
           } else if (c.it >= P.maxit) {
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
             c.res_old = res;
             c.it += 1;
             c.bt = 0;
-            c.gi = 1.0;
+            c.gi = TF(1);
             action = ACT_STEP;
           }
           c.first = 0;
@@ -408,44 +417,51 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
         __syncthreads();
         for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], da_s[i]);
       } else {
-        const TF f = TF(ctrl->gi * (1.0 - P.gamma));
+        const TF f = ctrl->gi * (TF(1) - gamma);
         for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
       }
       __syncthreads();
       if (t == 0 && action == ACT_BACK) {
-        ctrl->gi *= P.gamma;
+        ctrl->gi *= gamma;
         ctrl->bt += 1;
       }
     }
 
     // ---- outputs and state (the last pass is at the final a) ----
     if (t == 0) {
-      double *o = P.out + pt * kOutWords;
-      int st = ctrl->status;
-      double v[kOutWords];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[c] = hp_to(es1[c]);
+      for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) v[6 + 6 * i + j] = double(sget(rec.C, i, j));
-#pragma unroll
-      for (int c = 0; c < 6; ++c) v[42 + c] = double(rec.tau[c]);
+      for (int c = 0; c < 6; ++c) {
+        orec[21 + c] = rec.tau[c];
+        orec[27 + c] = rec.dd[c];
+      }
+      orec[33] = rec.gg;
       HP Db = redD[0], Xb = redX[0];
       for (int w = 1; w < nwarp; ++w) {
         Db = Db + redD[w];
         Xb = Xb + redX[w];
       }
-      v[48] = hp_to(Db);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) v[49 + c] = double(rec.dd[c]);
-      v[55] = double(rec.gg);
-      v[56] = hp_to(Xb);
-      for (int c = 0; c < kOutWords; ++c) {
-        if (!isfinite(v[c])) st = 2;
-        o[c] = v[c];
-      }
-      P.status[pt] = st;
+      misc[1] = Db;
+      misc[2] = Xb;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int c = t; c < kOutWords; c += G) {  // one output word per thread
+      double v;
+      if (c < 6) v = hp_to(es1[c]);
+      else if (c < 42) v = double(sget(orec, (c - 6) / 6, (c - 6) % 6));
+      else if (c < 48) v = double(orec[21 + c - 42]);
+      else if (c == 48) v = hp_to(misc[1]);
+      else if (c < 55) v = double(orec[27 + c - 49]);
+      else if (c == 55) v = double(orec[33]);
+      else v = hp_to(misc[2]);
+      if (!isfinite(v)) bad = 1;
+      P.out[pt * kOutWords + c] = v;
+    }
+    bad = __syncthreads_or(bad);
+    if (t == 0) {
+      P.status[pt] = bad ? 2 : ctrl->status;
       P.iters[pt] = ctrl->it;
     }
     for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
@@ -461,10 +477,10 @@ size_t solve_smem_bytes(int K, int nz, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const int nslot = G >= 64 ? G / 64 : 1;
   const size_t hp = 8;  // double or float-float
-  size_t b = hp * (3 * N + 9 * G + 14 * nz + 12 + 64) + sizeof(double) * (32 + nslot * kRecWords);
+  size_t b = hp * (3 * N + 9 * G + 14 * nz + 12 + 64 + 4) + sizeof(double) * (nslot * kRecWords);
   b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * kMaxMats;
-  b += sizeof(Ctrl);
-  b += (mixed ? sizeof(float) : sizeof(double)) * (24 * N + 3 * (G >= 2 ? G / 2 : 1));
+  b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
+  b += (mixed ? sizeof(float) : sizeof(double)) * (32 + 40 + 24 * N + 3 * (G >= 2 ? G / 2 : 1));
   return (b + 15) & ~size_t(15);
 }
 
