@@ -27,7 +27,10 @@
  *     of the Algorithm 1 residual does.
  *
  * Ownership: every d_* pointer is device memory owned by the caller.  A
- * handle owns only device copies of the tree and material constants.
+ * handle owns device copies of the tree and material constants and one
+ * work-queue counter that dmn_eval resets with a stream-ordered memset before
+ * each launch: calls on one handle must therefore not run concurrently on
+ * different streams (use one handle per stream).
  * Streams: every call that takes a stream is stream-ordered and does not
  * synchronise the device.  Errors: a non-zero dmn_status; the message of the
  * last error of the calling thread is returned by dmn_last_error().
@@ -95,8 +98,12 @@ typedef struct {
                            leaf tangents, condensation and the Newton
                            correction in FP32; strains, leaf stresses, the
                            residual, the convergence test and every output
-                           accumulation in FP64                                */
-  int32_t reserved_;
+                           accumulation in FP64-class precision (float-float
+                           on the FP32 pipe, about 48 significant bits)          */
+  int32_t solve_variant; /* kernel variant of the solve (0 = library default;
+                           2, 3, 4 = mixed-precision kernel compiled for that
+                           many resident CTAs per SM at depth K <= 8); chosen
+                           by the autotuner, ignored where it does not apply  */
 } dmn_options;
 
 /* Fill *opt with the defaults listed above. */

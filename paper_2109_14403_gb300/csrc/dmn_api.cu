@@ -17,7 +17,8 @@ struct dmn_handle_s {
   int K, N, nleaf, SW, zend, n_mats;
   dmn_options opt;
   int device, num_sms;
-  int blocks_per_sm[2];  // FP64, mixed
+  int blocks_per_sm;     // resident CTAs per SM of the selected kernel variant
+  unsigned long long *d_queue;  // work-queue counter (one per handle)
   double *d_node;        // [N][kNodeWords]
   float *d_node_df;      // [N][kNodeDfl]
   double *d_leafw;       // [nleaf]
@@ -63,6 +64,7 @@ static void free_handle(dmn_handle h) {
   cudaFree(h->d_phase);
   cudaFree(h->d_zoff);
   cudaFree(h->d_mat);
+  cudaFree(h->d_queue);
   delete h;
 }
 
@@ -194,28 +196,34 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
     free_handle(h);
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
-  for (int mixed = 0; mixed < 2; ++mixed) {
+  const bool mixed = o.precision == DMN_PREC_MIXED;
+  if (o.solve_variant != 0 && (o.solve_variant < 2 || o.solve_variant > 4)) {
+    free_handle(h);
+    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4}", o.solve_variant);
+  }
+  {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (solve_smem_bytes(K, nz, mixed) > (size_t)smem_optin) {
-      h->blocks_per_sm[mixed] = 0;  // this precision does not fit at this depth
-      continue;
+    if (solve_smem_bytes(K, nz, n_mats, mixed) > (size_t)smem_optin) {
+      free_handle(h);
+      return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
     }
-    if ((e = prepare_solve(K, nz, mixed != 0, &h->blocks_per_sm[mixed])) != cudaSuccess) {
+    if ((e = prepare_solve(K, nz, n_mats, mixed, o.solve_variant, &h->blocks_per_sm)) != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "prepare_solve");
     }
-  }
-  if (h->blocks_per_sm[o.precision == DMN_PREC_MIXED] < 1) {
-    free_handle(h);
-    return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
+    if (h->blocks_per_sm < 1) {
+      free_handle(h);
+      return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
+    }
   }
   if ((e = cudaMalloc(&h->d_node, sizeof(double) * kNodeWords * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_leafw, sizeof(double) * nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_node_df, sizeof(float) * kNodeDfl * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess) {
+      (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMalloc");
   }
@@ -315,9 +323,10 @@ extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points
   P.out = d_out;
   P.status = d_status;
   P.iters = d_iters;
-  int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm[mixed];
+  P.queue = h->d_queue;
+  int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm;
   if (grid > n_points) grid = n_points;
-  cudaError_t e = launch_solve(P, mixed, (int)grid, (cudaStream_t)stream);
+  cudaError_t e = launch_solve(P, mixed, h->opt.solve_variant, (int)grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "dmn_eval launch");
   return DMN_OK;
 }

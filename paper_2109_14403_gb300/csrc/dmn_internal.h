@@ -6,7 +6,8 @@
 #include "dmn_kernels.cuh"
 
 namespace dmn {
-size_t solve_smem_bytes(int K, int nz, bool mixed);
-cudaError_t prepare_solve(int K, int nz, bool mixed, int *blocks_per_sm);
-cudaError_t launch_solve(const SolveParams &P, bool mixed, int grid, cudaStream_t s);
+size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed);
+int solve_variant_count();
+cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm);
+cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);
 }  // namespace dmn

@@ -48,6 +48,7 @@ struct SolveParams {
   int K, N, G, SW;         // depth, nodes, threads per point, state words
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
   int nz, pad2_;                   // number of leaves with internal variables
+  unsigned long long *queue;       // device counter of points taken (zeroed per launch)
   double tol, gamma, res_floor, dt;
   const double *node;      // [N][kNodeWords]: n0 n1 n2 c1 c2 w w*c1*c2 1/(w*c1*c2)
                            //   n0/sqrt2 n1/sqrt2 n2/sqrt2 0

@@ -11,6 +11,7 @@ enum { ACT_STEP = 0, ACT_BACK = 1, ACT_DONE = 2 };
 template <typename TF>
 struct Ctrl {
   TF res, res_old, gi, pad0_;
+  unsigned long long next;  // point taken from the queue
   int action, it, bt, status, first, nonfinite, pad_[2];
 };
 
@@ -169,10 +170,13 @@ __device__ __forceinline__ T warp_sum(T v, unsigned mask, int W) {
 //  R3  per level, bottom-up: compact HP subtree stress sums S and residual
 //      r_p = B^T (c2 S_L - c1 S_R), then the owner-mapped TF condensation.
 // HP = double (FP64 path) or float-float (mixed path); TF = double or float.
-// MAXT bounds the threads per CTA (2^(K-1)); the 128-thread instance (K <= 8)
-// lets the compiler use up to 255 registers per thread.
-template <typename TF, typename HP, int MAXT>
-__global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
+// MAXT bounds the threads per CTA (2^(K-1)); MINB asks the compiler to fit
+// MINB CTAs per SM (register budget 65536 / (MAXT * MINB)).  Points are taken
+// from a device-side queue (one atomic counter per launch), so a CTA whose
+// point converged moves on at once: uneven Newton iteration counts do not
+// leave CTAs idle.
+template <typename TF, typename HP, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
   const int t = threadIdx.x;
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
   double *slots = reinterpret_cast<double *>(misc + 4);  // nslot * kRecWords
   MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(slots + nslot * kRecWords);
-  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(mp_s + kMaxMats);
+  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(mp_s + P.n_mats);
   TF *red = reinterpret_cast<TF *>(ctrl + 1);   // 32  warp partial sums of |r|^2
   TF *orec = red + 32;                          // 40  root record for the outputs
   TF *da_s = orec + 40;                         // 3N  Newton increment
@@ -216,7 +220,11 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
   const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
-  for (int64_t pt = blockIdx.x; pt < P.n_points; pt += gridDim.x) {
+  for (;;) {
+    if (t == 0) ctrl->next = atomicAdd(P.queue, 1ull);
+    __syncthreads();
+    const int64_t pt = int64_t(ctrl->next);
+    if (pt >= P.n_points) break;
     const double *sin = P.sin + pt * P.SW;
     double *sout = P.sout + pt * P.SW;
     const double theta = P.theta[pt];
@@ -473,44 +481,45 @@ __global__ void __launch_bounds__(MAXT) dmn_solve_kernel(const SolveParams P) {
   }
 }
 
-size_t solve_smem_bytes(int K, int nz, bool mixed) {
+size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const int nslot = G >= 64 ? G / 64 : 1;
   const size_t hp = 8;  // double or float-float
   size_t b = hp * (3 * N + 9 * G + 14 * nz + 12 + 64 + 4) + sizeof(double) * (nslot * kRecWords);
-  b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * kMaxMats;
+  b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
+  b = (b + 15) & ~size_t(15);
   b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
   b += (mixed ? sizeof(float) : sizeof(double)) * (32 + 40 + 24 * N + 3 * (G >= 2 ? G / 2 : 1));
   return (b + 15) & ~size_t(15);
 }
 
-template <typename TF, typename HP, int MAXT>
-static cudaError_t prepare_t(int K, int nz, int *blocks_per_sm) {
-  const size_t smem = solve_smem_bytes(K, nz, sizeof(TF) == 4);
-  cudaError_t e = cudaFuncSetAttribute(dmn_solve_kernel<TF, HP, MAXT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, dmn_solve_kernel<TF, HP, MAXT>, 1 << (K - 1), smem);
-}
-
-cudaError_t prepare_solve(int K, int nz, bool mixed, int *blocks_per_sm) {
-  if (K <= 8)
-    return mixed ? prepare_t<float, dfl, 128>(K, nz, blocks_per_sm)
-                 : prepare_t<double, double, 128>(K, nz, blocks_per_sm);
-  return mixed ? prepare_t<float, dfl, 512>(K, nz, blocks_per_sm)
-               : prepare_t<double, double, 512>(K, nz, blocks_per_sm);
-}
-
-cudaError_t launch_solve(const SolveParams &P, bool mixed, int grid, cudaStream_t s) {
-  const size_t smem = solve_smem_bytes(P.K, P.nz, mixed);
-  if (P.K <= 8) {
-    if (mixed) dmn_solve_kernel<float, dfl, 128><<<grid, P.G, smem, s>>>(P);
-    else dmn_solve_kernel<double, double, 128><<<grid, P.G, smem, s>>>(P);
-  } else {
-    if (mixed) dmn_solve_kernel<float, dfl, 512><<<grid, P.G, smem, s>>>(P);
-    else dmn_solve_kernel<double, double, 512><<<grid, P.G, smem, s>>>(P);
+// kernel variants: (precision, threads bound, CTAs per SM requested)
+using KernelFn = void (*)(const SolveParams);
+static KernelFn pick(int K, bool mixed, int variant) {
+  if (K > 8) return mixed ? dmn_solve_kernel<float, dfl, 512, 1> : dmn_solve_kernel<double, double, 512, 1>;
+  if (!mixed) return dmn_solve_kernel<double, double, 128, 1>;
+  switch (variant) {
+    case 2: return dmn_solve_kernel<float, dfl, 128, 2>;
+    case 4: return dmn_solve_kernel<float, dfl, 128, 4>;
+    default: return dmn_solve_kernel<float, dfl, 128, 3>;
   }
+}
+
+int solve_variant_count() { return 3; }
+
+cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm) {
+  const size_t smem = solve_smem_bytes(K, nz, n_mats, mixed);
+  KernelFn f = pick(K, mixed, variant);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem);
+}
+
+cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s) {
+  const size_t smem = solve_smem_bytes(P.K, P.nz, P.n_mats, mixed);
+  cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  pick(P.K, mixed, variant)<<<grid, P.G, smem, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ class dmn_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("res_floor", ctypes.c_double), ("maxit", ctypes.c_int32),
                 ("maxbacktrack", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("solve_variant", ctypes.c_int32)]
 
 
 # every symbol the header declares, with its signature
@@ -110,7 +110,7 @@ class DMN:
     """A DMN handle on the current CUDA device (``dmn_create``)."""
 
     def __init__(self, K, w, normals, phase, mats, *, tol=1e-10, maxit=50, maxbacktrack=8,
-                 gamma=0.5, precision="fp64", res_floor=0.0):
+                 gamma=0.5, precision="fp64", res_floor=0.0, solve_variant=0):
         lib = load()
         self.K = int(K)
         w = np.ascontiguousarray(w, np.float64)
@@ -122,6 +122,7 @@ class DMN:
         opt.tol, opt.maxit, opt.maxbacktrack, opt.gamma = tol, maxit, maxbacktrack, gamma
         opt.res_floor = res_floor
         opt.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        opt.solve_variant = int(solve_variant)
         self.precision = precision
         h = ctypes.c_void_p()
         _check(lib.dmn_create(ctypes.byref(h), self.K, w.ctypes.data_as(_P),
