@@ -173,6 +173,35 @@ dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points, const dou
                     const double *d_theta, double dt, const double *d_state_in,
                     double *d_state_out, double *d_out, int32_t *d_status, int32_t *d_iters);
 
+/*
+ * One load increment without any device allocation (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate).
+ * Some callers may not call cudaMalloc at all -- a material routine running
+ * inside a host finite-element code whose device memory belongs to another
+ * allocator or pool, a sandboxed or real-time plug-in, or code that cannot
+ * keep a dmn_handle alive between calls.  This call needs no handle: it takes
+ * the tree and materials as dmn_create does (host memory, same rules), derives
+ * the node tables on the host every call, copies them into a fixed device
+ * array that is part of the library (64 KiB per GPU, held by every GPU that
+ * loads the library until the process exits) and then runs the same solve as
+ * dmn_eval; the caller's inputs, outputs and state are as in dmn_eval.
+ *   Limit: K <= 8; larger trees are rejected with DMN_ERR_ARG.
+ *   The first call on a device looks up the device address of that array
+ *   (with the device current); make that first call before any stream
+ *   capture.  The host-to-device copies of the tables are ordinary
+ *   stream-ordered copies from host memory.
+ *   All calls share the one array (tables and the work-queue counter, which
+ *   each launch zeroes first): calls that overlap on the GPU -- on different
+ *   streams, or from different threads -- race; order them on one stream.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const double *normals,
+                            const uint8_t *phase_map, const dmn_material *mats, int32_t n_mats,
+                            const dmn_options *opt, dmn_stream stream, int64_t n_points,
+                            const double *d_deps, const double *d_theta, double dt,
+                            const double *d_state_in, double *d_state_out, double *d_out,
+                            int32_t *d_status, int32_t *d_iters);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *dmn_last_error(void);
 

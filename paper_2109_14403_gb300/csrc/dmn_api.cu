@@ -45,6 +45,8 @@ static dmn_status cuda_fail(cudaError_t e, const char *what) {
 
 extern "C" const char *dmn_last_error(void) { return g_err; }
 
+void dmn::set_error_message(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 extern "C" void dmn_default_options(dmn_options *o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));

@@ -10,4 +10,6 @@ size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed);
 int solve_variant_count();
 cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);
+// message returned by dmn_last_error() on this thread
+void set_error_message(const char *msg);
 }  // namespace dmn

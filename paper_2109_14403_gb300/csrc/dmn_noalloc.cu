@@ -1,0 +1,272 @@
+// dmn_noalloc.cu -- dmn_eval_noalloc: one load increment without any device
+// allocation.
+//
+// Who needs it: callers that may not call cudaMalloc at all -- for example a
+// material routine invoked by a host finite-element code inside a region
+// where the device allocator must not be touched (a memory pool owned by
+// another runtime, a real-time or sandboxed plug-in), or code that cannot
+// keep a handle alive between calls.  dmn_create allocates the handle's
+// tables and its work-queue counter with cudaMalloc; this entry point takes
+// the same tree and material description from host memory on every call and
+// places everything the solve kernel needs besides the caller's inputs and
+// outputs in one file-scope device array.
+//
+// The array is a static __device__ object: every GPU that loads the library
+// holds kScratchBytes of it until the process exits.  Its host-side name is
+// only a stand-in for the device object, so the device address is looked up
+// once per device (cudaGetSymbolAddress, with that device current) and that
+// address is what the kernel receives.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/dmn.h"
+#include "dmn_internal.h"
+
+using namespace dmn;
+
+namespace {
+
+constexpr int kNoAllocMaxK = 8;                 // largest supported depth
+constexpr size_t kScratchBytes = 64 * 1024;     // 64 KiB per device
+constexpr int kMaxDevices = 64;
+
+// node tables, leaf tables, material table and the work-queue counter
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+static void *g_scratch_addr[kMaxDevices];       // device address, per device
+static bool g_scratch_ready[kMaxDevices];
+
+// errors are reported through dmn_last_error() like every other call
+dmn_status na_fail(dmn_status s, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof(msg), fmt, ap);
+  va_end(ap);
+  set_error_message(msg);
+  return s;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const double *normals,
+                                       const uint8_t *phase_map, const dmn_material *mats,
+                                       int32_t n_mats, const dmn_options *opt, dmn_stream stream,
+                                       int64_t n_points, const double *d_deps, const double *d_theta,
+                                       double dt, const double *d_state_in, double *d_state_out,
+                                       double *d_out, int32_t *d_status, int32_t *d_iters) {
+  set_error_message("");
+  if (K < 1 || K > kNoAllocMaxK)
+    return na_fail(DMN_ERR_ARG,
+                   "dmn_eval_noalloc: K=%d outside 1..%d (the static scratch array holds the "
+                   "tables of trees up to depth %d)",
+                   K, kNoAllocMaxK, kNoAllocMaxK);
+  if (!leaf_w || !normals || !phase_map || !mats)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: NULL host array argument");
+  if (n_mats < 1 || n_mats > kMaxMats)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: n_mats=%d outside 1..%d", n_mats, kMaxMats);
+  if (n_points < 0) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: n_points < 0");
+  if (n_points == 0) return DMN_OK;
+  if (!d_deps || !d_theta || !d_state_in || !d_state_out || !d_out || !d_status || !d_iters)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: NULL device pointer");
+  if (!(dt > 0.0) || !isfinite(dt)) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: dt must be > 0");
+  dmn_options o;
+  if (opt) o = *opt; else dmn_default_options(&o);
+  if (!(o.tol > 0.0) || !(o.gamma > 0.0 && o.gamma < 1.0) || o.maxit < 1 || o.maxbacktrack < 0 ||
+      (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED) ||
+      (o.solve_variant != 0 && (o.solve_variant < 2 || o.solve_variant > 4)))
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: invalid options");
+
+  const int nleaf = 1 << K, N = nleaf - 1;
+  // ---- host tables (fixed-size arrays on the stack: no heap either) ----
+  double mat[8 * kMaxMats];
+  double Emax = 0.0;
+  for (int i = 0; i < n_mats; ++i) {
+    const dmn_material &m = mats[i];
+    if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR)
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has unknown kind %d", i, m.kind);
+    if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has invalid elastic constants", i);
+    if (m.kind == DMN_MAT_J2_LINEAR &&
+        (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has invalid J2 constants", i);
+    double *r = &mat[8 * i];
+    r[0] = m.kind;
+    r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+    r[2] = m.E / (2.0 * (1.0 + m.nu));
+    r[3] = m.alpha;
+    r[4] = m.theta0;
+    r[5] = m.kind == DMN_MAT_J2_LINEAR ? m.sy0 : 0.0;
+    r[6] = m.kind == DMN_MAT_J2_LINEAR ? m.dsy_dT : 0.0;
+    r[7] = m.kind == DMN_MAT_J2_LINEAR ? m.H : 0.0;
+    if (m.E > Emax) Emax = m.E;
+  }
+  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
+  double ws = 0.0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (!(leaf_w[j] > 0.0) || !isfinite(leaf_w[j]))
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: leaf weight %d is not positive", j);
+    if (phase_map[j] >= n_mats)
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: phase_map[%d]=%d >= n_mats", j, phase_map[j]);
+    ws += leaf_w[j];
+  }
+  if (fabs(ws - 1.0) > 1e-12)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: weights sum to %.17g", ws);
+
+  constexpr int NMAX = (1 << kNoAllocMaxK) - 1, LMAX = 1 << kNoAllocMaxK;
+  double node[kNodeWords * NMAX];
+  float node_df[kNodeDfl * NMAX];
+  double wl[LMAX], wn[LMAX];
+  for (int j = 0; j < nleaf; ++j) wl[j] = leaf_w[j];
+  for (int k = K; k >= 1; --k) {  // weight propagation, Sec. 3.1
+    const int cnt = 1 << (k - 1);
+    for (int i = 0; i < cnt; ++i) {
+      const double wa = wl[2 * i], wb = wl[2 * i + 1], w = wa + wb;
+      const int p = nleaf - (1 << k) + i;
+      const double *nv = normals + 3 * p;
+      const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (!(nn > 0.0) || !isfinite(nn))
+        return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: normal %d is zero or not finite", p);
+      double *r = &node[kNodeWords * p];
+      r[0] = nv[0] / nn;
+      r[1] = nv[1] / nn;
+      r[2] = nv[2] / nn;
+      r[3] = wa / w;
+      r[4] = 1.0 - r[3];
+      r[5] = w;
+      r[6] = w * r[3] * r[4];
+      r[7] = 1.0 / r[6];
+      for (int c = 0; c < 3; ++c) r[8 + c] = r[c] / sqrt(2.0);
+      r[11] = 0.0;
+      wn[i] = w;
+    }
+    for (int i = 0; i < cnt; ++i) wl[i] = wn[i];
+  }
+  for (int p = 0; p < N; ++p) {
+    const double *r = &node[kNodeWords * p];
+    const double v[8] = {r[0], r[1], r[2], r[8], r[9], r[10], r[3], r[4]};
+    float *q = &node_df[kNodeDfl * p];
+    for (int i = 0; i < kNodeDfl; ++i) q[i] = 0.0f;
+    for (int i = 0; i < 8; ++i) {
+      const float hi = (float)v[i];
+      q[2 * i] = hi;
+      q[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    q[16] = (float)r[7];
+    q[17] = (float)r[6];
+  }
+  int zoff[LMAX];
+  int off = 8 + 3 * N;
+  for (int j = 0; j < nleaf; ++j) {
+    if (mats[phase_map[j]].kind == DMN_MAT_J2_LINEAR) {
+      zoff[j] = off;
+      off += 7;
+    } else {
+      zoff[j] = -1;
+    }
+  }
+  const int zend = off;
+  const int nz = (zend - (8 + 3 * N)) / 7;
+  if (off & 1) off += 1;
+  const int SW = off;
+  const size_t sbytes = sizeof(double) * (size_t)SW * (size_t)n_points;
+  const char *sa = (const char *)d_state_in, *sb = (const char *)d_state_out;
+  if (sa < sb + sbytes && sb < sa + sbytes)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: state_in overlaps state_out");
+  if ((((uintptr_t)d_state_in) & 15) || (((uintptr_t)d_state_out) & 15))
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: state buffers must be 16-byte aligned");
+
+  // ---- scratch layout ----
+  const size_t o_queue = 0;
+  const size_t o_node = align256(o_queue + sizeof(unsigned long long));
+  const size_t o_ndf = align256(o_node + sizeof(double) * kNodeWords * N);
+  const size_t o_leafw = align256(o_ndf + sizeof(float) * kNodeDfl * N);
+  const size_t o_phase = align256(o_leafw + sizeof(double) * nleaf);
+  const size_t o_zoff = align256(o_phase + nleaf);
+  const size_t o_mat = align256(o_zoff + sizeof(int) * nleaf);
+  const size_t used = o_mat + sizeof(double) * 8 * n_mats;
+  if (used > kScratchBytes)
+    return na_fail(DMN_ERR_INTERNAL, "dmn_eval_noalloc: tables need %zu bytes of scratch", used);
+
+  // ---- per-device set-up: the device address of the scratch array ----
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return na_fail(DMN_ERR_INTERNAL, "device %d out of range", dev);
+  if (!g_scratch_ready[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return na_fail(DMN_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = ptr;
+    g_scratch_ready[dev] = true;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+  const bool mixed = o.precision == DMN_PREC_MIXED;
+  int num_sms = 0, smem_optin = 0, blocks_per_sm = 0;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (solve_smem_bytes(K, nz, n_mats, mixed) > (size_t)smem_optin)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: K=%d does not fit one SM in this precision", K);
+  e = prepare_solve(K, nz, n_mats, mixed, o.solve_variant, &blocks_per_sm);
+  if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "prepare_solve: %s", cudaGetErrorString(e));
+  if (blocks_per_sm < 1) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: kernel does not fit one SM");
+
+  // ---- upload the tables (stream-ordered; the host arrays may go out of
+  //      scope on return because pageable copies are staged before it) ----
+  cudaStream_t s = (cudaStream_t)stream;
+  struct {
+    size_t off;
+    const void *src;
+    size_t bytes;
+  } up[] = {{o_node, node, sizeof(double) * kNodeWords * N},
+            {o_ndf, node_df, sizeof(float) * kNodeDfl * N},
+            {o_leafw, leaf_w, sizeof(double) * nleaf},
+            {o_phase, phase_map, (size_t)nleaf},
+            {o_zoff, zoff, sizeof(int) * nleaf},
+            {o_mat, mat, sizeof(double) * 8 * n_mats}};
+  for (const auto &u : up) {
+    e = cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+  }
+
+  SolveParams P;
+  memset(&P, 0, sizeof(P));
+  P.K = K;
+  P.N = N;
+  P.G = 1 << (K - 1);
+  P.SW = SW;
+  P.zend = zend;
+  P.n_mats = n_mats;
+  P.maxit = o.maxit;
+  P.maxbt = o.maxbacktrack;
+  P.tol = o.tol;
+  P.gamma = o.gamma;
+  P.res_floor = o.res_floor;
+  P.dt = dt;
+  P.node = reinterpret_cast<const double *>(base + o_node);
+  P.node_df = reinterpret_cast<const float *>(base + o_ndf);
+  P.leafw = reinterpret_cast<const double *>(base + o_leafw);
+  P.phase = reinterpret_cast<const uint8_t *>(base + o_phase);
+  P.zoff = reinterpret_cast<const int *>(base + o_zoff);
+  P.mat = reinterpret_cast<const double *>(base + o_mat);
+  P.nz = nz;
+  P.queue = reinterpret_cast<unsigned long long *>(base + o_queue);  // zeroed by launch_solve
+  P.n_points = n_points;
+  P.deps = d_deps;
+  P.theta = d_theta;
+  P.sin = d_state_in;
+  P.sout = d_state_out;
+  P.out = d_out;
+  P.status = d_status;
+  P.iters = d_iters;
+  int64_t grid = (int64_t)num_sms * blocks_per_sm;
+  if (grid > n_points) grid = n_points;
+  e = launch_solve(P, mixed, o.solve_variant, (int)grid, s);
+  if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "dmn_eval_noalloc launch: %s", cudaGetErrorString(e));
+  return DMN_OK;
+}

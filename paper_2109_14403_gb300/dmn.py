@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _build
 
-DMN_OK = 0
+DMN_OK, DMN_ERR_ARG = 0, 1
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 OUT_WORDS = 57
@@ -44,6 +44,8 @@ SIGNATURES = {
     "dmn_state_init": (_I32, [_P, _P, _I64, _P, _P]),
     "dmn_eval": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P]),
     "dmn_last_error": (ctypes.c_char_p, []),
+    "dmn_eval_noalloc": (_I32, [_I32, _P, _P, _P, _P, _I32, _P, _P, _I64, _P, _P, _D, _P, _P, _P,
+                                _P, _P]),
 }
 
 
