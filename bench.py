@@ -42,6 +42,22 @@ def state_words(K, n_j2):
     return w + (w & 1)
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over all ranks (the whole job ends with the slowest)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, steps, t_ms):
+    """Units processed by all ranks per second over the slowest rank's time."""
+    return world * units_per_rank * steps / (t_ms / 1e3)
+
+
 def algorithmic_bytes_per_eval(K):
     """State in + state out + inputs (deps 6, theta 1) + outputs (57) + status + iters."""
     sw = state_words(K, (1 << K) // 2)
@@ -63,7 +79,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -163,6 +179,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args):
+    """262,144 points over three DMNs (K = 6, 7, 8), lognormal strain-increment
+    magnitudes; every increment is the three launches replayed as one CUDA graph."""
+    import torch
+
+    from paper_2109_14403_gb300 import DMN, synthetic as syn
+    from paper_2109_14403_gb300.graph import IncrementGraph
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 262144 if args.points == N_POINTS else args.points
+    steps, warm = args.steps, args.warmup
+    tid, deps, theta = syn.uneven_batch(n_points=n, n_incr=warm + steps, seed=42 + int(os.environ.get("RANK", "0")))
+    trees = syn.uneven_trees()
+    parts, sels = [], []
+    for i, K in enumerate(syn.UNEVEN_DEPTHS):
+        w, nrm, ph = trees[i]
+        sel = np.nonzero(tid == i)[0]
+        parts.append((DMN(K, w, nrm, ph, syn.materials(), tol=TOL, precision=args.precision), len(sel)))
+        sels.append(sel)
+    g = IncrementGraph(parts)
+    for i, (d, m) in enumerate(parts):
+        g.set_state(i, d.init_state(torch.full((m,), syn.THETA_START, dtype=torch.float64, device=dev)))
+    D = [torch.tensor(deps[:, s], device=dev) for s in sels]
+    T = [torch.tensor(theta[:, s], device=dev) for s in sels]
+
+    def load(k):
+        for i in range(len(parts)):
+            g.deps[i].copy_(D[i][k])
+            g.theta[i].copy_(T[i][k])
+
+    for k in range(warm):
+        load(k)
+        g.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    with ClockSampler(local) as clk:
+        e0.record()
+        for k in range(warm, warm + steps):
+            load(k)
+            g.step()
+            iters.append(torch.cat([it.clone() for it in g.iters]))
+        e1.record()
+        torch.cuda.synchronize()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    hist = torch.bincount(torch.cat(iters).long()).cpu().tolist()
+    if int(os.environ.get("RANK", "0")) == 0:
+        line = {"metric": "Gauss-pt DMN evals/s, uneven batch K=6/7/8", "value": whole_job_rate(n, world, steps, t_ms),
+                "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": t_ms / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+                "config": {"workload": f"uneven batch, {n} points over DMNs K=6/7/8, lognormal increments, "
+                                       "CUDA-graph increments", "precision": args.precision, "tol": TOL},
+                "iter_hist": hist, "clocks": clk.summary(), "gpu_launches": 4 * len(parts) * steps}
+        print(json.dumps(line), flush=True)
+    for d, _ in parts:
+        d.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,11 +253,15 @@ def main():
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-variant", action="store_true")
+    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
         return
 
     import torch
@@ -236,12 +320,8 @@ def main():
         return d, s_a, s_b, total_ms, per, clk.summary(), hist, nonconv
 
     d, s_a, s_b, total_ms, per, clocks, hist, nonconv = device_run(args.precision)
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n * steps / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(n, world, steps, t_max)
 
     # end to end through the public API: pinned host inputs in, results out
     deps_p = torch.tensor(deps_h[warm + steps:warm + 2 * steps]).pin_memory()
@@ -268,12 +348,8 @@ def main():
         s_a, s_b = s_b, s_a
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e = {"value": world * n * steps / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e = {"value": whole_job_rate(n, world, steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": n * 7 * 8, "d2h_bytes_per_step": n * (57 * 8 + 8)}
     d.close()
     del s_a, s_b

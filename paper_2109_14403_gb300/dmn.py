@@ -112,7 +112,7 @@ class DMN:
     """A DMN handle on the current CUDA device (``dmn_create``)."""
 
     def __init__(self, K, w, normals, phase, mats, *, tol=1e-10, maxit=50, maxbacktrack=8,
-                 gamma=0.5, precision="fp64", res_floor=0.0, solve_variant=0):
+                 gamma=0.5, precision="fp64", res_floor=0.0, solve_variant=None):
         lib = load()
         self.K = int(K)
         w = np.ascontiguousarray(w, np.float64)
@@ -124,7 +124,11 @@ class DMN:
         opt.tol, opt.maxit, opt.maxbacktrack, opt.gamma = tol, maxit, maxbacktrack, gamma
         opt.res_floor = res_floor
         opt.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        if solve_variant is None:  # the autotuner's choice, if it ran for this case
+            from .autotune import lookup
+            solve_variant = lookup(self.K, precision) if self.K <= 8 and precision == "mixed" else 0
         opt.solve_variant = int(solve_variant)
+        self.solve_variant = int(solve_variant)
         self.precision = precision
         h = ctypes.c_void_p()
         _check(lib.dmn_create(ctypes.byref(h), self.K, w.ctypes.data_as(_P),

@@ -16,7 +16,12 @@ stand in for its strain-controlled virtual experiments, Sec. 5.4):
   * K=4 ramp: 64 points, 20 increments of 0.1 % in the 11 component plus
     N(0, 1e-4) on all six Mandel components, temperature 293 -> 353 K;
   * K=8 random walk: 65,536 points, 50 increments with N(0, 2e-4) on every
-    Mandel component and temperature steps U(0, 1) K from 293 K.
+    Mandel component and temperature steps U(0, 1) K from 293 K;
+  * uneven batch: points spread evenly (shuffled) over three DMNs of depth 6,
+    7 and 8 with independent seeds; strain increments with a direction
+    uniform on the unit sphere of R^6 and a magnitude s0 * LogNormal(0, 1),
+    so Newton iteration counts vary from point to point; temperature steps as
+    above.
 Units: MPa, K, s.  Symmetric tensors are Mandel 6-vectors.
 """
 from __future__ import annotations
@@ -70,3 +75,23 @@ def single_increment(n_points, seed=7, scale=2e-4, theta=300.0):
     deps = rng.normal(0.0, scale, size=(n_points, 6))
     th = np.full(n_points, theta)
     return deps, th
+
+
+UNEVEN_DEPTHS = (6, 7, 8)
+
+
+def uneven_batch(n_points=262144, n_incr=50, s0=1e-3, seed=42):
+    """Returns (tree_id[n], deps[n_incr, n, 6], theta[n_incr, n]); tree_id
+    indexes UNEVEN_DEPTHS, trees come from tree(K, seed=2000 + K)."""
+    rng = np.random.default_rng(seed)
+    tree_id = rng.permutation(np.arange(n_points) % len(UNEVEN_DEPTHS)).astype(np.int32)
+    d = rng.standard_normal((n_incr, n_points, 6))
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    mag = s0 * rng.lognormal(0.0, 1.0, size=(n_incr, n_points, 1))
+    dth = rng.uniform(0.0, 1.0, size=(n_incr, n_points))
+    theta = THETA_START + np.cumsum(dth, axis=0)
+    return tree_id, d * mag, theta
+
+
+def uneven_trees():
+    return [tree(K, seed=2000 + K) for K in UNEVEN_DEPTHS]

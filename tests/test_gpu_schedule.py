@@ -1,0 +1,81 @@
+"""Scheduling paths on the GPU: CUDA-graph increments, the uneven batch of
+three trees (K = 6, 7, 8) against the oracle, and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_14403_gb300 import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def test_graph_replay_equals_direct_launches():
+    from paper_2109_14403_gb300 import DMN
+    from paper_2109_14403_gb300.graph import IncrementGraph
+    dev = _dev()
+    n = 2000
+    w, nrm, ph = syn.tree(8)
+    d = DMN(8, w, nrm, ph, syn.materials(), precision="mixed")
+    deps, theta = syn.random_walk_k8(n_points=n, n_incr=3)
+    s = d.init_state(torch.full((n,), 293.0, dtype=torch.float64, device=dev))
+    g = IncrementGraph([(d, n)])
+    g.set_state(0, s)
+    for k in range(3):
+        g.deps[0].copy_(torch.tensor(deps[k] * 5, device=dev))
+        g.theta[0].copy_(torch.tensor(theta[k], device=dev))
+        g.step()
+        s, out, st, it = d.eval(torch.tensor(deps[k] * 5, device=dev),
+                                torch.tensor(theta[k], device=dev), 1.0, s)
+        torch.cuda.synchronize()
+        assert torch.equal(out, g.out[0]) and torch.equal(s, g.current_state(0))
+        assert torch.equal(it, g.iters[0])
+    d.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_batch_three_depths_against_oracle(prec):
+    from paper_2109_14403_gb300 import DMN
+    dev = _dev()
+    n = 3000
+    tid, deps, theta = syn.uneven_batch(n_points=n, n_incr=2)
+    trees = syn.uneven_trees()
+    mats = syn.materials()
+    tol = {"fp64": 1e-10, "mixed": 1e-8}[prec]
+    iters_all = []
+    for i, K in enumerate(syn.UNEVEN_DEPTHS):
+        w, nrm, ph = trees[i]
+        sel = np.nonzero(tid == i)[0]
+        d = DMN(K, w, nrm, ph, mats, tol=1e-12, precision=prec)
+        s = d.init_state(torch.full((len(sel),), 293.0, dtype=torch.float64, device=dev))
+        ot = oracle.Tree(K, w, nrm, ph, mats)
+        chk = sel[:: max(1, len(sel) // 40)]
+        pos = np.searchsorted(sel, chk)
+        so = ot.init_state(len(chk), 293.0)
+        for k in range(2):
+            s, out, st, it = d.eval(torch.tensor(deps[k][sel], device=dev),
+                                    torch.tensor(theta[k][sel], device=dev), 1.0, s)
+            so, oo, sto, _ = oracle.eval_batch(ot, deps[k][chk], theta[k][chk], 1.0, so)
+            g = out.cpu().numpy()[pos]
+            assert (st.cpu().numpy() == 0).all() and (sto == 0).all()
+            rel = np.linalg.norm(g[:, :6] - oo[:, :6], axis=1) / np.linalg.norm(oo[:, :6], axis=1)
+            assert rel.max() < tol
+            iters_all.append(it.cpu().numpy())
+        d.close()
+    it = np.concatenate(iters_all)
+    assert it.max() >= 3 * it.min()  # uneven Newton iteration counts
+
+
+def test_autotuner_writes_a_choice(tmp_path):
+    from paper_2109_14403_gb300 import autotune
+    _dev()
+    p = str(tmp_path / "tuning.json")
+    e = autotune.tune(K=6, n_points=4096, n_steps=2, warmup=1, path=p)
+    assert e["variant"] in autotune.VARIANTS
+    assert autotune.lookup(6, "mixed", p) == e["variant"]
