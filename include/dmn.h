@@ -63,7 +63,8 @@ typedef enum {
 enum {
   DMN_PT_OK = 0,            /* residual < tol                              */
   DMN_PT_NOT_CONVERGED = 1, /* maxit Newton iterations without res < tol   */
-  DMN_PT_NONFINITE = 2      /* a residual or an output was NaN or Inf      */
+  DMN_PT_NONFINITE = 2,     /* a residual or an output was NaN or Inf      */
+  DMN_PT_FALLBACK_USED = 4  /* bit: warm start failed, re-run from a^n     */
 };
 
 /* phase laws (Sec. 4) */

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dmn.h"
+#include "../../include/dmn_mlp.h"
 #include "dmn_internal.h"
 
 using namespace dmn;
@@ -278,10 +279,10 @@ extern "C" dmn_status dmn_state_init(dmn_handle h, double *d_state, int64_t n_po
   return DMN_OK;
 }
 
-extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points,
-                               const double *d_deps, const double *d_theta, double dt,
-                               const double *d_state_in, double *d_state_out, double *d_out,
-                               int32_t *d_status, int32_t *d_iters) {
+static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
+                            const double *d_deps, const double *d_theta, double dt,
+                            const double *d_state_in, double *d_state_out, double *d_out,
+                            int32_t *d_status, int32_t *d_iters, const float *d_da) {
   g_err[0] = 0;
   if (!h) return fail(DMN_ERR_ARG, "dmn_eval: NULL handle");
   if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_eval: n_points < 0");
@@ -326,9 +327,27 @@ extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points
   P.status = d_status;
   P.iters = d_iters;
   P.queue = h->d_queue;
+  P.da0 = d_da;
   int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm;
   if (grid > n_points) grid = n_points;
   cudaError_t e = launch_solve(P, mixed, h->opt.solve_variant, (int)grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "dmn_eval launch");
   return DMN_OK;
+}
+
+extern "C" dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points,
+                               const double *d_deps, const double *d_theta, double dt,
+                               const double *d_state_in, double *d_state_out, double *d_out,
+                               int32_t *d_status, int32_t *d_iters) {
+  return eval_impl(h, stream, n_points, d_deps, d_theta, dt, d_state_in, d_state_out, d_out,
+                   d_status, d_iters, nullptr);
+}
+
+extern "C" dmn_status dmn_eval_warm(dmn_handle h, dmn_stream stream, int64_t n_points,
+                                    const double *d_deps, const double *d_theta, double dt,
+                                    const double *d_state_in, double *d_state_out, double *d_out,
+                                    int32_t *d_status, int32_t *d_iters, const float *d_da) {
+  if (!d_da && n_points > 0) return fail(DMN_ERR_ARG, "dmn_eval_warm: d_da is NULL");
+  return eval_impl(h, stream, n_points, d_deps, d_theta, dt, d_state_in, d_state_out, d_out,
+                   d_status, d_iters, d_da);
 }

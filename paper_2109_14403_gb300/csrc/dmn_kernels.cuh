@@ -49,6 +49,7 @@ struct SolveParams {
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
   int nz, pad2_;                   // number of leaves with internal variables
   unsigned long long *queue;       // device counter of points taken (zeroed per launch)
+  const float *da0;                // optional warm-start increment [n][3N] (NULL: start at a^n)
   double tol, gamma, res_floor, dt;
   const double *node;      // [N][kNodeWords]: n0 n1 n2 c1 c2 w w*c1*c2 1/(w*c1*c2)
                            //   n0/sqrt2 n1/sqrt2 n2/sqrt2 0

@@ -207,6 +207,30 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
   auto lev = [&](int k) { return ((k ^ K) & 1) ? esO : esK; };  // buffer of level k
   HP *const es1 = lev(1);  // root: strain, then sigma_bar
+  // top-down strain scatter from the root strain (eq. DMN kinematics): node j
+  // of level k on thread j; on return esK holds the bottom laminates' strains
+  auto scatter = [&](const HP *root) {
+    for (int c = t; c < 6; c += G) es1[c] = root[c];
+    __syncthreads();
+    for (int k = 1; k <= K - 1; ++k) {
+      if (t < (1 << (k - 1))) {
+        const int p = (1 << K) - (1 << k) + t;
+        HP *ep = lev(k) + 6 * t, *ec = lev(k + 1) + 12 * t;
+        NodeHP<HP> nd;
+        load_node(P, p, nd);
+        const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
+        HP J[6];
+        bvec_hp(nd, av, J);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const HP e = ep[c];
+          ec[c] = e + nd.c2 * J[c];
+          ec[6 + c] = e - nd.c1 * J[c];
+        }
+      }
+      __syncthreads();
+    }
+  };
 
   for (int i = t; i < P.n_mats; i += G)
     mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
@@ -252,31 +276,34 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
     HP *zw1 = zq1 >= 0 ? zw_s + zq1 : nullptr;
 
     HP trn0 = hp_zero(tag), trn1 = hp_zero(tag);
-    bool first = true;
+    bool first = true;  // the first pass also yields the traces of eps^n
+    if (P.da0) {
+      // warm start a^n + da0: the traces of eps^n come from a scatter at a^n
+      HP ebn[6];
+      for (int c = 0; c < 6; ++c) ebn[c] = hp_load(sin[c], tag);  // eps_bar^n
+      __syncthreads();
+      scatter(ebn);
+      NodeHP<HP> nd;
+      load_node(P, t, nd);
+      const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
+      HP J[6];
+      bvec_hp(nd, av, J);
+      const HP trj = J[0] + J[1] + J[2];
+      const HP tre = esK[6 * t] + esK[6 * t + 1] + esK[6 * t + 2];
+      trn0 = tre + nd.c2 * trj;
+      trn1 = tre - nd.c1 * trj;
+      first = false;
+      __syncthreads();
+      const float *d0 = P.da0 + pt * (3 * N);
+      for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], TF(d0[i]));
+      __syncthreads();
+    }
+    int attempt = 0, it_total = 0;
     HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
     Rec<TF> rec;
     for (;;) {
       // ---- R1: strains, top-down (eq. DMN kinematics) ----
-      for (int c = t; c < 6; c += G) es1[c] = eb[c];
-      __syncthreads();
-      for (int k = 1; k <= K - 1; ++k) {
-        if (t < (1 << (k - 1))) {
-          const int p = (1 << K) - (1 << k) + t;
-          HP *ep = lev(k) + 6 * t, *ec = lev(k + 1) + 12 * t;
-          NodeHP<HP> nd;
-          load_node(P, p, nd);
-          const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
-          HP J[6];
-          bvec_hp(nd, av, J);
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const HP e = ep[c];
-            ec[c] = e + nd.c2 * J[c];
-            ec[6 + c] = e - nd.c1 * J[c];
-          }
-        }
-        __syncthreads();
-      }
+      scatter(eb);
       // ---- R2: leaves and laminate t ----
       TF r2;
       {
@@ -419,7 +446,26 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
       first = false;
       __syncthreads();
       const int action = ctrl->action;
-      if (action == ACT_DONE) break;
+      if (action == ACT_DONE) {
+        if (P.da0 && attempt == 0 && ctrl->status != 0) {
+          // warm-started iteration failed: run Algorithm 1 again from a^n
+          attempt = 1;
+          it_total = ctrl->it;
+          for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
+          __syncthreads();
+          if (t == 0) {
+            ctrl->first = 1;
+            ctrl->it = 0;
+            ctrl->bt = 0;
+            ctrl->gi = TF(1);
+            ctrl->res_old = TF(0);
+            ctrl->status = 0;
+          }
+          __syncthreads();
+          continue;
+        }
+        break;
+      }
       if (action == ACT_STEP) {
         back_substitute<TF>(P, da_s, gh_s, slots, t);
         __syncthreads();
@@ -469,8 +515,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
     }
     bad = __syncthreads_or(bad);
     if (t == 0) {
-      P.status[pt] = bad ? 2 : ctrl->status;
-      P.iters[pt] = ctrl->it;
+      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
+      P.iters[pt] = ctrl->it + it_total;
     }
     for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
       sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);

@@ -14,7 +14,7 @@ import numpy as np
 from . import _build
 
 DMN_OK, DMN_ERR_ARG = 0, 1
-PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
+PT_OK, PT_NOT_CONVERGED, PT_NONFINITE, PT_FALLBACK_USED = 0, 1, 2, 4
 PREC_FP64, PREC_MIXED = 0, 1
 OUT_WORDS = 57
 
@@ -46,6 +46,24 @@ SIGNATURES = {
     "dmn_last_error": (ctypes.c_char_p, []),
     "dmn_eval_noalloc": (_I32, [_I32, _P, _P, _P, _P, _I32, _P, _P, _I64, _P, _P, _D, _P, _P, _P,
                                 _P, _P]),
+    # include/dmn_mlp.h
+    "dmn_mlp_create": (_I32, [_P, _I32, _I32, _I32, _I64, ctypes.c_uint64]),
+    "dmn_mlp_destroy": (_I32, [_P]),
+    "dmn_mlp_dims": (_I32, [_P, _P, _P, _P, _P]),
+    "dmn_mlp_features": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _I64, _P]),
+    "dmn_mlp_targets": (_I32, [_P, _P, _I64, _P, _P, _I64, _P]),
+    "dmn_mlp_fit_normalization": (_I32, [_P, _P, _I64, _P, _P]),
+    "dmn_mlp_normalize_features": (_I32, [_P, _P, _I64, _P, _P]),
+    "dmn_mlp_normalize_targets": (_I32, [_P, _P, _I64, _P, _P]),
+    "dmn_mlp_train_step": (_I32, [_P, _P, _I64, _P, _P, ctypes.c_float, _P]),
+    "dmn_mlp_predict": (_I32, [_P, _P, _I64, _P, _P]),
+    "dmn_mlp_param_count": (_I64, [_P]),
+    "dmn_mlp_get_params": (_I32, [_P, _P]),
+    "dmn_mlp_set_params": (_I32, [_P, _P]),
+    "dmn_mlp_get_grads": (_I32, [_P, _P]),
+    "dmn_mlp_get_normalization": (_I32, [_P, _P, _P, _P, _P]),
+    "dmn_gemm_bf16_tn": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
+    "dmn_eval_warm": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -181,4 +199,29 @@ class DMN:
                              _dev(out, torch.float64, (n, OUT_WORDS), "out"),
                              _dev(status, torch.int32, (n,), "status"),
                              _dev(iters, torch.int32, (n,), "iters")), "dmn_eval")
+        return state_out, out, status, iters
+
+    def eval_warm(self, deps, theta, dt, state_in, da, state_out=None, out=None, status=None,
+                  iters=None, stream=None):
+        """``dmn_eval_warm``: start from a^n + da (fp32 [n, 3(2^K-1)])."""
+        import torch
+        n = deps.shape[0]
+        dev = deps.device
+        if state_out is None:
+            state_out = torch.empty_like(state_in)
+        if out is None:
+            out = torch.empty((n, OUT_WORDS), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=dev)
+        if iters is None:
+            iters = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(_lib.dmn_eval_warm(self._h, _stream_ptr(stream), n,
+                                  _dev(deps, torch.float64, (n, 6), "deps"),
+                                  _dev(theta, torch.float64, (n,), "theta"), float(dt),
+                                  _dev(state_in, torch.float64, (n, self.state_words), "state_in"),
+                                  _dev(state_out, torch.float64, (n, self.state_words), "state_out"),
+                                  _dev(out, torch.float64, (n, OUT_WORDS), "out"),
+                                  _dev(status, torch.int32, (n,), "status"),
+                                  _dev(iters, torch.int32, (n,), "iters"),
+                                  _dev(da, torch.float32, (n, 3 * self.nnode), "da")), "dmn_eval_warm")
         return state_out, out, status, iters

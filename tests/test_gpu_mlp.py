@@ -1,0 +1,197 @@
+"""Warm-start network on the GPU: the tcgen05 GEMM, gradients and forward pass
+against the FP64 reference in oracle/mlp.py, training, and what the trained
+network gains in the Newton solve."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2109_14403_gb300 import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _bf16_round(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (512, 768, 896)])
+def test_gemm_matches_fp32_reference(M, N, K):
+    from paper_2109_14403_gb300.mlp import gemm_bf16_tn
+    dev = _dev()
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    a = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
+    b = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
+    c = gemm_bf16_tn(a, b)
+    ref = a.float() @ b.float().T
+    torch.cuda.synchronize()
+    err = (c - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5
+
+
+def _small_net(dev, seed=3):
+    from paper_2109_14403_gb300.mlp import MLP
+    net = MLP(K=2, hidden=128, n_hidden=2, max_batch=512, seed=seed)
+    rng = np.random.default_rng(seed)
+    p = np.zeros(net.n_params, np.float32)
+    o = 0
+    for li, (din, dout) in enumerate(net.layer_dims()):
+        rows = net.n_out if li == len(net.layer_dims()) - 1 else dout
+        cols = net.n_in if li == 0 else din
+        W = np.zeros((dout, din), np.float32)
+        W[:rows, :cols] = rng.normal(0, 1.0 / np.sqrt(cols), (rows, cols))
+        b = np.zeros(dout, np.float32)
+        b[:rows] = rng.normal(0, 0.1, rows)
+        p[o:o + din * dout] = W.ravel()
+        o += din * dout
+        p[o:o + dout] = b
+        o += dout
+    net.set_params(p)
+    return net, p, rng
+
+
+def _inputs(net, rng, n, dev):
+    x = np.zeros((n, net.n_in_pad), np.float32)
+    x[:, :net.n_in] = rng.normal(size=(n, net.n_in))
+    t = np.zeros((n, net.n_out_pad), np.float32)
+    t[:, :net.n_out] = rng.normal(size=(n, net.n_out))
+    xg = torch.tensor(x).to(torch.bfloat16).to(dev)
+    return xg, torch.tensor(t, device=dev), _bf16_round(x), t
+
+
+def _oracle_params(net, p):
+    """bf16 weights (as the GPU multiplies them), fp32 biases."""
+    q = p.astype(np.float64).copy()
+    o = 0
+    for din, dout in net.layer_dims():
+        q[o:o + din * dout] = _bf16_round(p[o:o + din * dout])
+        o += din * dout + dout
+    return q
+
+
+def test_gradients_match_fp64_reference():
+    dev = _dev()
+    net, p, rng = _small_net(dev)
+    n = 200  # ragged: padded to 256 rows inside
+    xg, tg, x64, t64 = _inputs(net, rng, n, dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    net.train_step(xg, tg, 0.0, loss)
+    torch.cuda.synchronize()
+    g = net.grads().astype(np.float64)
+    L, gref = omlp.loss_and_grads(_oracle_params(net, p), net.layer_dims(), x64, t64, net.n_out)
+    assert abs(loss.item() - L) <= 2e-2 * L
+    o = 0
+    for din, dout in net.layer_dims():
+        for size in (din * dout, dout):
+            a, b = g[o:o + size], gref[o:o + size]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-12
+            o += size
+    net.close()
+
+
+def test_forward_matches_fp64_reference():
+    dev = _dev()
+    net, p, rng = _small_net(dev, seed=5)
+    n = 300
+    xg, _, x64, _ = _inputs(net, rng, n, dev)
+    y = net.predict(xg).cpu().numpy()  # default normalisation: identity
+    hs, _ = omlp.forward(omlp.unpack(_oracle_params(net, p), net.layer_dims()), x64)
+    ref = hs[-1][:, :net.n_out]
+    assert np.abs(y - ref).max() <= 2e-2 * np.abs(ref).max()
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    from paper_2109_14403_gb300.mlp import MLP
+    dev = _dev()
+    net = MLP(K=2, hidden=128, n_hidden=2, max_batch=1024, seed=1)
+    rng = np.random.default_rng(2)
+    n = 1024
+    x = np.zeros((n, net.n_in_pad), np.float32)
+    x[:, :net.n_in] = rng.normal(size=(n, net.n_in))
+    R = rng.normal(0, 0.3, (net.n_in, net.n_out))
+    t = np.zeros((n, net.n_out_pad), np.float32)
+    t[:, :net.n_out] = np.tanh(x[:, :net.n_in] @ R)
+    xg = torch.tensor(x).to(torch.bfloat16).to(dev)
+    tg = torch.tensor(t, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    net.train_step(xg, tg, 0.0, loss)
+    l0 = loss.item()
+    for _ in range(300):
+        net.train_step(xg, tg, 3e-3, loss)
+    torch.cuda.synchronize()
+    assert loss.item() < 0.1 * l0
+    net.close()
+
+
+def test_warm_start_gain_on_the_k8_random_walk():
+    """Pairs from the plain FP64 solver on the K=8 random walk train the
+    network; on later, held-out increments the warm-started mixed solve
+    (tol 1e-12, the paper's tolerance) must stay within 2e-8 of the FP64
+    solution (tol 1e-13), like the plain mixed solve, and take fewer Newton
+    iterations."""
+    from paper_2109_14403_gb300 import DMN
+    from paper_2109_14403_gb300.mlp import MLP
+    dev = _dev()
+    K, n, n_train, n_eval = 8, 16384, 10, 3
+    w, nrm, ph = syn.tree(K)
+    mats = syn.materials()
+    deps, theta = syn.random_walk_k8(n_points=n, n_incr=n_train + n_eval, seed=11)
+    D = torch.tensor(deps, device=dev)
+    T = torch.tensor(theta, device=dev)
+    plain = DMN(K, w, nrm, ph, mats, precision="fp64", tol=1e-13)
+    net = MLP(K=K, hidden=512, n_hidden=3, max_batch=n, seed=0)
+    s_prev = None
+    s = plain.init_state(torch.full((n,), 293.0, dtype=torch.float64, device=dev))
+    feats, tgts, hist = [], [], []
+    for k in range(n_train + n_eval):
+        s1, out, st, it = plain.eval(D[k], T[k], 1.0, s)
+        if k < n_train:
+            feats.append(net.features(D[k], T[k], s, s_prev))
+            tgts.append(net.targets(s, s1))
+        hist.append((s_prev, s, out.cpu().numpy()[:, :6]))
+        s_prev, s = s, s1
+    F = torch.cat(feats)
+    Tg = torch.cat(tgts)
+    net.fit_normalization(F, Tg)
+    X = net.normalize_features(F)
+    Y = net.normalize_targets(Tg)
+    perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    X, Y = X[perm].contiguous(), Y[perm].contiguous()
+    B = 4096
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    for ep in range(12):
+        for i in range(0, X.shape[0] - B + 1, B):
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
+    torch.cuda.synchronize()
+    assert loss.item() < 0.01  # normalised MSE
+    mixed = DMN(K, w, nrm, ph, mats, precision="mixed", tol=1e-12)
+    it_plain, it_warm, fallbacks = [], [], 0
+    for k in range(n_train, n_train + n_eval):
+        sp, si, ref = hist[k]
+        da = net.predict(net.normalize_features(net.features(D[k], T[k], si, sp)))
+        _, op, stp, itp = mixed.eval(D[k], T[k], 1.0, si)
+        _, ow, stw, itw = mixed.eval_warm(D[k], T[k], 1.0, si, da)
+        torch.cuda.synchronize()
+        assert (stp.cpu() == 0).all() and ((stw.cpu() & 3) == 0).all()
+        fallbacks += int(((stw.cpu() & 4) != 0).sum())
+        for o in (op, ow):
+            g = o.cpu().numpy()[:, :6]
+            assert (np.linalg.norm(g - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 2e-8
+        it_plain.append(itp.cpu().numpy())
+        it_warm.append(itw.cpu().numpy())
+    ip, iw = np.concatenate(it_plain), np.concatenate(it_warm)
+    print(f"\nwarm start: mean Newton iterations {ip.mean():.4f} -> {iw.mean():.4f}, "
+          f"points needing >1 iteration {np.mean(ip > 1):.4f} -> {np.mean(iw > 1):.4f}, "
+          f"fallback rate {fallbacks / ip.size:.5f}")
+    assert iw.mean() < 0.8 * ip.mean()
+    assert fallbacks / ip.size < 0.01
+    plain.close()
+    mixed.close()
+    net.close()
