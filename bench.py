@@ -249,6 +249,47 @@ def run_uneven(args):
         d.close()
 
 
+def run_mlp(args):
+    """Inference of the warm-start network alone (4 tcgen05 GEMMs with fused
+    bias/SiLU/de-normalisation epilogues) on 65,536 points: the tensor path."""
+    import torch
+
+    from paper_2109_14403_gb300.mlp import MLP
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.points
+    net = MLP(K=K_DEPTH, hidden=512, n_hidden=3, max_batch=n, seed=0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    x = torch.randn((n, net.n_in_pad), generator=g, device=dev).to(torch.bfloat16)
+    da = torch.empty((n, net.n_out), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        net.predict(x, out=da)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.predict(x, out=da)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    dims = net.layer_dims()
+    flops = 2.0 * n * sum(a * b for a, b in dims)
+    tf = flops / (ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, how = float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, how = 1900.0, "fallback"
+    print(json.dumps({"metric": "warm-start MLP inference", "value": n / (ms / 1e3), "unit": "points/s",
+                      "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": f"{n} x (896 -> 512 -> 512 -> 512 -> 768) bf16, fp32 accumulate"},
+                      "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": tf / peak, "peak_source": how, "flops_per_step": flops},
+                      "gpu_launches": 4 * args.steps}), flush=True)
+    net.close()
+
+
 def alu_flops_per_pass(K):
     """Algorithmic FLOPs of one Newton pass (Residual + condensation), counted
     from the formulas: ~950 per laminate for the condensation (K_p, its
@@ -270,7 +311,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="uneven workload only")
-    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven"])
+    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven", "mlp"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -279,6 +320,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args)
+        return
+    if args.workload == "mlp":
+        run_mlp(args)
         return
 
     import torch
@@ -353,8 +397,7 @@ def main():
 
     def warm_step(k, it_out, ev=None):
         p, c, nx = bufs
-        net.features(D[k], T[k], c, p, out=feat)
-        net.normalize_features(feat, out=xin)
+        net.input(D[k], T[k], c, p, out=xin)
         net.predict(xin, out=da)
         if ev is not None:
             ev[0].record(stream)
@@ -415,8 +458,7 @@ def main():
         dd.copy_(deps_p[j], non_blocking=True)
         th.copy_(theta_p[j], non_blocking=True)
         p, c, nx = bufs
-        net.features(dd, th, c, p, out=feat)
-        net.normalize_features(feat, out=xin)
+        net.input(dd, th, c, p, out=xin)
         net.predict(xin, out=da)
         mixed.eval_warm(dd, th, 1.0, c, da, nx, out, st, it)
         bufs[0], bufs[1], bufs[2] = c, nx, p
@@ -487,7 +529,7 @@ def main():
             "iter_hist": hist, "mean_iters": mean_iters, "fallback_rate": fallback_rate,
             "warm_start_training": train_info, "variants": variants,
             "solve_kernel_ms": solve_ms,
-            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 7 * steps}
+            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 6 * steps}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

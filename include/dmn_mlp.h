@@ -50,6 +50,12 @@ dmn_status dmn_mlp_features(dmn_mlp m, dmn_stream stream, int64_t n, const doubl
                             const double *d_theta, const double *d_state_in,
                             const double *d_state_prev, int64_t state_words, float *d_feat);
 
+/* The network input in one pass: the features above, normalised and rounded
+   to bf16 [n x n_in_pad] (what dmn_mlp_predict takes). */
+dmn_status dmn_mlp_input(dmn_mlp m, dmn_stream stream, int64_t n, const double *d_deps,
+                         const double *d_theta, const double *d_state_in,
+                         const double *d_state_prev, int64_t state_words, void *d_x_bf16);
+
 /* Raw targets, fp32 [n x n_out]: a^{n+1} - a^n from the states before and
    after a converged increment. */
 dmn_status dmn_mlp_targets(dmn_mlp m, dmn_stream stream, int64_t n, const double *d_state_in,

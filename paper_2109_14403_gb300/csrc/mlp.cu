@@ -91,6 +91,28 @@ __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const 
   }
 }
 
+// features of k_features, normalised and rounded to bf16 in one pass
+__global__ void k_features_norm(int64_t n, int n3, int sw, int ld, const double *deps,
+                                const double *theta, const double *sin, const double *sprev,
+                                const float *mean, const float *inv, bf16 *x) {
+  const int nin = 8 + n3;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * ld;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / ld;
+    const int c = int(i - r * ld);
+    float v = 0.0f;
+    if (c < nin) {
+      double f;
+      if (c < 6) f = deps[r * 6 + c];
+      else if (c == 6) f = theta[r];
+      else if (c == 7) f = theta[r] - sin[r * sw + 6];
+      else f = sprev ? sin[r * sw + 8 + (c - 8)] - sprev[r * sw + 8 + (c - 8)] : 0.0;
+      v = (float(f) - mean[c]) * inv[c];
+    }
+    x[i] = __float2bfloat16(v);
+  }
+}
+
 __global__ void k_targets(int64_t n, int n3, int sw, const double *sin, const double *sout,
                           float *tgt) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * n3;
@@ -178,21 +200,27 @@ __global__ void k_transpose(int rows, int cols, const bf16 *src, bf16 *dst) {
 }
 
 // MSE on normalised targets: dY = 2 (y - t) / (n n_out) on valid rows and
-// columns, 0 elsewhere; bf16 copy and transposed copy; loss sum
+// columns, 0 elsewhere; bf16 copy and (through a 32 x 32 shared tile) a
+// transposed copy; loss sum.  Block (32, 8) per tile of 32 rows x 32 columns.
 __global__ void k_loss(int n, int npad, int nout, int ld, const float *y, const float *t, bf16 *dz,
                        bf16 *dzt, float *loss, float scale) {
+  __shared__ bf16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   float part = 0.0f;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(npad) * ld;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int r = int(i / ld), c = int(i - int64_t(r) * ld);
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int r = r0 + j, c = c0 + threadIdx.x;
+    const size_t i = size_t(r) * ld + c;
     const float d = (r < n && c < nout) ? y[i] - t[i] : 0.0f;
     part += d * d;
     const bf16 g = __float2bfloat16(2.0f * d * scale);
     dz[i] = g;
-    dzt[size_t(c) * npad + r] = g;
+    tile[j][threadIdx.x] = g;
   }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8)
+    dzt[size_t(c0 + j) * npad + r0 + threadIdx.x] = tile[threadIdx.x][j];
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part * scale);
+  if (threadIdx.x == 0 && loss) atomicAdd(loss, part * scale);
 }
 
 // db[i] = sum_j dzt[i][j] (one warp per row)
@@ -307,9 +335,10 @@ cudaError_t stage_x(dmn_mlp p, cudaStream_t s, int64_t n, int64_t npad, const vo
   return e;
 }
 // forward pass; train = keep pre-activations and transposed activations
-cudaError_t forward(dmn_mlp p, cudaStream_t s, int64_t n, int64_t npad, bool train, float *da) {
+cudaError_t forward(dmn_mlp p, cudaStream_t s, int64_t n, int64_t npad, bool train, float *da,
+                    const bf16 *x_in) {
   cudaError_t e = cudaSuccess;
-  const bf16 *in = p->x;
+  const bf16 *in = x_in;
   for (int l = 0; l < p->L; ++l) {
     EpiArgs ep;
     memset(&ep, 0, sizeof(ep));
@@ -319,7 +348,7 @@ cudaError_t forward(dmn_mlp p, cudaStream_t s, int64_t n, int64_t npad, bool tra
     ep.ldt = int(npad);
     if (l < p->L - 1) {
       ep.mode = EPI_BIAS_SILU;
-      ep.z_out = p->z[l];
+      ep.z_out = train ? p->z[l] : nullptr;  // pre-activations only for the backward pass
       ep.h_out = p->h[l];
       ep.t_out = train ? p->ht[l] : nullptr;
     } else {
@@ -475,6 +504,21 @@ extern "C" dmn_status dmn_mlp_features(dmn_mlp m, dmn_stream stream, int64_t n, 
   return e == cudaSuccess ? DMN_OK : cuda_fail(e, "dmn_mlp_features");
 }
 
+extern "C" dmn_status dmn_mlp_input(dmn_mlp m, dmn_stream stream, int64_t n, const double *d_deps,
+                                    const double *d_theta, const double *d_state_in,
+                                    const double *d_state_prev, int64_t state_words,
+                                    void *d_x_bf16) {
+  set_error_message("");
+  if (!m || n < 0 || !d_deps || !d_theta || !d_state_in || !d_x_bf16 || state_words < 8 + m->n3)
+    return fail(DMN_ERR_ARG, "dmn_mlp_input: invalid argument");
+  if (n == 0) return DMN_OK;
+  k_features_norm<<<blocks_for(n * m->kin), 256, 0, (cudaStream_t)stream>>>(
+      n, m->n3, int(state_words), m->kin, d_deps, d_theta, d_state_in, d_state_prev, m->fmean,
+      m->finv, static_cast<bf16 *>(d_x_bf16));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DMN_OK : cuda_fail(e, "dmn_mlp_input");
+}
+
 extern "C" dmn_status dmn_mlp_targets(dmn_mlp m, dmn_stream stream, int64_t n,
                                       const double *d_state_in, const double *d_state_out,
                                       int64_t state_words, float *d_tgt) {
@@ -543,11 +587,11 @@ extern "C" dmn_status dmn_mlp_train_step(dmn_mlp m, dmn_stream stream, int64_t n
   if (e != cudaSuccess) return cuda_fail(e, "dmn_mlp_train_step staging");
   k_transpose<<<dim3((m->kin + 31) / 32, unsigned((npad + 31) / 32)), dim3(32, 8), 0, s>>>(
       int(npad), m->kin, m->x, m->xt);
-  if ((e = forward(m, s, n, npad, true, nullptr)) != cudaSuccess) return cuda_fail(e, "forward");
+  if ((e = forward(m, s, n, npad, true, nullptr, m->x)) != cudaSuccess) return cuda_fail(e, "forward");
   const int Lo = m->L - 1;
-  k_loss<<<blocks_for(npad * m->nout_pad), 256, 0, s>>>(int(n), int(npad), m->n3, m->nout_pad, m->y,
-                                                         m->t, m->dz[Lo], m->dzt[Lo], d_loss,
-                                                         1.0f / (float(n) * float(m->n3)));
+  k_loss<<<dim3(m->nout_pad / 32, unsigned(npad / 32)), dim3(32, 8), 0, s>>>(
+      int(n), int(npad), m->n3, m->nout_pad, m->y, m->t, m->dz[Lo], m->dzt[Lo], d_loss,
+      1.0f / (float(n) * float(m->n3)));
   for (int l = Lo; l >= 0; --l) {
     // weight gradient dW_l = dZ_l^T . input_l  (reduction over the batch)
     EpiArgs ep;
@@ -590,8 +634,13 @@ extern "C" dmn_status dmn_mlp_predict(dmn_mlp m, dmn_stream stream, int64_t n, c
   if (n == 0) return DMN_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t npad = rup(n, 128);
-  cudaError_t e = stage_x(m, s, n, npad, d_x_bf16);
-  if (e == cudaSuccess) e = forward(m, s, n, npad, false, d_da);
+  cudaError_t e = cudaSuccess;
+  const bf16 *xin = static_cast<const bf16 *>(d_x_bf16);
+  if (npad != n || (reinterpret_cast<uintptr_t>(d_x_bf16) & 15)) {  // pad into the workspace
+    e = stage_x(m, s, n, npad, d_x_bf16);
+    xin = m->x;
+  }
+  if (e == cudaSuccess) e = forward(m, s, n, npad, false, d_da, xin);
   return e == cudaSuccess ? DMN_OK : cuda_fail(e, "dmn_mlp_predict");
 }
 

@@ -2,9 +2,10 @@
 //   C[M x N] = A[M x K] . B[N x K]^T   (A, B bf16 with K contiguous; FP32
 //   accumulation in tensor memory), followed by a fused epilogue.
 //
-// One CTA of 128 threads computes a 128 x 128 tile:
+// One CTA of 128 threads computes a 128 x 128 tile; two CTAs share an SM, so
+// one's epilogue overlaps the other's MMAs:
 //   warp 0, lane 0  loads A and B tiles (64 wide in K) with TMA bulk tensor
-//                   copies into a 4-stage ring of 128-byte-swizzled shared
+//                   copies into a 3-stage ring of 128-byte-swizzled shared
 //                   memory, signalled by mbarriers with transaction counts;
 //   warp 1          allocates 128 TMEM columns; its lane 0 issues
 //                   tcgen05.mma (kind::f16, BF16 x BF16 -> F32, M=128,
@@ -24,7 +25,7 @@
 namespace dmn {
 namespace mlp {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
 constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;  // bytes per stage
 constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
@@ -128,7 +129,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  int K, const EpiArgs ep) {
   extern __shared__ __align__(1024) unsigned char gsm[];
@@ -219,10 +220,12 @@ __global__ void __launch_bounds__(128, 1)
           zb[i] = __float2bfloat16(z);
           hb[i] = __float2bfloat16(z * sigmoidf_(z));
         }
-        uint4 *zo = reinterpret_cast<uint4 *>(ep.z_out + size_t(r) * ep.ldc + n);
+        if (ep.z_out) {
+          uint4 *zo = reinterpret_cast<uint4 *>(ep.z_out + size_t(r) * ep.ldc + n);
+          zo[0] = reinterpret_cast<uint4 *>(zb)[0];
+          zo[1] = reinterpret_cast<uint4 *>(zb)[1];
+        }
         uint4 *ho = reinterpret_cast<uint4 *>(ep.h_out + size_t(r) * ep.ldc + n);
-        zo[0] = reinterpret_cast<uint4 *>(zb)[0];
-        zo[1] = reinterpret_cast<uint4 *>(zb)[1];
         ho[0] = reinterpret_cast<uint4 *>(hb)[0];
         ho[1] = reinterpret_cast<uint4 *>(hb)[1];
         if (ep.t_out) {

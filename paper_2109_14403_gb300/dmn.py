@@ -51,6 +51,7 @@ SIGNATURES = {
     "dmn_mlp_destroy": (_I32, [_P]),
     "dmn_mlp_dims": (_I32, [_P, _P, _P, _P, _P]),
     "dmn_mlp_features": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _I64, _P]),
+    "dmn_mlp_input": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _I64, _P]),
     "dmn_mlp_targets": (_I32, [_P, _P, _I64, _P, _P, _I64, _P]),
     "dmn_mlp_fit_normalization": (_I32, [_P, _P, _I64, _P, _P]),
     "dmn_mlp_normalize_features": (_I32, [_P, _P, _I64, _P, _P]),

@@ -55,6 +55,21 @@ class MLP:
                                        _dev(out, torch.float32, (n, self.n_in), "feat")), "dmn_mlp_features")
         return out
 
+    def input(self, deps, theta, state_in, state_prev=None, out=None, stream=None):
+        """Normalised bf16 network input in one pass (``dmn_mlp_input``)."""
+        import torch
+        n = deps.shape[0]
+        if out is None:
+            out = torch.empty((n, self.n_in_pad), dtype=torch.bfloat16, device=deps.device)
+        sw = state_in.shape[1]
+        prev = ctypes.c_void_p(0) if state_prev is None else _dev(state_prev, torch.float64, (n, sw), "state_prev")
+        _check(load().dmn_mlp_input(self._h, _stream_ptr(stream), n,
+                                    _dev(deps, torch.float64, (n, 6), "deps"),
+                                    _dev(theta, torch.float64, (n,), "theta"),
+                                    _dev(state_in, torch.float64, (n, sw), "state_in"), prev, sw,
+                                    _dev(out, torch.bfloat16, (n, self.n_in_pad), "x")), "dmn_mlp_input")
+        return out
+
     def targets(self, state_in, state_out, out=None, stream=None):
         import torch
         n, sw = state_in.shape

@@ -175,7 +175,10 @@ def test_warm_start_gain_on_the_k8_random_walk():
     it_plain, it_warm, fallbacks = [], [], 0
     for k in range(n_train, n_train + n_eval):
         sp, si, ref = hist[k]
-        da = net.predict(net.normalize_features(net.features(D[k], T[k], si, sp)))
+        x1 = net.normalize_features(net.features(D[k], T[k], si, sp))
+        x2 = net.input(D[k], T[k], si, sp)  # fused path used in the solve loop
+        assert torch.equal(x1, x2)
+        da = net.predict(x2)
         _, op, stp, itp = mixed.eval(D[k], T[k], 1.0, si)
         _, ow, stw, itw = mixed.eval_warm(D[k], T[k], 1.0, si, da)
         torch.cuda.synchronize()
