@@ -101,10 +101,16 @@ typedef struct {
                            residual, the convergence test and every output
                            accumulation in FP64-class precision (float-float
                            on the FP32 pipe, about 48 significant bits)          */
-  int32_t solve_variant; /* kernel variant of the solve (0 = library default;
-                           2, 3, 4 = mixed-precision kernel compiled for that
-                           many resident CTAs per SM at depth K <= 8); chosen
-                           by the autotuner, ignored where it does not apply  */
+  int32_t solve_variant; /* kernel variant of the solve, depth K <= 8 (deeper
+                           trees always take the default).  0 = library
+                           default (owner-mapped kernel; mixed: 3 CTAs/SM);
+                           2, 3, 4 = owner-mapped mixed kernel compiled for
+                           that many resident CTAs per SM; 11 = compact kernel
+                           (upper tree levels on one warp, strains updated by
+                           the Newton step), FP64 (mixed: as 12); 12, 13 =
+                           compact mixed kernel for 2 or 3 CTAs per SM.  The
+                           2..4 choice has no effect in FP64.  Any other value
+                           is DMN_ERR_ARG.  Chosen by the autotuner          */
 } dmn_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -1,11 +1,15 @@
 """Autotuner for the solve kernel's launch mapping.
 
-The mixed-precision solve is compiled in several variants that differ in the
-number of CTAs per SM the compiler is asked to fit (register budget per
-thread: 65536 / (128 * variant)).  The best one depends on the tree depth and
-on how many Newton iterations the workload takes, so it is measured: every
-variant runs the same synthetic increments and the fastest is written to a
-JSON table that ``DMN`` consults when no variant is given.
+The solve is compiled in several variants: two kernel forms (owner-mapped
+tree sweeps; compact upper levels with incrementally updated strains) and,
+for the mixed precision, several numbers of CTAs per SM the compiler is asked
+to fit (register budget per thread: 65536 / (128 * CTAs)).  The best one
+depends on the tree depth and on how many Newton iterations the workload
+takes, so it is measured: every variant runs the same synthetic increments
+and the fastest is written to a JSON table that ``DMN`` consults when no
+variant is given.  Variant numbers are those of ``dmn_options.solve_variant``:
+2, 3, 4 owner-mapped mixed; 12, 13 compact mixed; 0 owner-mapped FP64; 11
+compact FP64.
 
 Usage (on a GPU):  python -m paper_2109_14403_gb300.autotune [--K 8] [--points 65536]
 """
@@ -16,7 +20,7 @@ import json
 import os
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
-VARIANTS = (2, 3, 4)
+VARIANTS = {"mixed": (2, 3, 4, 12, 13), "fp64": (0, 11)}
 
 
 def key(K: int, precision: str) -> str:
@@ -56,7 +60,7 @@ def tune(K: int = 8, n_points: int = 65536, n_steps: int = 4, warmup: int = 2,
     D = torch.tensor(deps, device=dev)
     T = torch.tensor(theta, device=dev)
     times = {}
-    for v in VARIANTS:
+    for v in VARIANTS[precision]:
         d = DMN(K, w, nrm, ph, syn.materials(), precision=precision, solve_variant=v)
         s = d.init_state(torch.full((n_points,), syn.THETA_START, dtype=torch.float64, device=dev))
         s2 = torch.empty_like(s)

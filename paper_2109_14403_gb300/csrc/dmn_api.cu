@@ -87,6 +87,9 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   if (!(o.tol > 0.0) || !(o.gamma > 0.0 && o.gamma < 1.0) || o.maxit < 1 || o.maxbacktrack < 0 ||
       (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED))
     return fail(DMN_ERR_ARG, "dmn_create: invalid options");
+  if (!solve_variant_valid(o.solve_variant))
+    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4, 11, 12, 13}",
+                o.solve_variant);
   const int nleaf = 1 << K, N = nleaf - 1;
 
   // materials: derived bulk and shear moduli (Sec. 4: K = E/(3(1-2nu)), G = E/(2(1+nu)))
@@ -200,14 +203,10 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
   const bool mixed = o.precision == DMN_PREC_MIXED;
-  if (o.solve_variant != 0 && (o.solve_variant < 2 || o.solve_variant > 4)) {
-    free_handle(h);
-    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4}", o.solve_variant);
-  }
   {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (solve_smem_bytes(K, nz, n_mats, mixed) > (size_t)smem_optin) {
+    if (solve_smem_bytes(K, nz, n_mats, mixed, o.solve_variant) > (size_t)smem_optin) {
       free_handle(h);
       return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
     }

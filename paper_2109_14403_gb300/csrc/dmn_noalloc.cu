@@ -78,7 +78,7 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   if (opt) o = *opt; else dmn_default_options(&o);
   if (!(o.tol > 0.0) || !(o.gamma > 0.0 && o.gamma < 1.0) || o.maxit < 1 || o.maxbacktrack < 0 ||
       (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED) ||
-      (o.solve_variant != 0 && (o.solve_variant < 2 || o.solve_variant > 4)))
+      !solve_variant_valid(o.solve_variant))
     return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: invalid options");
 
   const int nleaf = 1 << K, N = nleaf - 1;
@@ -210,7 +210,7 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   int num_sms = 0, smem_optin = 0, blocks_per_sm = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (solve_smem_bytes(K, nz, n_mats, mixed) > (size_t)smem_optin)
+  if (solve_smem_bytes(K, nz, n_mats, mixed, o.solve_variant) > (size_t)smem_optin)
     return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: K=%d does not fit one SM in this precision", K);
   e = prepare_solve(K, nz, n_mats, mixed, o.solve_variant, &blocks_per_sm);
   if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "prepare_solve: %s", cudaGetErrorString(e));

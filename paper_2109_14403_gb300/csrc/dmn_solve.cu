@@ -1,98 +1,10 @@
 // dmn_solve.cu -- the Newton solve of Algorithm 1 (arXiv 2109.14403, Sec. 3.3)
 // for one Gauss point per CTA.  See dmn_kernels.cuh for the mapping and the
 // condensation.
-#include "dmn_kernels.cuh"
 #include "dmn_internal.h"
+#include "solve_common.cuh"
 
 namespace dmn {
-
-enum { ACT_STEP = 0, ACT_BACK = 1, ACT_DONE = 2 };
-
-template <typename TF>
-struct Ctrl {
-  TF res, res_old, gi, pad0_;
-  unsigned long long next;  // point taken from the queue
-  int action, it, bt, status, first, nonfinite, pad_[2];
-};
-
-__device__ __forceinline__ unsigned group_mask(int G) {
-  return G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
-}
-// shuffle segment width: a point with fewer than 32 threads is one segment
-__device__ __forceinline__ int group_width(int G) { return G >= 32 ? 32 : G; }
-
-// ------------------------------------------------------------------ node constants
-template <typename HP>
-struct NodeHP {
-  HP n[3], ns[3], c1, c2;  // normal, normal / sqrt2, volume fractions
-};
-__device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<double> &o) {
-  const double *r = P.node + kNodeWords * p;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    o.n[i] = __ldg(r + i);
-    o.ns[i] = __ldg(r + 8 + i);
-  }
-  o.c1 = __ldg(r + 3);
-  o.c2 = __ldg(r + 4);
-}
-__device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<dfl> &o) {
-  const float4 *r = reinterpret_cast<const float4 *>(P.node_df + kNodeDfl * p);
-  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
-  o.n[0] = {a.x, a.y};
-  o.n[1] = {a.z, a.w};
-  o.n[2] = {b.x, b.y};
-  o.ns[0] = {b.z, b.w};
-  o.ns[1] = {c.x, c.y};
-  o.ns[2] = {c.z, c.w};
-  o.c1 = {d.x, d.y};
-  o.c2 = {d.z, d.w};
-}
-// normal, c1, c2, 1/(w c1 c2), w c1 c2 in the condensation precision
-__device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, double n[3], double &c1,
-                                             double &c2, double &iwcc, double &wcc) {
-  const double *r = P.node + kNodeWords * p;
-  n[0] = __ldg(r);
-  n[1] = __ldg(r + 1);
-  n[2] = __ldg(r + 2);
-  c1 = __ldg(r + 3);
-  c2 = __ldg(r + 4);
-  wcc = __ldg(r + 6);
-  iwcc = __ldg(r + 7);
-}
-__device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, float n[3], float &c1,
-                                             float &c2, float &iwcc, float &wcc) {
-  const float *r = P.node_df + kNodeDfl * p;
-  n[0] = __ldg(r);
-  n[1] = __ldg(r + 2);
-  n[2] = __ldg(r + 4);
-  c1 = __ldg(r + 12);
-  c2 = __ldg(r + 14);
-  iwcc = __ldg(r + 16);
-  wcc = __ldg(r + 17);
-}
-__device__ __forceinline__ double hp_add_tf(double a, double d) { return a + d; }
-__device__ __forceinline__ dfl hp_add_tf(dfl a, float d) { return a + dfl{d, 0.0f}; }
-
-// B a = sym(a (x) n) with the pre-scaled normal ns = n / sqrt2
-template <typename HP>
-__device__ __forceinline__ void bvec_hp(const NodeHP<HP> &nd, const HP a[3], HP out[6]) {
-  out[0] = a[0] * nd.n[0];
-  out[1] = a[1] * nd.n[1];
-  out[2] = a[2] * nd.n[2];
-  out[3] = a[1] * nd.ns[2] + a[2] * nd.ns[1];
-  out[4] = a[0] * nd.ns[2] + a[2] * nd.ns[0];
-  out[5] = a[0] * nd.ns[1] + a[1] * nd.ns[0];
-}
-
-// B^T s = s n (traction) in HP; the cancellation of the residual happens
-// here, so it must run in the high precision before any rounding to TF
-template <typename HP>
-__device__ __forceinline__ void btvec_hp(const NodeHP<HP> &nd, const HP s[6], HP out[3]) {
-  out[0] = s[0] * nd.n[0] + s[5] * nd.ns[1] + s[4] * nd.ns[2];
-  out[1] = s[1] * nd.n[1] + s[5] * nd.ns[0] + s[3] * nd.ns[2];
-  out[2] = s[2] * nd.n[2] + s[4] * nd.ns[0] + s[3] * nd.ns[1];
-}
 
 // Top-down back-substitution of the Newton increment (owner mapping):
 // da_p = -(G_p de_p + h_p); children de_1 = de + c2 B da, de_2 = de - c1 B da.
@@ -154,14 +66,6 @@ __device__ __forceinline__ void back_substitute(const SolveParams &P, TF *da_s, 
       }
     }
   }
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v, unsigned mask, int W) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    if (o < W) v = v + hp_shfl_down(mask, v, o, W);
-  return v;
 }
 
 // One Newton pass ("Residual" of Algorithm 1 plus the condensation):
@@ -527,7 +431,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   }
 }
 
-size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed) {
+static size_t owner_smem_bytes(int K, int nz, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const int nslot = G >= 64 ? G / 64 : 1;
   const size_t hp = 8;  // double or float-float
@@ -539,9 +443,18 @@ size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed) {
   return (b + 15) & ~size_t(15);
 }
 
-// kernel variants: (precision, threads bound, CTAs per SM requested)
-using KernelFn = void (*)(const SolveParams);
+// kernel variants: (form, precision, threads bound, CTAs per SM requested).
+// 0 = default; 2..4 = owner-mapped mixed kernel for that many CTAs per SM;
+// 10 + m = compact kernel (dmn_solve_compact.cu), mixed compiled for m = 2 or
+// 3 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 always takes the
+// owner-mapped 512-thread kernel.
+bool solve_variant_valid(int variant) {
+  return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 13);
+}
+static bool is_compact(int K, int variant) { return K <= 8 && variant >= 11; }
+
 static KernelFn pick(int K, bool mixed, int variant) {
+  if (is_compact(K, variant)) return compact_kernel(K, mixed, variant - 10);
   if (K > 8) return mixed ? dmn_solve_kernel<float, dfl, 512, 1> : dmn_solve_kernel<double, double, 512, 1>;
   if (!mixed) return dmn_solve_kernel<double, double, 128, 1>;
   switch (variant) {
@@ -551,10 +464,13 @@ static KernelFn pick(int K, bool mixed, int variant) {
   }
 }
 
-int solve_variant_count() { return 3; }
+size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed, int variant) {
+  return is_compact(K, variant) ? compact_smem_bytes(K, nz, n_mats, mixed)
+                                : owner_smem_bytes(K, nz, n_mats, mixed);
+}
 
 cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm) {
-  const size_t smem = solve_smem_bytes(K, nz, n_mats, mixed);
+  const size_t smem = solve_smem_bytes(K, nz, n_mats, mixed, variant);
   KernelFn f = pick(K, mixed, variant);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -562,7 +478,7 @@ cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, in
 }
 
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s) {
-  const size_t smem = solve_smem_bytes(P.K, P.nz, P.n_mats, mixed);
+  const size_t smem = solve_smem_bytes(P.K, P.nz, P.n_mats, mixed, variant);
   cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   pick(P.K, mixed, variant)<<<grid, P.G, smem, s>>>(P);

@@ -1,0 +1,524 @@
+// dmn_solve_compact.cu -- second form of the Algorithm 1 solve (arXiv
+// 2109.14403, Sec. 3.3): one CTA per Gauss point, G = 2^(K-1) threads, with
+//  * incremental strains: the strains of the bottom laminates live in shared
+//    memory and are updated by the Newton back-substitution itself, which
+//    carries the strain increments de in the high precision HP (float-float in
+//    the mixed path) from the exact FP32 jump increments da; the top-down strain
+//    scatter (eq. DMN kinematics) runs once per point, not once per pass;
+//  * compact levels: the laminates just above the bottom pair neighbouring
+//    lanes by shuffle; every higher level puts node j of the level on thread j,
+//    with the children's condensed records and stress sums in shared memory,
+//    so an upper level occupies one warp, not every warp;
+//  * the back-substitution compact in the same way, one barrier per level.
+// The condensation, the residual and the leaf laws are those of
+// dmn_kernels.cuh.  The internal variables of the current pass are parked in
+// the caller's output state (same 8-byte slots) and converted at the end.
+#include "dmn_internal.h"
+#include "solve_common.cuh"
+
+namespace dmn {
+
+namespace {
+constexpr int RS = 41;  // record stride in shared memory (40 values, odd)
+
+template <typename TF>
+__device__ __forceinline__ void rec_put(TF *s, const Rec<TF> &r) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) s[q] = r.C[q];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    s[21 + c] = r.ds[c];
+    s[27 + c] = r.tau[c];
+    s[33 + c] = r.dd[c];
+  }
+  s[39] = r.gg;
+}
+template <typename TF>
+__device__ __forceinline__ void rec_get(Rec<TF> &r, const TF *s) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) r.C[q] = s[q];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    r.ds[c] = s[21 + c];
+    r.tau[c] = s[27 + c];
+    r.dd[c] = s[33 + c];
+  }
+  r.gg = s[39];
+}
+
+__host__ __device__ constexpr int half_or_one(int G) { return G >= 2 ? G / 2 : 1; }
+__host__ __device__ constexpr int quarter_or_one(int G) { return G >= 4 ? G / 4 : 1; }
+}  // namespace
+
+template <typename TF, typename HP, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
+  const int t = threadIdx.x;
+  const int GX = half_or_one(G), GY = quarter_or_one(G);
+  HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
+  HP *eK = a_s + 3 * N;                        // 6G   strains of the bottom laminates
+  HP *deK = eK + 6 * G;                        // 6G   their increment in the last Newton step
+  HP *zn_s = deK + 6 * G;                      // 7 NZ internal variables at t^n
+  HP *Sx = zn_s + 7 * NZ;                      // 6 GX subtree stress sums (levels K-1, K-3, ...)
+  HP *Sy = Sx + 6 * GX;                        // 6 GY (levels K-2, K-4, ...)
+  HP *eb = Sy + 6 * GY;                        // 12: eps_bar^{n+1}, deps
+  HP *sroot = eb + 12;                         // 6: sigma_bar of the last pass
+  HP *redD = sroot + 6;                        // 32
+  HP *redX = redD + 32;                        // 32
+  HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
+  MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(misc + 4);
+  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(
+      (reinterpret_cast<uintptr_t>(mp_s + P.n_mats) + 15) & ~uintptr_t(15));
+  TF *red = reinterpret_cast<TF *>(ctrl + 1);  // 32
+  TF *orec = red + 32;                         // 40
+  TF *da_s = orec + 40;                        // 3N  Newton increment
+  TF *gh_s = da_s + 3 * N;                     // 21N G_p, h_p
+  TF *recX = gh_s + 21 * N;                    // RS GX records (levels K-1, K-3, ...)
+  TF *recY = recX + ((RS * GX + 1) & ~1);      // RS GY records (levels K-2, K-4, ...)
+  HP *tag = nullptr;
+  // the record buffers double as high-precision level buffers for the strain
+  // sweeps (at least 6 HP per entry fit: RS TF >= 6 HP for both precisions)
+  HP *hX = reinterpret_cast<HP *>(recX);  // 2 GX entries of 6 HP
+  HP *hY = reinterpret_cast<HP *>(recY);  // 2 GY entries of 6 HP
+  // compact condensation: level k (K-1 >= k >= 1) in X if (K-1-k) is even
+  auto recbuf = [&](int k) { return ((K - 1 - k) & 1) ? recY : recX; };
+  auto sbuf = [&](int k) { return ((K - 1 - k) & 1) ? Sy : Sx; };
+  // strain sweeps: level k (k >= 2) in X if (K - k) is even (level K: G entries)
+  auto ebuf = [&](int k) { return ((K - k) & 1) ? hY : hX; };
+
+  const unsigned mask = group_mask(G);
+  const int W = group_width(G);
+  const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
+
+  for (int i = t; i < P.n_mats; i += G)
+    mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
+  if (t == 0) misc[0] = hp_from(1.0 / P.dt, tag);
+  const TF idt_f = TF(1.0 / P.dt);
+  const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
+
+  const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
+  const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
+  const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
+  const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
+
+  // top-down strain sweep from the root strain (eq. DMN kinematics): node j of
+  // level k on thread j; the bottom laminates' strains end in eK
+  auto scatter = [&](const HP *root) {
+    HP *top = K == 1 ? eK : ebuf(1);
+    for (int c = t; c < 6; c += G) top[c] = root[c];
+    __syncthreads();
+    for (int k = 1; k <= K - 1; ++k) {
+      if (t < (1 << (k - 1))) {
+        const int p = (1 << K) - (1 << k) + t;
+        const HP *ep = ebuf(k) + 6 * t;
+        HP *ec = (k + 1 == K ? eK : ebuf(k + 1)) + 12 * t;
+        NodeHP<HP> nd;
+        load_node(P, p, nd);
+        const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
+        HP J[6];
+        bvec_hp(nd, av, J);
+        HP e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] = ep[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          ec[c] = e[c] + nd.c2 * J[c];
+          ec[6 + c] = e[c] - nd.c1 * J[c];
+        }
+      }
+      __syncthreads();
+    }
+  };
+
+  for (;;) {
+    if (t == 0) ctrl->next = atomicAdd(P.queue, 1ull);
+    __syncthreads();
+    const int64_t pt = int64_t(ctrl->next);
+    if (pt >= P.n_points) break;
+    const double *sin = P.sin + pt * P.SW;
+    double *sout = P.sout + pt * P.SW;
+    HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
+    const double theta = P.theta[pt];
+    for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
+    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_load(sin[8 + 3 * N + i], tag);
+    for (int c = t; c < 6; c += G) {
+      const double d = P.deps[pt * 6 + c];
+      eb[c] = hp_load(sin[c] + d, tag);
+      eb[6 + c] = hp_load(d, tag);
+    }
+    __syncthreads();
+    for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
+    if (t == 0) {
+      ctrl->first = 1;
+      ctrl->it = 0;
+      ctrl->bt = 0;
+      ctrl->gi = TF(1);
+      ctrl->res_old = TF(0);
+      ctrl->status = 0;
+    }
+    const HP *zn0 = zq0 >= 0 ? zn_s + zq0 : nullptr;
+    const HP *zn1 = zq1 >= 0 ? zn_s + zq1 : nullptr;
+    HP *zw0 = zq0 >= 0 ? zw + zq0 : nullptr;
+    HP *zw1 = zq1 >= 0 ? zw + zq1 : nullptr;
+
+    HP trn0 = hp_zero(tag), trn1 = hp_zero(tag);
+    bool first = true;  // the first pass also yields the traces of eps^n
+    if (P.da0) {
+      // warm start a^n + da0: the traces of eps^n from a sweep at a^n
+      HP ebn[6];
+      for (int c = 0; c < 6; ++c) ebn[c] = hp_load(sin[c], tag);
+      scatter(ebn);
+      NodeHP<HP> nd;
+      load_node(P, t, nd);
+      const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
+      HP J[6];
+      bvec_hp(nd, av, J);
+      const HP trj = J[0] + J[1] + J[2];
+      const HP tre = eK[6 * t] + eK[6 * t + 1] + eK[6 * t + 2];
+      trn0 = tre + nd.c2 * trj;
+      trn1 = tre - nd.c1 * trj;
+      first = false;
+      __syncthreads();
+      const float *d0 = P.da0 + pt * (3 * N);
+      for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], TF(d0[i]));
+      __syncthreads();
+    }
+    scatter(eb);  // strains of the bottom laminates at the starting a
+    int attempt = 0, it_total = 0;
+    HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
+    Rec<TF> rec;
+    for (;;) {
+      // ---- R2: leaves and laminate t ----
+      TF r2;
+      HP S[6];
+      {
+        NodeHP<HP> nd;
+        load_node(P, t, nd);
+        HP el[6], er[6];
+        {
+          const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
+          HP J[6];
+          bvec_hp(nd, av, J);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const HP e = eK[6 * t + c];
+            el[c] = e + nd.c2 * J[c];
+            er[c] = e - nd.c1 * J[c];
+          }
+        }
+        if (first) {  // at a = a^n: eps^n = eps - deps
+          const HP trd = eb[6] + eb[7] + eb[8];
+          trn0 = (el[0] + el[1] + el[2]) - trd;
+          trn1 = (er[0] + er[1] + er[2]) - trd;
+        }
+        HP sl[6], sr[6], DL, DR, XL, XR;
+        Rec<TF> rr;
+        leaf_eval<TF, HP>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+        leaf_eval<TF, HP>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
+        Dsum = wL * DL + wR * DR;
+        Xsum = wL * XL + wR * XR;
+        HP dsh[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          S[c] = wL * sl[c] + wR * sr[c];
+          dsh[c] = sl[c] - sr[c];
+        }
+        HP rbh[3];
+        btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_t / (w c1 c2)
+        TF n[3], c1, c2, iwcc, wcc;
+        load_node_tf(P, t, n, c1, c2, iwcc, wcc);
+        const TF rbv[3] = {tf_of(rbh[0], (TF *)nullptr), tf_of(rbh[1], (TF *)nullptr),
+                           tf_of(rbh[2], (TF *)nullptr)};
+        r2 = wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
+        combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t);
+      }
+      // ---- level K-1: neighbouring lanes (2j, 2j+1) ----
+      if (K >= 2) {
+        Rec<TF> other;
+        rec_shfl_down(other, rec, 1, mask, W);
+        HP So[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) So[c] = hp_shfl_down(mask, S[c], 1, W);
+        if ((t & 1) == 0) {
+          const int j = t >> 1;
+          const int p = (1 << K) - (1 << (K - 1)) + j;
+          NodeHP<HP> nd;
+          load_node(P, p, nd);
+          HP dh[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            dh[c] = nd.c2 * S[c] - nd.c1 * So[c];
+            S[c] = S[c] + So[c];
+          }
+          HP rh[3];
+          btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
+          TF n[3], c1, c2, iwcc, wcc;
+          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+          const TF rv[3] = {tf_of(rh[0], (TF *)nullptr), tf_of(rh[1], (TF *)nullptr),
+                            tf_of(rh[2], (TF *)nullptr)};
+          r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
+          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
+          if (K >= 3) {
+            rec_put(recX + RS * j, rec);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Sx[6 * j + c] = S[c];
+          }
+        }
+      }
+      // ---- levels K-2 .. 1: node j on thread j.  Once the producers of the
+      //      level below all sit in warp 0, warp 0 goes on alone with warp
+      //      barriers and the other warps move to the reduction barrier ----
+      for (int k = K - 2; k >= 1; --k) {
+        const int prod = k + 1 == K - 1 ? G : (1 << k);  // threads that wrote level k+1
+        if (prod > 32) {
+          __syncthreads();
+        } else {
+          if (warp != 0) break;
+          __syncwarp(mask);
+        }
+        if (t < (1 << (k - 1))) {
+          const int p = (1 << K) - (1 << k) + t;
+          const TF *rc = recbuf(k + 1) + RS * (2 * t);
+          const HP *sc = sbuf(k + 1) + 12 * t;
+          Rec<TF> other;
+          rec_get(rec, rc);
+          rec_get(other, rc + RS);
+          NodeHP<HP> nd;
+          load_node(P, p, nd);
+          HP dh[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const HP SL = sc[c], SR = sc[6 + c];
+            S[c] = SL + SR;
+            dh[c] = nd.c2 * SL - nd.c1 * SR;
+          }
+          HP rh[3];
+          btvec_hp(nd, dh, rh);
+          TF n[3], c1, c2, iwcc, wcc;
+          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+          const TF rv[3] = {tf_of(rh[0], (TF *)nullptr), tf_of(rh[1], (TF *)nullptr),
+                            tf_of(rh[2], (TF *)nullptr)};
+          r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
+          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
+          if (k > 1) {
+            rec_put(recbuf(k) + RS * t, rec);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sbuf(k)[6 * t + c] = S[c];
+          }
+        }
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sroot[c] = S[c];  // thread 0 holds the root
+      }
+      // ---- residual norm, decision (Algorithm 1) ----
+      r2 = warp_sum(r2, mask, W);
+      const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
+      if (lane == 0) {
+        red[warp] = r2;
+        redD[warp] = ds_;
+        redX[warp] = xs_;
+      }
+      __syncthreads();
+      if (t == 0) {
+        TF s = TF(0);
+        for (int w = 0; w < nwarp; ++w) s += red[w];
+        TF sn = TF(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const TF v = tf_of(sroot[c], (TF *)nullptr);
+          sn += v * v;
+        }
+        TF den = sqrt(sn);
+        if (den < res_floor) den = res_floor;
+        const TF res = sqrt(s) / (TF(N) * den);
+        Ctrl<TF> &c = *ctrl;
+        const bool accept = c.first || (res < c.res_old) || (c.bt >= P.maxbt);
+        int action;
+        if (accept) {
+          if (!isfinite(res)) {
+            c.status = 2;
+            action = ACT_DONE;
+          } else if (!c.first && res < tol) {
+            c.status = 0;
+            action = ACT_DONE;
+          } else if (c.it >= P.maxit) {
+            c.status = 1;
+            action = ACT_DONE;
+          } else {
+            c.res_old = res;
+            c.it += 1;
+            c.bt = 0;
+            c.gi = TF(1);
+            action = ACT_STEP;
+          }
+          c.first = 0;
+        } else {
+          action = ACT_BACK;
+        }
+        c.res = res;
+        c.action = action;
+      }
+      first = false;
+      __syncthreads();
+      const int action = ctrl->action;
+      if (action == ACT_DONE) {
+        if (P.da0 && attempt == 0 && ctrl->status != 0) {
+          // warm-started iteration failed: run Algorithm 1 again from a^n
+          attempt = 1;
+          it_total = ctrl->it;
+          for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
+          __syncthreads();  // every thread has read ctrl->status and ctrl->it
+          if (t == 0) {
+            ctrl->first = 1;
+            ctrl->it = 0;
+            ctrl->bt = 0;
+            ctrl->gi = TF(1);
+            ctrl->res_old = TF(0);
+            ctrl->status = 0;
+          }
+          scatter(eb);  // its first barrier orders the reset before later reads
+          continue;
+        }
+        break;
+      }
+      if (action == ACT_STEP) {
+        // ---- back-substitution, node j of level k on thread j:
+        //      da_p = -(G_p de_p + h_p); children de + c2 B da, de - c1 B da (HP)
+        for (int k = 1; k <= K; ++k) {
+          if (t < (1 << (k - 1))) {
+            const int p = (1 << K) - (1 << k) + t;
+            HP de[6];
+            if (k == 1) {
+#pragma unroll
+              for (int c = 0; c < 6; ++c) de[c] = hp_zero(tag);
+            } else {
+              const HP *src = (k == K ? hX : ebuf(k)) + 6 * t;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) de[c] = src[c];
+            }
+            const TF *g = gh_s + 21 * p;
+            TF da[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              TF s = g[18 + r];
+#pragma unroll
+              for (int c = 0; c < 6; ++c) s += g[6 * r + c] * tf_of(de[c], (TF *)nullptr);
+              da[r] = -s;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              da_s[3 * p + r] = da[r];
+              a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
+            }
+            if (k < K) {
+              NodeHP<HP> nd;
+              load_node(P, p, nd);
+              const HP dah[3] = {hp_add_tf(hp_zero(tag), da[0]), hp_add_tf(hp_zero(tag), da[1]),
+                                 hp_add_tf(hp_zero(tag), da[2])};
+              HP J[6];
+              bvec_hp(nd, dah, J);
+              HP *dst = (k + 1 == K ? hX : ebuf(k + 1)) + 12 * t;
+#pragma unroll
+              for (int c = 0; c < 6; ++c) {
+                dst[c] = de[c] + nd.c2 * J[c];
+                dst[6 + c] = de[c] - nd.c1 * J[c];
+              }
+            } else {
+#pragma unroll
+              for (int c = 0; c < 6; ++c) {
+                eK[6 * t + c] = eK[6 * t + c] + de[c];
+                deK[6 * t + c] = de[c];
+              }
+            }
+          }
+          // level k+1 is read by threads < 2^k: a warp barrier while they
+          // all sit in warp 0 (the other warps wait at the next block barrier)
+          if (k == K || (1 << k) > 32) __syncthreads();
+          else if (warp == 0) __syncwarp(mask);
+        }
+      } else {
+        // ---- backtracking: a -= f da, strains -= f de ----
+        const TF f = ctrl->gi * (TF(1) - gamma);
+        const HP fh = hp_add_tf(hp_zero(tag), -f);
+        for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
+        for (int i = t; i < 6 * G; i += G) eK[i] = eK[i] + fh * deK[i];
+        __syncthreads();
+        if (t == 0) {
+          ctrl->gi *= gamma;
+          ctrl->bt += 1;
+        }
+      }
+    }
+
+    // ---- outputs and state (the last pass is at the final a) ----
+    if (t == 0) {
+#pragma unroll
+      for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        orec[21 + c] = rec.tau[c];
+        orec[27 + c] = rec.dd[c];
+      }
+      orec[33] = rec.gg;
+      HP Db = redD[0], Xb = redX[0];
+      for (int w = 1; w < nwarp; ++w) {
+        Db = Db + redD[w];
+        Xb = Xb + redX[w];
+      }
+      misc[1] = Db;
+      misc[2] = Xb;
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int c = t; c < kOutWords; c += G) {
+      double v;
+      if (c < 6) v = hp_to(sroot[c]);
+      else if (c < 42) v = double(sget(orec, (c - 6) / 6, (c - 6) % 6));
+      else if (c < 48) v = double(orec[21 + c - 42]);
+      else if (c == 48) v = hp_to(misc[1]);
+      else if (c < 55) v = double(orec[27 + c - 49]);
+      else if (c == 55) v = double(orec[33]);
+      else v = hp_to(misc[2]);
+      if (!isfinite(v)) bad = 1;
+      P.out[pt * kOutWords + c] = v;
+    }
+    bad = __syncthreads_or(bad);
+    if (t == 0) {
+      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
+      P.iters[pt] = ctrl->it + it_total;
+    }
+    for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
+      sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);
+    for (int i = t; i < 3 * N; i += G) sout[8 + i] = hp_to(a_s[i]);
+    for (int i = t; i < 7 * NZ; i += G) {  // parked internal variables -> FP64 in place
+      const HP v = zw[i];
+      sout[8 + 3 * N + i] = hp_to(v);
+    }
+    for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
+    __syncthreads();
+  }
+}
+
+size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed) {
+  const int N = (1 << K) - 1, G = 1 << (K - 1);
+  const int GX = half_or_one(G), GY = quarter_or_one(G);
+  const size_t hp = 8, tf = mixed ? 4 : 8;
+  size_t b = hp * (3 * N + 12 * G + 7 * nz + 6 * GX + 6 * GY + 12 + 6 + 64 + 4);
+  b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
+  b = (b + 15) & ~size_t(15);
+  b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
+  b += tf * (32 + 40 + 24 * N + ((RS * GX + 1) & ~1) + RS * GY);
+  return (b + 15) & ~size_t(15);
+}
+
+KernelFn compact_kernel(int K, bool mixed, int minb) {
+  (void)K;  // depth <= 8: at most 128 threads
+  if (!mixed) return dmn_solve_compact<double, double, 128, 1>;
+  return minb >= 3 ? dmn_solve_compact<float, dfl, 128, 3> : dmn_solve_compact<float, dfl, 128, 2>;
+}
+
+}  // namespace dmn

@@ -145,7 +145,7 @@ class DMN:
         opt.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         if solve_variant is None:  # the autotuner's choice, if it ran for this case
             from .autotune import lookup
-            solve_variant = lookup(self.K, precision) if self.K <= 8 and precision == "mixed" else 0
+            solve_variant = lookup(self.K, precision) if self.K <= 8 else 0
         opt.solve_variant = int(solve_variant)
         self.solve_variant = int(solve_variant)
         self.precision = precision

@@ -33,8 +33,8 @@ def rel(a, b, floor):
     return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), floor)
 
 
-def compare(out, out_o, prec, sel=slice(None)):
-    t = TOL[prec]
+def compare(out, out_o, prec, sel=slice(None), tol=None):
+    t = TOL[prec] if tol is None else tol[prec]
     g, o = oracle.split_out(out[sel]), oracle.split_out(out_o)
     assert rel(g["sig"], o["sig"], 1e-3).max() < t["sig"]
     assert rel(g["C"].reshape(-1, 36), o["C"].reshape(-1, 36), 1.0).max() < t["tan"]
@@ -47,12 +47,12 @@ def compare(out, out_o, prec, sel=slice(None)):
     assert np.abs(g["diss"] - o["diss"]).max() <= t["scal"] * sc
 
 
-def run_path(K, prec, deps, theta, n_check=None, dt=1.0, tree_seed=None, mats=None):
+def run_path(K, prec, deps, theta, n_check=None, dt=1.0, tree_seed=None, mats=None, variant=None):
     dev = _dev()
     from paper_2109_14403_gb300 import DMN
     mats = syn.materials() if mats is None else mats
     w, nrm, ph = syn.tree(K, tree_seed)
-    d = DMN(K, w, nrm, ph, mats, tol=1e-12, precision=prec)
+    d = DMN(K, w, nrm, ph, mats, tol=1e-12, precision=prec, solve_variant=variant)
     tree = oracle.Tree(K, w, nrm, ph, mats)
     n = deps.shape[1]
     s = d.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
@@ -107,6 +107,44 @@ def test_k8_full_batch_sampled(prec):
     configuration; the oracle checks 96 sampled points."""
     deps, theta = syn.random_walk_k8(n_points=65536, n_incr=2)
     run_path(8, prec, deps, theta, n_check=96)
+
+
+# the compact kernel form (incremental strains, compact upper levels): FP64
+# variant 11, mixed variants 12 and 13 (2 or 3 CTAs per SM)
+COMPACT = [("fp64", 11), ("mixed", 12), ("mixed", 13)]
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("prec,variant", COMPACT)
+def test_compact_kernel_depths(K, prec, variant):
+    rng = np.random.default_rng(200 + K)
+    n = 37
+    deps = rng.normal(0, 3e-3, size=(3, n, 6))
+    theta = 293.0 + np.cumsum(rng.uniform(0, 5, size=(3, n)), axis=0)
+    run_path(K, prec, deps, theta, dt=0.7, variant=variant)
+
+
+@pytest.mark.parametrize("prec,variant", COMPACT)
+def test_compact_kernel_k8_backtracking_walk(prec, variant):
+    """Large K=8 increments: several Newton iterations and line-search
+    backtracking, which the compact kernel undoes on its stored strains."""
+    deps, theta = syn.random_walk_k8(n_points=200, n_incr=4)
+    run_path(8, prec, deps * 8.0, theta, variant=variant)
+
+
+@pytest.mark.parametrize("prec,variant", [("fp64", 11), ("mixed", 13)])
+def test_compact_kernel_k8_full_batch_sampled(prec, variant):
+    deps, theta = syn.random_walk_k8(n_points=65536, n_incr=2)
+    run_path(8, prec, deps, theta, n_check=96, variant=variant)
+
+
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("mixed", 0)] + COMPACT)
+def test_backtracking_walk(prec, variant):
+    """K=8 walk scaled by 20: in its second increment the oracle rejects full
+    Newton steps at some points (tests/test_inputs.py checks that), so the
+    line search of Algorithm 1 runs on the GPU too."""
+    deps, theta = syn.random_walk_k8(n_points=200, n_incr=2)
+    run_path(8, prec, deps * 20.0, theta, variant=variant)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -177,12 +215,12 @@ def test_nonfinite_input_is_reported_per_point():
     d.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_deterministic_bits(prec):
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("mixed", 0), ("fp64", 11), ("mixed", 13)])
+def test_deterministic_bits(prec, variant):
     from paper_2109_14403_gb300 import DMN
     dev = _dev()
     w, nrm, ph = syn.tree(8)
-    d = DMN(8, w, nrm, ph, syn.materials(), precision=prec)
+    d = DMN(8, w, nrm, ph, syn.materials(), precision=prec, solve_variant=variant)
     deps, theta = syn.random_walk_k8(n_points=3000, n_incr=1)
     dd = torch.tensor(deps[0] * 8, device=dev)
     th = torch.tensor(theta[0], device=dev)
@@ -191,4 +229,61 @@ def test_deterministic_bits(prec):
     r2 = d.eval(dd, th, 1.0, s)
     for a, b in zip(r1, r2):
         assert torch.equal(a, b)
+    d.close()
+
+
+# A warm-started row stops at another iterate than the oracle's plain path;
+# both lie within Algorithm 1's stopping test, |r| < tol N |sigma_bar|, of the
+# solution, so they differ by about tol * N * (stiffness contrast)
+# = 1e-12 * 63 * 29 ~ 2e-9 in the stress (K = 6); compared with an oracle
+# converged to 1e-14, the bounds below leave a factor 2-3.
+TOL_WARM = {"fp64": dict(sig=5e-9, tan=5e-8, scal=5e-9), "mixed": dict(sig=2e-8, tan=1e-4, scal=2e-8)}
+
+
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("mixed", 0)] + COMPACT)
+def test_warm_start_parity_and_fallback(prec, variant):
+    """dmn_eval_warm from a^n + da: rows 0-7 get a non-finite da (their
+    warm-started iteration fails and is re-run from a^n in the same launch,
+    status bit 4), rows 8-15 da = 0 (the plain start: oracle parity at the
+    plain path's tolerances), the rest the oracle's increment a^{n+1} - a^n
+    perturbed by 5 % (parity within the stopping-criterion bound)."""
+    from paper_2109_14403_gb300 import DMN
+    dev = _dev()
+    K, n = 6, 64
+    w, nrm, ph = syn.tree(K)
+    mats = syn.materials()
+    d = DMN(K, w, nrm, ph, mats, tol=1e-12, precision=prec, solve_variant=variant)
+    tree = oracle.Tree(K, w, nrm, ph, mats)
+    rng = np.random.default_rng(77)
+    deps = rng.normal(0, 3e-3, size=(2, n, 6))
+    theta = 293.0 + np.cumsum(rng.uniform(0, 5, size=(2, n)), axis=0)
+    s = d.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+    so = tree.init_state(n, syn.THETA_START)
+    s, _, st, _ = d.eval(torch.tensor(deps[0], device=dev), torch.tensor(theta[0], device=dev), 0.7, s)
+    so, _, _, _ = oracle.eval_batch(tree, deps[0], theta[0], 0.7, so)
+    so2, out_o, st_o, _ = oracle.eval_batch(tree, deps[1], theta[1], 0.7, so)
+    so3, out_x, st_x, _ = oracle.eval_batch(tree, deps[1], theta[1], 0.7, so, tol=1e-14)
+    asl = slice(8, 8 + 3 * tree.nnode)
+    inc = so2[:, asl] - so[:, asl]
+    da = (inc * (1.0 + 0.05 * rng.standard_normal(inc.shape))).astype(np.float32)
+    da[:8] = np.nan
+    da[8:16] = 0.0
+    D1, T1 = torch.tensor(deps[1], device=dev), torch.tensor(theta[1], device=dev)
+    s2, out, st, it = d.eval_warm(D1, T1, 0.7, s, torch.tensor(da, device=dev))
+    _, out_p, st_p, it_p = d.eval(D1, T1, 0.7, s)
+    st, it, it_p = st.cpu().numpy(), it.cpu().numpy(), it_p.cpu().numpy()
+    assert (st & 3 == 0).all() and (st_o == 0).all() and (st_x == 0).all()
+    assert (st[:8] & 4 != 0).all() and (st[8:] & 4 == 0).all()
+    out_h, s2h = out.cpu().numpy(), s2.cpu().numpy()
+    plain, warm = slice(0, 16), slice(16, n)
+    compare(out_h[plain], out_o[plain], prec)
+    compare(out_h[warm], out_x[warm], prec, tol=TOL_WARM)
+    amax = max(np.abs(so2[:, asl]).max(), 1e-12)
+    assert np.abs(s2h[plain, asl] - so2[plain, asl]).max() <= (1e-8 if prec == "fp64" else 1e-6) * amax
+    assert np.abs(s2h[warm, asl] - so3[warm, asl]).max() <= (1e-7 if prec == "fp64" else 1e-6) * amax
+    # da = 0 is the plain start: same iterations; a non-finite start fails in
+    # its first pass, before any Newton step, so the re-run's count stands
+    assert (it[8:16] == it_p[8:16]).all()
+    assert (it[:8] == it_p[:8]).all()
+    assert it[16:].mean() <= it_p[16:].mean()
     d.close()
