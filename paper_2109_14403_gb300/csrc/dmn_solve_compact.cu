@@ -6,10 +6,13 @@
 //    the mixed path) from the exact FP32 jump increments da; the top-down strain
 //    scatter (eq. DMN kinematics) runs once per point, not once per pass;
 //  * compact levels: the laminates just above the bottom pair neighbouring
-//    lanes by shuffle; every higher level puts node j of the level on thread j,
-//    with the children's condensed records and stress sums in shared memory,
-//    so an upper level occupies one warp, not every warp;
+//    lanes by shuffle; every higher level puts node j of the level on one
+//    thread, with the children's condensed records and stress sums in shared
+//    memory, so a level of at most 32 nodes occupies one warp (the CTA's
+//    leader warp, with warp barriers only) while the other warps go ahead;
 //  * the back-substitution compact in the same way, one barrier per level.
+// The leader warp is picked from the CTA's warp slot so that the CTAs resident
+// on one SM run their single-warp phases on different SM sub-partitions.
 // The condensation, the residual and the leaf laws are those of
 // dmn_kernels.cuh.  The internal variables of the current pass are parked in
 // the caller's output state (same 8-byte slots) and converted at the end.
@@ -90,6 +93,24 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   const unsigned mask = group_mask(G);
   const int W = group_width(G);
   const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
+  if (t == 0) {
+    // a warp slot's sub-partition is slot mod 4 and a CTA's warps take
+    // consecutive slots: rotate the leader by the CTA's slot group
+    unsigned wid;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
+    ctrl->lead = nwarp > 1 ? int(((wid >> 2) - wid) & unsigned(nwarp - 1)) : 0;
+  }
+  __syncthreads();
+  const int L = ctrl->lead;
+  // node of level k handled by this thread, or -1: a level of more than 32
+  // nodes on threads 0.., one of at most 32 nodes on the lanes of warp L
+  auto node_at = [&](int k) -> int {
+    const int cnt = 1 << (k - 1);
+    if (cnt > 32) return t < cnt ? t : -1;
+    return (warp == L && lane < cnt) ? lane : -1;
+  };
+  // thread that ends the bottom-up sweep with the root record
+  const int root_t = K >= 3 ? 32 * L : 0;
 
   for (int i = t; i < P.n_mats; i += G)
     mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
@@ -102,17 +123,18 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
   const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
-  // top-down strain sweep from the root strain (eq. DMN kinematics): node j of
-  // level k on thread j; the bottom laminates' strains end in eK
+  // top-down strain sweep from the root strain (eq. DMN kinematics); the
+  // bottom laminates' strains end in eK
   auto scatter = [&](const HP *root) {
     HP *top = K == 1 ? eK : ebuf(1);
     for (int c = t; c < 6; c += G) top[c] = root[c];
     __syncthreads();
     for (int k = 1; k <= K - 1; ++k) {
-      if (t < (1 << (k - 1))) {
-        const int p = (1 << K) - (1 << k) + t;
-        const HP *ep = ebuf(k) + 6 * t;
-        HP *ec = (k + 1 == K ? eK : ebuf(k + 1)) + 12 * t;
+      const int j = node_at(k);
+      if (j >= 0) {
+        const int p = (1 << K) - (1 << k) + j;
+        const HP *ep = ebuf(k) + 6 * j;
+        HP *ec = (k + 1 == K ? eK : ebuf(k + 1)) + 12 * j;
         NodeHP<HP> nd;
         load_node(P, p, nd);
         const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
@@ -131,6 +153,75 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     }
   };
 
+  // warm start: one sweep gives the strains at (eps_bar^{n+1}, a^n + da) and
+  // the traces of the strains at (eps_bar^n, a^n) (tr B a = a . n), which
+  // the thermoelastic coupling term needs; a += da on the way.  Level
+  // entries hold 7 HP (strain, trace); the bottom traces go to deK.
+  auto scatter_warm = [&](HP tr_root) {
+    if (K == 1) {
+      for (int c = t; c < 6; c += G) eK[c] = eb[c];
+      if (t == 0) deK[0] = tr_root;
+    } else {
+      HP *top = ebuf(1);
+      for (int c = t; c < 6; c += G) top[c] = eb[c];
+      if (t == 0) top[6] = tr_root;
+    }
+    __syncthreads();
+    for (int k = 1; k <= K - 1; ++k) {
+      const int j = node_at(k);
+      if (j >= 0) {
+        const int p = (1 << K) - (1 << k) + j;
+        const HP *ep = ebuf(k) + 7 * j;
+        NodeHP<HP> nd;
+        load_node(P, p, nd);
+        const HP an[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
+        const HP a1[3] = {hp_add_tf(an[0], da_s[3 * p]), hp_add_tf(an[1], da_s[3 * p + 1]),
+                          hp_add_tf(an[2], da_s[3 * p + 2])};
+        HP J[6];
+        bvec_hp(nd, a1, J);
+        const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
+        HP e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) e[c] = ep[c];
+        const HP tr = ep[6];
+        if (k + 1 == K) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            eK[12 * j + c] = e[c] + nd.c2 * J[c];
+            eK[12 * j + 6 + c] = e[c] - nd.c1 * J[c];
+          }
+          deK[2 * j] = tr + nd.c2 * trj;
+          deK[2 * j + 1] = tr - nd.c1 * trj;
+        } else {
+          HP *ec = ebuf(k + 1) + 14 * j;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            ec[c] = e[c] + nd.c2 * J[c];
+            ec[7 + c] = e[c] - nd.c1 * J[c];
+          }
+          ec[6] = tr + nd.c2 * trj;
+          ec[13] = tr - nd.c1 * trj;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) a_s[3 * p + r] = a1[r];
+      }
+      __syncthreads();
+    }
+  };
+
+  // n doubles from global memory into HP in shared memory, U loads in flight
+  auto load_hp = [&](HP *dst, const double *src, int n) {
+    constexpr int U = 8;
+    for (int i0 = t; i0 < n; i0 += U * G) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = i0 + u * G < n ? ld_stream(src + i0 + u * G) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (i0 + u * G < n) dst[i0 + u * G] = hp_load(v[u], tag);
+    }
+  };
+
   for (;;) {
     if (t == 0) ctrl->next = atomicAdd(P.queue, 1ull);
     __syncthreads();
@@ -140,8 +231,19 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     double *sout = P.sout + pt * P.SW;
     HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
     const double theta = P.theta[pt];
-    for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
-    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_load(sin[8 + 3 * N + i], tag);
+    load_hp(a_s, sin + 8, 3 * N);
+    load_hp(zn_s, sin + 8 + 3 * N, 7 * NZ);
+    if (P.da0) {  // predicted increment, in flight with the state loads
+      const float *d0 = P.da0 + pt * (3 * N);
+      for (int i0 = t; i0 < 3 * N; i0 += 8 * G) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < 3 * N ? ld_stream(d0 + i0 + u * G) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * G < 3 * N) da_s[i0 + u * G] = TF(v[u]);
+      }
+    }
     for (int c = t; c < 6; c += G) {
       const double d = P.deps[pt * 6 + c];
       eb[c] = hp_load(sin[c] + d, tag);
@@ -165,26 +267,22 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     HP trn0 = hp_zero(tag), trn1 = hp_zero(tag);
     bool first = true;  // the first pass also yields the traces of eps^n
     if (P.da0) {
-      // warm start a^n + da0: the traces of eps^n from a sweep at a^n
-      HP ebn[6];
-      for (int c = 0; c < 6; ++c) ebn[c] = hp_load(sin[c], tag);
-      scatter(ebn);
+      // warm start a^n + da0; the traces of eps^n come with the same sweep
+      scatter_warm(hp_load(sin[0], tag) + hp_load(sin[1], tag) + hp_load(sin[2], tag));
       NodeHP<HP> nd;
       load_node(P, t, nd);
-      const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
-      HP J[6];
-      bvec_hp(nd, av, J);
-      const HP trj = J[0] + J[1] + J[2];
-      const HP tre = eK[6 * t] + eK[6 * t + 1] + eK[6 * t + 2];
+      const HP an[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};  // still a^n
+      const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
+      const HP tre = deK[t];
       trn0 = tre + nd.c2 * trj;
       trn1 = tre - nd.c1 * trj;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a_s[3 * t + r] = hp_add_tf(an[r], da_s[3 * t + r]);
       first = false;
-      __syncthreads();
-      const float *d0 = P.da0 + pt * (3 * N);
-      for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], TF(d0[i]));
-      __syncthreads();
+      // thread t alone reads a_s[3t..] and deK[t] before the next barrier
+    } else {
+      scatter(eb);  // strains of the bottom laminates at a^n
     }
-    scatter(eb);  // strains of the bottom laminates at the starting a
     int attempt = 0, it_total = 0;
     HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
     Rec<TF> rec;
@@ -275,13 +373,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         if (prod > 32) {
           __syncthreads();
         } else {
-          if (warp != 0) break;
+          if (warp != L) break;
           __syncwarp(mask);
         }
-        if (t < (1 << (k - 1))) {
-          const int p = (1 << K) - (1 << k) + t;
-          const TF *rc = recbuf(k + 1) + RS * (2 * t);
-          const HP *sc = sbuf(k + 1) + 12 * t;
+        const int j = node_at(k);
+        if (j >= 0) {
+          const int p = (1 << K) - (1 << k) + j;
+          const TF *rc = recbuf(k + 1) + RS * (2 * j);
+          const HP *sc = sbuf(k + 1) + 12 * j;
           Rec<TF> other;
           rec_get(rec, rc);
           rec_get(other, rc + RS);
@@ -304,15 +403,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
           combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
           if (k > 1) {
-            rec_put(recbuf(k) + RS * t, rec);
+            rec_put(recbuf(k) + RS * j, rec);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) sbuf(k)[6 * t + c] = S[c];
+            for (int c = 0; c < 6; ++c) sbuf(k)[6 * j + c] = S[c];
           }
         }
       }
-      if (t == 0) {
+      if (t == root_t) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sroot[c] = S[c];  // thread 0 holds the root
+        for (int c = 0; c < 6; ++c) sroot[c] = S[c];
       }
       // ---- residual norm, decision (Algorithm 1) ----
       r2 = warp_sum(r2, mask, W);
@@ -389,14 +488,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         // ---- back-substitution, node j of level k on thread j:
         //      da_p = -(G_p de_p + h_p); children de + c2 B da, de - c1 B da (HP)
         for (int k = 1; k <= K; ++k) {
-          if (t < (1 << (k - 1))) {
-            const int p = (1 << K) - (1 << k) + t;
+          const int j = node_at(k);  // level K: j = t
+          if (j >= 0) {
+            const int p = (1 << K) - (1 << k) + j;
             HP de[6];
             if (k == 1) {
 #pragma unroll
               for (int c = 0; c < 6; ++c) de[c] = hp_zero(tag);
             } else {
-              const HP *src = (k == K ? hX : ebuf(k)) + 6 * t;
+              const HP *src = (k == K ? hX : ebuf(k)) + 6 * j;
 #pragma unroll
               for (int c = 0; c < 6; ++c) de[c] = src[c];
             }
@@ -421,7 +521,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
                                  hp_add_tf(hp_zero(tag), da[2])};
               HP J[6];
               bvec_hp(nd, dah, J);
-              HP *dst = (k + 1 == K ? hX : ebuf(k + 1)) + 12 * t;
+              HP *dst = (k + 1 == K ? hX : ebuf(k + 1)) + 12 * j;
 #pragma unroll
               for (int c = 0; c < 6; ++c) {
                 dst[c] = de[c] + nd.c2 * J[c];
@@ -430,15 +530,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
             } else {
 #pragma unroll
               for (int c = 0; c < 6; ++c) {
-                eK[6 * t + c] = eK[6 * t + c] + de[c];
-                deK[6 * t + c] = de[c];
+                eK[6 * j + c] = eK[6 * j + c] + de[c];
+                deK[6 * j + c] = de[c];
               }
             }
           }
           // level k+1 is read by threads < 2^k: a warp barrier while they
           // all sit in warp 0 (the other warps wait at the next block barrier)
           if (k == K || (1 << k) > 32) __syncthreads();
-          else if (warp == 0) __syncwarp(mask);
+          else if (warp == L) __syncwarp(mask);
         }
       } else {
         // ---- backtracking: a -= f da, strains -= f de ----
@@ -455,7 +555,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     }
 
     // ---- outputs and state (the last pass is at the final a) ----
-    if (t == 0) {
+    if (t == root_t) {
 #pragma unroll
       for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
 #pragma unroll
@@ -484,7 +584,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       else if (c == 55) v = double(orec[33]);
       else v = hp_to(misc[2]);
       if (!isfinite(v)) bad = 1;
-      P.out[pt * kOutWords + c] = v;
+      __stcs(P.out + pt * kOutWords + c, v);
     }
     bad = __syncthreads_or(bad);
     if (t == 0) {
@@ -493,10 +593,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     }
     for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
       sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);
-    for (int i = t; i < 3 * N; i += G) sout[8 + i] = hp_to(a_s[i]);
+    for (int i = t; i < 3 * N; i += G) __stcs(sout + 8 + i, hp_to(a_s[i]));
     for (int i = t; i < 7 * NZ; i += G) {  // parked internal variables -> FP64 in place
-      const HP v = zw[i];
-      sout[8 + 3 * N + i] = hp_to(v);
+      const HP v = ld_once(zw + i);
+      __stcs(sout + 8 + 3 * N + i, hp_to(v));
     }
     for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
     __syncthreads();

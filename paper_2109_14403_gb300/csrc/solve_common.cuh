@@ -12,7 +12,9 @@ template <typename TF>
 struct Ctrl {
   TF res, res_old, gi, pad0_;
   unsigned long long next;  // point taken from the queue
-  int action, it, bt, status, first, nonfinite, pad_[2];
+  int action, it, bt, status, first, nonfinite;
+  int lead;  // warp that runs the levels of at most 32 nodes (compact kernel)
+  int pad_;
 };
 
 __device__ __forceinline__ unsigned group_mask(int G) {
@@ -20,6 +22,50 @@ __device__ __forceinline__ unsigned group_mask(int G) {
 }
 // shuffle segment width: a point with fewer than 32 threads is one segment
 __device__ __forceinline__ int group_width(int G) { return G >= 32 ? 32 : G; }
+
+// ------------------------------------------------------------------ cache hints
+// Per-point data (state blocks, predicted increments, parked internal
+// variables) is read once and streamed past L1, which then keeps the node
+// tables that every pass of every point reads (L1 is what shared memory
+// leaves over, about 28 KB per SM at three CTAs).
+__device__ __forceinline__ double ld_stream(const double *p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+// coherent load that does not allocate in L1 (data written earlier in the
+// same launch by this CTA, read once)
+template <typename T>
+__device__ __forceinline__ T ld_once(const T *p) {
+  static_assert(sizeof(T) == 8, "8-byte values");
+  unsigned long long b;
+  asm volatile("ld.global.L1::no_allocate.b64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+  T v;
+  memcpy(&v, &b, 8);
+  return v;
+}
+__device__ __forceinline__ double ld_keep(const double *p) {
+  double v;
+  asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_keep(const float *p) {
+  float v;
+  asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_keep(const float4 *p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
 
 // ------------------------------------------------------------------ node constants
 template <typename HP>
@@ -30,15 +76,15 @@ __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<do
   const double *r = P.node + kNodeWords * p;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    o.n[i] = __ldg(r + i);
-    o.ns[i] = __ldg(r + 8 + i);
+    o.n[i] = ld_keep(r + i);
+    o.ns[i] = ld_keep(r + 8 + i);
   }
-  o.c1 = __ldg(r + 3);
-  o.c2 = __ldg(r + 4);
+  o.c1 = ld_keep(r + 3);
+  o.c2 = ld_keep(r + 4);
 }
 __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<dfl> &o) {
   const float4 *r = reinterpret_cast<const float4 *>(P.node_df + kNodeDfl * p);
-  const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+  const float4 a = ld_keep(r), b = ld_keep(r + 1), c = ld_keep(r + 2), d = ld_keep(r + 3);
   o.n[0] = {a.x, a.y};
   o.n[1] = {a.z, a.w};
   o.n[2] = {b.x, b.y};
@@ -52,24 +98,24 @@ __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<df
 __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, double n[3], double &c1,
                                              double &c2, double &iwcc, double &wcc) {
   const double *r = P.node + kNodeWords * p;
-  n[0] = __ldg(r);
-  n[1] = __ldg(r + 1);
-  n[2] = __ldg(r + 2);
-  c1 = __ldg(r + 3);
-  c2 = __ldg(r + 4);
-  wcc = __ldg(r + 6);
-  iwcc = __ldg(r + 7);
+  n[0] = ld_keep(r);
+  n[1] = ld_keep(r + 1);
+  n[2] = ld_keep(r + 2);
+  c1 = ld_keep(r + 3);
+  c2 = ld_keep(r + 4);
+  wcc = ld_keep(r + 6);
+  iwcc = ld_keep(r + 7);
 }
 __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, float n[3], float &c1,
                                              float &c2, float &iwcc, float &wcc) {
   const float *r = P.node_df + kNodeDfl * p;
-  n[0] = __ldg(r);
-  n[1] = __ldg(r + 2);
-  n[2] = __ldg(r + 4);
-  c1 = __ldg(r + 12);
-  c2 = __ldg(r + 14);
-  iwcc = __ldg(r + 16);
-  wcc = __ldg(r + 17);
+  n[0] = ld_keep(r);
+  n[1] = ld_keep(r + 2);
+  n[2] = ld_keep(r + 4);
+  c1 = ld_keep(r + 12);
+  c2 = ld_keep(r + 14);
+  iwcc = ld_keep(r + 16);
+  wcc = ld_keep(r + 17);
 }
 __device__ __forceinline__ double hp_add_tf(double a, double d) { return a + d; }
 __device__ __forceinline__ dfl hp_add_tf(dfl a, float d) { return a + dfl{d, 0.0f}; }

@@ -73,6 +73,7 @@ def test_noalloc_matches_eval_on_two_calls_in_a_row(prec):
     deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=2)
     deps_h *= 8.0  # plastic increments: several Newton iterations
     ref = DMN(K, w, nrm, ph, rows, tol=1e-12, precision=prec)
+    opt.solve_variant = ref.solve_variant  # the same kernel on both entry points
     s0 = ref.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
     s_ref, s_na = s0, s0.clone()
     ts, tt = TOL[prec]
