@@ -107,8 +107,8 @@ typedef struct {
                            2, 3, 4 = owner-mapped mixed kernel compiled for
                            that many resident CTAs per SM; 11 = compact kernel
                            (upper tree levels on one warp, strains updated by
-                           the Newton step), FP64 (mixed: as 12); 12, 13 =
-                           compact mixed kernel for 2 or 3 CTAs per SM.  The
+                           the Newton step), FP64 (mixed: as 12); 12, 13, 14
+                           = compact mixed kernel for 2, 3 or 4 CTAs per SM.  The
                            2..4 choice has no effect in FP64.  Any other value
                            is DMN_ERR_ARG.  Chosen by the autotuner          */
 } dmn_options;

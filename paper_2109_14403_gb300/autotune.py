@@ -8,8 +8,8 @@ depends on the tree depth and on how many Newton iterations the workload
 takes, so it is measured: every variant runs the same synthetic increments
 and the fastest is written to a JSON table that ``DMN`` consults when no
 variant is given.  Variant numbers are those of ``dmn_options.solve_variant``:
-2, 3, 4 owner-mapped mixed; 12, 13 compact mixed; 0 owner-mapped FP64; 11
-compact FP64.
+2, 3, 4 owner-mapped mixed; 12, 13, 14 compact mixed; 0 owner-mapped FP64;
+11 compact FP64.
 
 Usage (on a GPU):  python -m paper_2109_14403_gb300.autotune [--K 8] [--points 65536]
 """
@@ -20,7 +20,7 @@ import json
 import os
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
-VARIANTS = {"mixed": (2, 3, 4, 12, 13), "fp64": (0, 11)}
+VARIANTS = {"mixed": (2, 3, 4, 12, 13, 14), "fp64": (0, 11)}
 
 
 def key(K: int, precision: str) -> str:

@@ -88,7 +88,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED))
     return fail(DMN_ERR_ARG, "dmn_create: invalid options");
   if (!solve_variant_valid(o.solve_variant))
-    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4, 11, 12, 13}",
+    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4, 11, 12, 13, 14}",
                 o.solve_variant);
   const int nleaf = 1 << K, N = nleaf - 1;
 

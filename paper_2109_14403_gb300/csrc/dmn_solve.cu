@@ -445,11 +445,11 @@ static size_t owner_smem_bytes(int K, int nz, int n_mats, bool mixed) {
 
 // kernel variants: (form, precision, threads bound, CTAs per SM requested).
 // 0 = default; 2..4 = owner-mapped mixed kernel for that many CTAs per SM;
-// 10 + m = compact kernel (dmn_solve_compact.cu), mixed compiled for m = 2 or
-// 3 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 always takes the
+// 10 + m = compact kernel (dmn_solve_compact.cu), mixed compiled for m = 2, 3
+// or 4 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 always takes the
 // owner-mapped 512-thread kernel.
 bool solve_variant_valid(int variant) {
-  return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 13);
+  return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 14);
 }
 static bool is_compact(int K, int variant) { return K <= 8 && variant >= 11; }
 
@@ -474,7 +474,30 @@ cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, in
   KernelFn f = pick(K, mixed, variant);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem)) != cudaSuccess)
+    return e;
+  // shared memory carveout: the smallest configuration that holds the
+  // resident CTAs (plus 1 KB per CTA for the system); the rest of the SM's
+  // unified 256 KB stays L1 for the node tables and spills.  The driver
+  // rounds a requested percentage up to the next configuration, so request
+  // the largest percentage below the chosen one.
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (per_sm > 0 && *blocks_per_sm > 0) {
+    static const int kConfigKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+    const size_t need = size_t(*blocks_per_sm) * (smem + 1024);
+    size_t pick_b = size_t(per_sm);
+    for (int kb : kConfigKB)
+      if (size_t(kb) * 1024 >= need) {
+        pick_b = size_t(kb) * 1024;
+        break;
+      }
+    int pct = pick_b >= size_t(per_sm) ? 100 : int(pick_b * 100 / size_t(per_sm));
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s) {

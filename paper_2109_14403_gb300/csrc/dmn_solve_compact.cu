@@ -49,8 +49,34 @@ __device__ __forceinline__ void rec_get(Rec<TF> &r, const TF *s) {
   r.gg = s[39];
 }
 
-__host__ __device__ constexpr int half_or_one(int G) { return G >= 2 ? G / 2 : 1; }
-__host__ __device__ constexpr int quarter_or_one(int G) { return G >= 4 ? G / 4 : 1; }
+// Shared scratch region, in 8-byte words, used in turn by the condensation
+// (stress sums and records of the levels K-1, K-2, ..., two parities) and by
+// the strain sweeps (level entries of 6 or 7 HP words, two parities; level K
+// of the back-substitution: 6G words).
+struct Scratch {
+  int GX, GY;         // entries of the two condensation parities
+  int sx, sy, rx, ry;  // offsets: S sums in HP words, records in TF words from rx
+  int hx, hy;          // sweep buffers, HP words
+  int words;           // size of the region in 8-byte words
+};
+__host__ __device__ inline Scratch scratch_layout(int G, int tf_bytes) {
+  Scratch c;
+  c.GX = G >= 2 ? G / 2 : 1;  // level K-1 has G/2 nodes
+  c.GY = G >= 4 ? G / 4 : 1;  // level K-2
+  c.sx = 0;
+  c.sy = 6 * c.GX;
+  const int rx_tf = (6 * c.GX + 6 * c.GY) * (8 / tf_bytes);  // records start after the sums
+  c.rx = rx_tf;
+  c.ry = rx_tf + ((RS * c.GX + 1) & ~1);
+  const int cond_words = (c.ry + RS * c.GY) * tf_bytes / 8 + 1;
+  c.hx = 0;
+  const int hxw = 6 * G > 7 ? 6 * G : 7;
+  c.hy = hxw;
+  const int hyw = (7 * G + 1) / 2 > 7 ? (7 * G + 1) / 2 : 7;
+  const int sweep_words = hxw + hyw;
+  c.words = cond_words > sweep_words ? cond_words : sweep_words;
+  return c;
+}
 }  // namespace
 
 template <typename TF, typename HP, int MAXT, int MINB>
@@ -58,36 +84,33 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
   const int t = threadIdx.x;
-  const int GX = half_or_one(G), GY = quarter_or_one(G);
+  const Scratch sc_ = scratch_layout(G, int(sizeof(TF)));
   HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
   HP *eK = a_s + 3 * N;                        // 6G   strains of the bottom laminates
-  HP *deK = eK + 6 * G;                        // 6G   their increment in the last Newton step
-  HP *zn_s = deK + 6 * G;                      // 7 NZ internal variables at t^n
-  HP *Sx = zn_s + 7 * NZ;                      // 6 GX subtree stress sums (levels K-1, K-3, ...)
-  HP *Sy = Sx + 6 * GX;                        // 6 GY (levels K-2, K-4, ...)
-  HP *eb = Sy + 6 * GY;                        // 12: eps_bar^{n+1}, deps
+  HP *zn_s = eK + 6 * G;                       // 7 NZ internal variables at t^n
+  HP *eb = zn_s + 7 * NZ;                      // 12: eps_bar^{n+1}, deps
   HP *sroot = eb + 12;                         // 6: sigma_bar of the last pass
   HP *redD = sroot + 6;                        // 32
   HP *redX = redD + 32;                        // 32
   HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
-  MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(misc + 4);
+  HP *scr = misc + 4;                          // scratch region (Scratch)
+  MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(scr + sc_.words);
   Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(
       (reinterpret_cast<uintptr_t>(mp_s + P.n_mats) + 15) & ~uintptr_t(15));
   TF *red = reinterpret_cast<TF *>(ctrl + 1);  // 32
   TF *orec = red + 32;                         // 40
   TF *da_s = orec + 40;                        // 3N  Newton increment
   TF *gh_s = da_s + 3 * N;                     // 21N G_p, h_p
-  TF *recX = gh_s + 21 * N;                    // RS GX records (levels K-1, K-3, ...)
-  TF *recY = recX + ((RS * GX + 1) & ~1);      // RS GY records (levels K-2, K-4, ...)
   HP *tag = nullptr;
-  // the record buffers double as high-precision level buffers for the strain
-  // sweeps (at least 6 HP per entry fit: RS TF >= 6 HP for both precisions)
-  HP *hX = reinterpret_cast<HP *>(recX);  // 2 GX entries of 6 HP
-  HP *hY = reinterpret_cast<HP *>(recY);  // 2 GY entries of 6 HP
-  // compact condensation: level k (K-1 >= k >= 1) in X if (K-1-k) is even
+  // condensation: stress sums and records of levels K-1, K-2, ...; level k
+  // in X if (K-1-k) is even
+  HP *Sx = scr + sc_.sx, *Sy = scr + sc_.sy;
+  TF *recX = reinterpret_cast<TF *>(scr) + sc_.rx, *recY = reinterpret_cast<TF *>(scr) + sc_.ry;
   auto recbuf = [&](int k) { return ((K - 1 - k) & 1) ? recY : recX; };
   auto sbuf = [&](int k) { return ((K - 1 - k) & 1) ? Sy : Sx; };
-  // strain sweeps: level k (k >= 2) in X if (K - k) is even (level K: G entries)
+  // strain sweeps (the same region): level k in X if (K - k) is even (level
+  // K of the back-substitution: G entries of 6; warm-start traces: G words)
+  HP *hX = scr + sc_.hx, *hY = scr + sc_.hy;
   auto ebuf = [&](int k) { return ((K - k) & 1) ? hY : hX; };
 
   const unsigned mask = group_mask(G);
@@ -109,7 +132,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     if (cnt > 32) return t < cnt ? t : -1;
     return (warp == L && lane < cnt) ? lane : -1;
   };
-  // thread that ends the bottom-up sweep with the root record
+  // thread that ends the bottom-up sweep with the root record (level K-1 is
+  // condensed by shuffles, on threads 0, 2, ..)
   const int root_t = K >= 3 ? 32 * L : 0;
 
   for (int i = t; i < P.n_mats; i += G)
@@ -156,11 +180,11 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   // warm start: one sweep gives the strains at (eps_bar^{n+1}, a^n + da) and
   // the traces of the strains at (eps_bar^n, a^n) (tr B a = a . n), which
   // the thermoelastic coupling term needs; a += da on the way.  Level
-  // entries hold 7 HP (strain, trace); the bottom traces go to deK.
+  // entries hold 7 HP (strain, trace); the bottom traces go to hX[0, G).
   auto scatter_warm = [&](HP tr_root) {
     if (K == 1) {
       for (int c = t; c < 6; c += G) eK[c] = eb[c];
-      if (t == 0) deK[0] = tr_root;
+      if (t == 0) hX[0] = tr_root;
     } else {
       HP *top = ebuf(1);
       for (int c = t; c < 6; c += G) top[c] = eb[c];
@@ -190,8 +214,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
             eK[12 * j + c] = e[c] + nd.c2 * J[c];
             eK[12 * j + 6 + c] = e[c] - nd.c1 * J[c];
           }
-          deK[2 * j] = tr + nd.c2 * trj;
-          deK[2 * j + 1] = tr - nd.c1 * trj;
+          hX[2 * j] = tr + nd.c2 * trj;  // the level K-2 entries of hX are consumed
+          hX[2 * j + 1] = tr - nd.c1 * trj;
         } else {
           HP *ec = ebuf(k + 1) + 14 * j;
 #pragma unroll
@@ -273,13 +297,13 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       load_node(P, t, nd);
       const HP an[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};  // still a^n
       const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
-      const HP tre = deK[t];
+      const HP tre = hX[t];
       trn0 = tre + nd.c2 * trj;
       trn1 = tre - nd.c1 * trj;
 #pragma unroll
       for (int r = 0; r < 3; ++r) a_s[3 * t + r] = hp_add_tf(an[r], da_s[3 * t + r]);
       first = false;
-      // thread t alone reads a_s[3t..] and deK[t] before the next barrier
+      __syncthreads();  // hX is condensation scratch again from here
     } else {
       scatter(eb);  // strains of the bottom laminates at a^n
     }
@@ -365,9 +389,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           }
         }
       }
-      // ---- levels K-2 .. 1: node j on thread j.  Once the producers of the
-      //      level below all sit in warp 0, warp 0 goes on alone with warp
-      //      barriers and the other warps move to the reduction barrier ----
+      // ---- levels K-2 .. 1: node j of the level on one thread.  Once the
+      //      producers of the level below all sit in warp L, warp L goes on
+      //      alone with warp barriers and the other warps move to the
+      //      reduction barrier ----
       for (int k = K - 2; k >= 1; --k) {
         const int prod = k + 1 == K - 1 ? G : (1 << k);  // threads that wrote level k+1
         if (prod > 32) {
@@ -529,10 +554,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
               }
             } else {
 #pragma unroll
-              for (int c = 0; c < 6; ++c) {
-                eK[6 * j + c] = eK[6 * j + c] + de[c];
-                deK[6 * j + c] = de[c];
-              }
+              for (int c = 0; c < 6; ++c) eK[6 * j + c] = eK[6 * j + c] + de[c];
             }
           }
           // level k+1 is read by threads < 2^k: a warp barrier while they
@@ -541,12 +563,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           else if (warp == L) __syncwarp(mask);
         }
       } else {
-        // ---- backtracking: a -= f da, strains -= f de ----
+        // ---- backtracking (rare): a -= f da, strains from a new sweep ----
         const TF f = ctrl->gi * (TF(1) - gamma);
-        const HP fh = hp_add_tf(hp_zero(tag), -f);
         for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
-        for (int i = t; i < 6 * G; i += G) eK[i] = eK[i] + fh * deK[i];
-        __syncthreads();
+        scatter(eb);  // its barriers also order the reads of ctrl->gi above
         if (t == 0) {
           ctrl->gi *= gamma;
           ctrl->bt += 1;
@@ -605,20 +625,21 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
 
 size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
-  const int GX = half_or_one(G), GY = quarter_or_one(G);
   const size_t hp = 8, tf = mixed ? 4 : 8;
-  size_t b = hp * (3 * N + 12 * G + 7 * nz + 6 * GX + 6 * GY + 12 + 6 + 64 + 4);
+  const Scratch sc = scratch_layout(G, int(tf));
+  size_t b = hp * (3 * N + 6 * G + 7 * nz + 12 + 6 + 64 + 4 + sc.words);
   b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
   b = (b + 15) & ~size_t(15);
   b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
-  b += tf * (32 + 40 + 24 * N + ((RS * GX + 1) & ~1) + RS * GY);
+  b += tf * (32 + 40 + 24 * N);
   return (b + 15) & ~size_t(15);
 }
 
 KernelFn compact_kernel(int K, bool mixed, int minb) {
   (void)K;  // depth <= 8: at most 128 threads
   if (!mixed) return dmn_solve_compact<double, double, 128, 1>;
-  return minb >= 3 ? dmn_solve_compact<float, dfl, 128, 3> : dmn_solve_compact<float, dfl, 128, 2>;
+  if (minb >= 4) return dmn_solve_compact<float, dfl, 128, 4>;
+  return minb == 3 ? dmn_solve_compact<float, dfl, 128, 3> : dmn_solve_compact<float, dfl, 128, 2>;
 }
 
 }  // namespace dmn

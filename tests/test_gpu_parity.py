@@ -111,7 +111,7 @@ def test_k8_full_batch_sampled(prec):
 
 # the compact kernel form (incremental strains, compact upper levels): FP64
 # variant 11, mixed variants 12 and 13 (2 or 3 CTAs per SM)
-COMPACT = [("fp64", 11), ("mixed", 12), ("mixed", 13)]
+COMPACT = [("fp64", 11), ("mixed", 12), ("mixed", 13), ("mixed", 14)]
 
 
 @pytest.mark.parametrize("K", [1, 2, 3, 4, 5, 6, 7])
