@@ -1,16 +1,20 @@
 // dmn_solve_compact.cu -- second form of the Algorithm 1 solve (arXiv
 // 2109.14403, Sec. 3.3): one CTA per Gauss point, G = 2^(K-1) threads, with
 //  * incremental strains: the strains of the bottom laminates live in shared
-//    memory and are updated by the Newton back-substitution itself, which
-//    carries the strain increments de in the high precision HP (float-float in
-//    the mixed path) from the exact FP32 jump increments da; the top-down strain
-//    scatter (eq. DMN kinematics) runs once per point, not once per pass;
+//    memory and are updated after each Newton step by adding, in the high
+//    precision HP (float-float in the mixed path), the strain increments the
+//    exact FP32 jump increments da cause (eq. DMN kinematics);
+//  * strain sums instead of level sweeps: a bottom laminate's strain (or
+//    increment) is the root value plus one term per ancestor; all terms are
+//    formed at once, one node per thread, and summed per laminate after a
+//    single barrier;
 //  * compact levels: the laminates just above the bottom pair neighbouring
 //    lanes by shuffle; every higher level puts node j of the level on one
 //    thread, with the children's condensed records and stress sums in shared
 //    memory, so a level of at most 32 nodes occupies one warp (the CTA's
 //    leader warp, with warp barriers only) while the other warps go ahead;
-//  * the back-substitution compact in the same way, one barrier per level.
+//  * the back-substitution of the Newton increment, a chain through the
+//    levels, in the condensation precision TF on the same compact mapping.
 // The leader warp is picked from the CTA's warp slot so that the CTAs resident
 // on one SM run their single-warp phases on different SM sub-partitions.
 // The condensation, the residual and the leaf laws are those of
@@ -50,13 +54,12 @@ __device__ __forceinline__ void rec_get(Rec<TF> &r, const TF *s) {
 }
 
 // Shared scratch region, in 8-byte words, used in turn by the condensation
-// (stress sums and records of the levels K-1, K-2, ..., two parities) and by
-// the strain sweeps (level entries of 6 or 7 HP words, two parities; level K
-// of the back-substitution: 6G words).
+// (stress sums and records of the levels K-1, K-2, ..., two parities), by the
+// Newton back-substitution (TF strain increments of two level parities, level
+// K: 6G values) and by the strain sums (14 HP words per non-bottom node).
 struct Scratch {
-  int GX, GY;         // entries of the two condensation parities
+  int GX, GY;          // entries of the two condensation parities
   int sx, sy, rx, ry;  // offsets: S sums in HP words, records in TF words from rx
-  int hx, hy;          // sweep buffers, HP words
   int words;           // size of the region in 8-byte words
 };
 __host__ __device__ inline Scratch scratch_layout(int G, int tf_bytes) {
@@ -69,12 +72,11 @@ __host__ __device__ inline Scratch scratch_layout(int G, int tf_bytes) {
   c.rx = rx_tf;
   c.ry = rx_tf + ((RS * c.GX + 1) & ~1);
   const int cond_words = (c.ry + RS * c.GY) * tf_bytes / 8 + 1;
-  c.hx = 0;
-  const int hxw = 6 * G > 7 ? 6 * G : 7;
-  c.hy = hxw;
-  const int hyw = (7 * G + 1) / 2 > 7 ? (7 * G + 1) / 2 : 7;
-  const int sweep_words = hxw + hyw;
-  c.words = cond_words > sweep_words ? cond_words : sweep_words;
+  const int chain_words = (9 * G * tf_bytes + 7) / 8;
+  const int sum_words = 14 * (G - 1);
+  c.words = cond_words;
+  if (chain_words > c.words) c.words = chain_words;
+  if (sum_words > c.words) c.words = sum_words;
   return c;
 }
 }  // namespace
@@ -108,10 +110,11 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   TF *recX = reinterpret_cast<TF *>(scr) + sc_.rx, *recY = reinterpret_cast<TF *>(scr) + sc_.ry;
   auto recbuf = [&](int k) { return ((K - 1 - k) & 1) ? recY : recX; };
   auto sbuf = [&](int k) { return ((K - 1 - k) & 1) ? Sy : Sx; };
-  // strain sweeps (the same region): level k in X if (K - k) is even (level
-  // K of the back-substitution: G entries of 6; warm-start traces: G words)
-  HP *hX = scr + sc_.hx, *hY = scr + sc_.hy;
-  auto ebuf = [&](int k) { return ((K - k) & 1) ? hY : hX; };
+  // back-substitution (the same region): TF strain increments, level k in X
+  // if (K - k) is even (level K: G entries of 6)
+  TF *tX = reinterpret_cast<TF *>(scr), *tY = tX + 6 * G;
+  auto tbuf = [&](int k) { return ((K - k) & 1) ? tY : tX; };
+  HP *anc = scr;  // strain sums: per non-bottom node c2 B x, c1 B x, c2 tr, c1 tr
 
   const unsigned mask = group_mask(G);
   const int W = group_width(G);
@@ -147,90 +150,68 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
   const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
-  // top-down strain sweep from the root strain (eq. DMN kinematics); the
-  // bottom laminates' strains end in eK
-  auto scatter = [&](const HP *root) {
-    HP *top = K == 1 ? eK : ebuf(1);
-    for (int c = t; c < 6; c += G) top[c] = root[c];
-    __syncthreads();
-    for (int k = 1; k <= K - 1; ++k) {
-      const int j = node_at(k);
-      if (j >= 0) {
-        const int p = (1 << K) - (1 << k) + j;
-        const HP *ep = ebuf(k) + 6 * j;
-        HP *ec = (k + 1 == K ? eK : ebuf(k + 1)) + 12 * j;
-        NodeHP<HP> nd;
-        load_node(P, p, nd);
-        const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
-        HP J[6];
-        bvec_hp(nd, av, J);
-        HP e[6];
+  // Strains of the bottom laminates by ancestor sums (eq. DMN kinematics):
+  // laminate t's strain is the root strain plus, for every ancestor p on its
+  // path, +c2 B x_p (the path goes through child 1) or -c1 B x_p (child 2).
+  // The two terms of every non-bottom node are formed at once, one node per
+  // thread; after one barrier each thread adds its K-1 ancestors' terms root
+  // first, the order (and rounding) of a level-by-level top-down sweep.
+  //   SW_PLAIN: eK = eps_bar^{n+1} + sum of the B a terms
+  //   SW_WARM:  a += da (da_s) on the way; eK as SW_PLAIN at the new a, and
+  //             the trace of the strain at (eps_bar^n = tr_root, a^n) of
+  //             laminate t is returned (tr B a = a . n)
+  //   SW_STEP:  eK += sum of the B da terms (the Newton increment in da_s)
+  // Ends with a barrier: eK is complete and the scratch region free again.
+  enum { SW_PLAIN = 0, SW_WARM = 1, SW_STEP = 2 };
+  auto sweep = [&](int mode, HP tr_root) -> HP {
+    for (int q = t; q < G - 1; q += G) {
+      const int p = G + q;
+      NodeHP<HP> nd;
+      load_node(P, p, nd);
+      HP x[3];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = ep[c];
+      for (int r = 0; r < 3; ++r)
+        x[r] = mode == SW_STEP ? hp_add_tf(hp_zero(tag), da_s[3 * p + r]) : a_s[3 * p + r];
+      HP *ent = anc + 14 * q;
+      if (mode == SW_WARM) {
+        const HP trj = x[0] * nd.n[0] + x[1] * nd.n[1] + x[2] * nd.n[2];
+        ent[12] = nd.c2 * trj;
+        ent[13] = nd.c1 * trj;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          ec[c] = e[c] + nd.c2 * J[c];
-          ec[6 + c] = e[c] - nd.c1 * J[c];
+        for (int r = 0; r < 3; ++r) {
+          x[r] = hp_add_tf(x[r], da_s[3 * p + r]);
+          a_s[3 * p + r] = x[r];
         }
       }
-      __syncthreads();
-    }
-  };
-
-  // warm start: one sweep gives the strains at (eps_bar^{n+1}, a^n + da) and
-  // the traces of the strains at (eps_bar^n, a^n) (tr B a = a . n), which
-  // the thermoelastic coupling term needs; a += da on the way.  Level
-  // entries hold 7 HP (strain, trace); the bottom traces go to hX[0, G).
-  auto scatter_warm = [&](HP tr_root) {
-    if (K == 1) {
-      for (int c = t; c < 6; c += G) eK[c] = eb[c];
-      if (t == 0) hX[0] = tr_root;
-    } else {
-      HP *top = ebuf(1);
-      for (int c = t; c < 6; c += G) top[c] = eb[c];
-      if (t == 0) top[6] = tr_root;
+      HP J[6];
+      bvec_hp(nd, x, J);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        ent[c] = nd.c2 * J[c];
+        ent[6 + c] = nd.c1 * J[c];
+      }
     }
     __syncthreads();
+    HP e[6], tr = tr_root;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = mode == SW_STEP ? hp_zero(tag) : eb[c];
     for (int k = 1; k <= K - 1; ++k) {
-      const int j = node_at(k);
-      if (j >= 0) {
-        const int p = (1 << K) - (1 << k) + j;
-        const HP *ep = ebuf(k) + 7 * j;
-        NodeHP<HP> nd;
-        load_node(P, p, nd);
-        const HP an[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
-        const HP a1[3] = {hp_add_tf(an[0], da_s[3 * p]), hp_add_tf(an[1], da_s[3 * p + 1]),
-                          hp_add_tf(an[2], da_s[3 * p + 2])};
-        HP J[6];
-        bvec_hp(nd, a1, J);
-        const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
-        HP e[6];
+      const int p = (1 << K) - (1 << k) + (t >> (K - k));
+      const HP *ent = anc + 14 * (p - G);
+      if ((t >> (K - k - 1)) & 1) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = ep[c];
-        const HP tr = ep[6];
-        if (k + 1 == K) {
+        for (int c = 0; c < 6; ++c) e[c] = e[c] - ent[6 + c];
+        if (mode == SW_WARM) tr = tr - ent[13];
+      } else {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            eK[12 * j + c] = e[c] + nd.c2 * J[c];
-            eK[12 * j + 6 + c] = e[c] - nd.c1 * J[c];
-          }
-          hX[2 * j] = tr + nd.c2 * trj;  // the level K-2 entries of hX are consumed
-          hX[2 * j + 1] = tr - nd.c1 * trj;
-        } else {
-          HP *ec = ebuf(k + 1) + 14 * j;
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            ec[c] = e[c] + nd.c2 * J[c];
-            ec[7 + c] = e[c] - nd.c1 * J[c];
-          }
-          ec[6] = tr + nd.c2 * trj;
-          ec[13] = tr - nd.c1 * trj;
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) a_s[3 * p + r] = a1[r];
+        for (int c = 0; c < 6; ++c) e[c] = e[c] + ent[c];
+        if (mode == SW_WARM) tr = tr + ent[12];
       }
-      __syncthreads();
     }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) eK[6 * t + c] = mode == SW_STEP ? eK[6 * t + c] + e[c] : e[c];
+    __syncthreads();
+    return tr;
   };
 
   // n doubles from global memory into HP in shared memory, U loads in flight
@@ -292,20 +273,19 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     bool first = true;  // the first pass also yields the traces of eps^n
     if (P.da0) {
       // warm start a^n + da0; the traces of eps^n come with the same sweep
-      scatter_warm(hp_load(sin[0], tag) + hp_load(sin[1], tag) + hp_load(sin[2], tag));
+      const HP tre =
+          sweep(SW_WARM, hp_load(sin[0], tag) + hp_load(sin[1], tag) + hp_load(sin[2], tag));
       NodeHP<HP> nd;
       load_node(P, t, nd);
       const HP an[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};  // still a^n
       const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
-      const HP tre = hX[t];
       trn0 = tre + nd.c2 * trj;
       trn1 = tre - nd.c1 * trj;
 #pragma unroll
       for (int r = 0; r < 3; ++r) a_s[3 * t + r] = hp_add_tf(an[r], da_s[3 * t + r]);
-      first = false;
-      __syncthreads();  // hX is condensation scratch again from here
+      first = false;  // thread t alone uses a_s[3t..] until the next barrier
     } else {
-      scatter(eb);  // strains of the bottom laminates at a^n
+      sweep(SW_PLAIN, hp_zero(tag));  // strains of the bottom laminates at a^n
     }
     int attempt = 0, it_total = 0;
     HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
@@ -504,24 +484,26 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
             ctrl->res_old = TF(0);
             ctrl->status = 0;
           }
-          scatter(eb);  // its first barrier orders the reset before later reads
+          sweep(SW_PLAIN, hp_zero(tag));  // its barriers order the reset before later reads
           continue;
         }
         break;
       }
       if (action == ACT_STEP) {
-        // ---- back-substitution, node j of level k on thread j:
-        //      da_p = -(G_p de_p + h_p); children de + c2 B da, de - c1 B da (HP)
+        // ---- back-substitution in TF, node j of level k on one thread:
+        //      da_p = -(G_p de_p + h_p); children de + c2 B da, de - c1 B da;
+        //      then the bottom strains take the high-precision sum of the
+        //      B da terms of their ancestors
         for (int k = 1; k <= K; ++k) {
           const int j = node_at(k);  // level K: j = t
           if (j >= 0) {
             const int p = (1 << K) - (1 << k) + j;
-            HP de[6];
+            TF de[6];
             if (k == 1) {
 #pragma unroll
-              for (int c = 0; c < 6; ++c) de[c] = hp_zero(tag);
+              for (int c = 0; c < 6; ++c) de[c] = TF(0);
             } else {
-              const HP *src = (k == K ? hX : ebuf(k)) + 6 * j;
+              const TF *src = tbuf(k) + 6 * j;
 #pragma unroll
               for (int c = 0; c < 6; ++c) de[c] = src[c];
             }
@@ -529,10 +511,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
             TF da[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-              TF s = g[18 + r];
+              TF sum = g[18 + r];
 #pragma unroll
-              for (int c = 0; c < 6; ++c) s += g[6 * r + c] * tf_of(de[c], (TF *)nullptr);
-              da[r] = -s;
+              for (int c = 0; c < 6; ++c) sum += g[6 * r + c] * de[c];
+              da[r] = -sum;
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -540,33 +522,30 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
               a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
             }
             if (k < K) {
-              NodeHP<HP> nd;
-              load_node(P, p, nd);
-              const HP dah[3] = {hp_add_tf(hp_zero(tag), da[0]), hp_add_tf(hp_zero(tag), da[1]),
-                                 hp_add_tf(hp_zero(tag), da[2])};
-              HP J[6];
-              bvec_hp(nd, dah, J);
-              HP *dst = (k + 1 == K ? hX : ebuf(k + 1)) + 12 * j;
+              TF n[3], c1, c2, iwcc, wcc;
+              load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+              TF J[6];
+              bvec(n, da, J);
+              TF *dst = tbuf(k + 1) + 12 * j;
 #pragma unroll
               for (int c = 0; c < 6; ++c) {
-                dst[c] = de[c] + nd.c2 * J[c];
-                dst[6 + c] = de[c] - nd.c1 * J[c];
+                dst[c] = de[c] + c2 * J[c];
+                dst[6 + c] = de[c] - c1 * J[c];
               }
-            } else {
-#pragma unroll
-              for (int c = 0; c < 6; ++c) eK[6 * j + c] = eK[6 * j + c] + de[c];
             }
           }
           // level k+1 is read by threads < 2^k: a warp barrier while they
-          // all sit in warp 0 (the other warps wait at the next block barrier)
+          // all sit in warp L (the other warps wait at the next block barrier)
           if (k == K || (1 << k) > 32) __syncthreads();
           else if (warp == L) __syncwarp(mask);
         }
+        sweep(SW_STEP, hp_zero(tag));
       } else {
         // ---- backtracking (rare): a -= f da, strains from a new sweep ----
         const TF f = ctrl->gi * (TF(1) - gamma);
         for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
-        scatter(eb);  // its barriers also order the reads of ctrl->gi above
+        __syncthreads();
+        sweep(SW_PLAIN, hp_zero(tag));  // its barriers also order the reads of ctrl->gi above
         if (t == 0) {
           ctrl->gi *= gamma;
           ctrl->bt += 1;
