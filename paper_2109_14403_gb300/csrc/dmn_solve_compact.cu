@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
   HP *eK = a_s + 3 * N;                        // 6G   strains of the bottom laminates
   HP *zn_s = eK + 6 * G;                       // 7 NZ internal variables at t^n
-  HP *eb = zn_s + 7 * NZ;                      // 12: eps_bar^{n+1}, deps
-  HP *sroot = eb + 12;                         // 6: sigma_bar of the last pass
+  HP *eb = zn_s + 7 * NZ;                      // 18: eps_bar^{n+1}, deps (HP), eps_bar^{n+1} (FP64)
+  double *ebd = reinterpret_cast<double *>(eb + 12);
+  HP *sroot = eb + 18;                         // 6: sigma_bar of the last pass
   HP *redD = sroot + 6;                        // 32
   HP *redX = redD + 32;                        // 32
   HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
@@ -236,23 +237,48 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     double *sout = P.sout + pt * P.SW;
     HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
     const double theta = P.theta[pt];
-    load_hp(a_s, sin + 8, 3 * N);
-    load_hp(zn_s, sin + 8 + 3 * N, 7 * NZ);
-    if (P.da0) {  // predicted increment, in flight with the state loads
-      const float *d0 = P.da0 + pt * (3 * N);
-      for (int i0 = t; i0 < 3 * N; i0 += 8 * G) {
-        float v[8];
+    {
+      // one wave of loads: jumps (3N < 8G), the first 8G internal variables,
+      // the predicted increment, eps_bar^n and deps
+      constexpr int U = 8;
+      double va[U], vz[U], ve = 0.0, vd = 0.0;
+      float vp[U];
+      const float *d0 = P.da0 ? P.da0 + pt * (3 * N) : nullptr;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < 3 * N ? ld_stream(d0 + i0 + u * G) : 0.0f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (i0 + u * G < 3 * N) da_s[i0 + u * G] = TF(v[u]);
+      for (int u = 0; u < U; ++u) {
+        const int i = t + u * G;
+        va[u] = i < 3 * N ? ld_stream(sin + 8 + i) : 0.0;
+        vz[u] = i < 7 * NZ ? ld_stream(sin + 8 + 3 * N + i) : 0.0;
+        vp[u] = d0 && i < 3 * N ? ld_stream(d0 + i) : 0.0f;
       }
-    }
-    for (int c = t; c < 6; c += G) {
-      const double d = P.deps[pt * 6 + c];
-      eb[c] = hp_load(sin[c] + d, tag);
-      eb[6 + c] = hp_load(d, tag);
+      if (G >= 8 && t < 6) {
+        ve = ld_stream(sin + t);
+        vd = ld_stream(P.deps + pt * 6 + t);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = t + u * G;
+        if (i < 3 * N) {
+          a_s[i] = hp_load(va[u], tag);
+          if (d0) da_s[i] = TF(vp[u]);
+        }
+        if (i < 7 * NZ) zn_s[i] = hp_load(vz[u], tag);
+      }
+      if (7 * NZ > U * G) load_hp(zn_s + U * G, sin + 8 + 3 * N + U * G, 7 * NZ - U * G);
+      if (G >= 8) {
+        if (t < 6) {
+          ebd[t] = ve + vd;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
+          eb[t] = hp_load(ve + vd, tag);
+          eb[6 + t] = hp_load(vd, tag);
+        }
+      } else {
+        for (int c = t; c < 6; c += G) {
+          const double d = P.deps[pt * 6 + c], e1 = sin[c] + d;
+          ebd[c] = e1;
+          eb[c] = hp_load(e1, tag);
+          eb[6 + c] = hp_load(d, tag);
+        }
+      }
     }
     __syncthreads();
     for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
@@ -590,12 +616,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
       P.iters[pt] = ctrl->it + it_total;
     }
-    for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
-      sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);
+    for (int c = t; c < 8; c += G) sout[c] = c < 6 ? ebd[c] : (c == 6 ? theta : 0.0);
     for (int i = t; i < 3 * N; i += G) __stcs(sout + 8 + i, hp_to(a_s[i]));
-    for (int i = t; i < 7 * NZ; i += G) {  // parked internal variables -> FP64 in place
-      const HP v = ld_once(zw + i);
-      __stcs(sout + 8 + 3 * N + i, hp_to(v));
+    for (int i0 = t; i0 < 7 * NZ; i0 += 8 * G) {  // parked internal variables -> FP64 in place
+      HP v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < 7 * NZ ? ld_once(zw + i0 + u * G) : hp_zero(tag);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * G < 7 * NZ) __stcs(sout + 8 + 3 * N + i0 + u * G, hp_to(v[u]));
     }
     for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
     __syncthreads();
@@ -606,7 +635,7 @@ size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const size_t hp = 8, tf = mixed ? 4 : 8;
   const Scratch sc = scratch_layout(G, int(tf));
-  size_t b = hp * (3 * N + 6 * G + 7 * nz + 12 + 6 + 64 + 4 + sc.words);
+  size_t b = hp * (3 * N + 6 * G + 7 * nz + 18 + 6 + 64 + 4 + sc.words);
   b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
   b = (b + 15) & ~size_t(15);
   b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
