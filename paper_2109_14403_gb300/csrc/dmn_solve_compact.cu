@@ -446,12 +446,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       }
       // ---- residual norm, decision (Algorithm 1) ----
       r2 = warp_sum(r2, mask, W);
-      const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
-      if (lane == 0) {
-        red[warp] = r2;
-        redD[warp] = ds_;
-        redX[warp] = xs_;
-      }
+      if (lane == 0) red[warp] = r2;
       __syncthreads();
       if (t == 0) {
         TF s = TF(0);
@@ -579,7 +574,16 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       }
     }
 
-    // ---- outputs and state (the last pass is at the final a) ----
+    // ---- outputs and state (the last pass is at the final a; its coupling
+    //      term and dissipation sums are still in the registers) ----
+    {
+      const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
+      if (lane == 0) {
+        redD[warp] = ds_;
+        redX[warp] = xs_;
+      }
+    }
+    __syncthreads();
     if (t == root_t) {
 #pragma unroll
       for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
