@@ -126,6 +126,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources of the library (file names and bytes)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_14403_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def solve_kernel_name(variant, precision):
+    """Template instance the solve launches for K = 8 (see dmn_solve.cu)."""
+    if variant >= 11:
+        if precision == "fp64":
+            return "dmn_solve_compact<double, double, 128, 1>"
+        return f"dmn_solve_compact<float, dfl, 128, {max(2, variant - 10)}>"
+    if precision == "fp64":
+        return "dmn_solve_kernel<double, double, 128, 1>"
+    return f"dmn_solve_kernel<float, dfl, 128, {variant if variant in (2, 4) else 3}>"
+
+
+def measured_traffic(kernel, n_points):
+    """DRAM bytes (read + write) of one launch of `kernel` on n_points, from the
+    committed ncu summary profiles/dram_traffic.json (captured on a smaller
+    batch and scaled by the points processed); None when the kernel sources
+    changed since the capture or no capture exists."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            e = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not e or e.get("source_sha256") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes"]) * n_points / float(e["points"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -494,6 +533,7 @@ def main():
             variants[name] = {"value": whole_job_rate(n, world, steps, ms), "ms_per_step": ms / steps,
                               "mean_iters": float(torch.cat(its).float().mean().item())}
             del sa, sb
+    solve_variant = mixed.solve_variant
     fp64.close()
     mixed.close()
     net.close()
@@ -503,13 +543,14 @@ def main():
             dist.destroy_process_group()
         return
     bpe = algorithmic_bytes_per_eval(K_DEPTH) + 4 * 3 * ((1 << K_DEPTH) - 1)  # + predicted increment
+    kname = solve_kernel_name(solve_variant, "mixed")
     hbm_achieved = bpe * n / (solve_ms / 1e3) / 1e9
     peak, how = measured_peaks()
     passes = mean_iters + 1.0
     flops = alu_flops_per_pass(K_DEPTH) * passes * n / (solve_ms / 1e3) / 1e12
     alu_peak = 73.2  # measured FP32 FMA throughput on this GB300
     roof = {"bound": "alu", "achieved": flops, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": flops / alu_peak, "traffic": None, "kernel": "dmn_solve_kernel",
+            "frac": flops / alu_peak, "traffic": measured_traffic(kname, n), "kernel": kname,
             "flops_per_pass": alu_flops_per_pass(K_DEPTH), "passes_per_eval": passes,
             "hbm": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s", "frac": hbm_achieved / peak,
                     "peak_source": how, "bytes_per_eval": bpe}}
