@@ -23,6 +23,16 @@ _lock = threading.Lock()
 
 OUT_WORDS = 57
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
+MAT_WORDS = 12  # kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT 0
+Z_WORDS = {0: 0, 1: 7, 2: 13}  # internal variables per leaf, by material kind
+
+
+def mat_rows(mats):
+    """Material table as n x 12 rows; rows of 8 (kinds 0 and 1) are padded with 0."""
+    m = np.atleast_2d(np.asarray(mats, np.float64))
+    if m.shape[1] < MAT_WORDS:
+        m = np.hstack([m, np.zeros((m.shape[0], MAT_WORDS - m.shape[1]))])
+    return np.ascontiguousarray(m[:, :MAT_WORDS], dtype=np.float64)
 
 
 def build(force: bool = False) -> str:
@@ -70,14 +80,15 @@ def _c(a, dtype):
 class Tree:
     """DMN description: depth K, leaf weights (2^K), normals ((2^K-1) x 3 in the
     paper's order: bottom level first, root last), phase map (2^K) and a material
-    table (n_mats x 8: kind, E, nu, alpha, theta0, sy0, dsy_dT, H)."""
+    table (n_mats x 12: kind, E, nu, alpha, theta0, sy0, dsy_dT, H, m, t_visc,
+    dE_dT, 0; rows of 8 are padded)."""
 
     def __init__(self, K, w, normals, phase, mats):
         self.K = int(K)
         self.w = _c(w, np.float64)
         self.normals = _c(normals, np.float64).reshape(-1, 3)
         self.phase = _c(phase, np.uint8)
-        self.mats = _c(mats, np.float64).reshape(-1, 8)
+        self.mats = mat_rows(mats)
         n = _load().oracle_state_words(self.K, _ptr(self.w), _ptr(self.normals), _ptr(self.phase),
                                        _ptr(self.mats), self.mats.shape[0])
         if n < 0:
@@ -141,14 +152,17 @@ def eval_point_trace(tree: Tree, deps, theta, dt, state_in, *, tol=1e-12, maxit=
 
 def leaf(mat_row, eps, theta, zn=None, trn=0.0, dt=1.0):
     """One phase-law evaluation.  Returns a dict with sig, C, tau, D, d, g, diss, znew."""
-    m = _c(mat_row, np.float64).reshape(8)
+    m = mat_rows(mat_row).reshape(MAT_WORDS)
     e = _c(eps, np.float64).reshape(6)
-    z = _c(np.zeros(7) if zn is None else zn, np.float64).reshape(7)
-    o = np.zeros(64, np.float64)
+    z = np.zeros(13, np.float64)
+    if zn is not None:
+        zn = np.asarray(zn, np.float64).ravel()
+        z[:zn.size] = zn
+    o = np.zeros(70, np.float64)
     _load().oracle_leaf(_ptr(m), _ptr(e), float(theta), _ptr(z), float(trn), float(dt), _ptr(o))
     return {"sig": o[0:6].copy(), "C": o[6:42].reshape(6, 6).copy(), "tau": o[42:48].copy(),
             "D": float(o[48]), "d": o[49:55].copy(), "g": float(o[55]), "diss": float(o[56]),
-            "znew": o[57:64].copy()}
+            "znew": o[57:57 + max(Z_WORDS[int(m[0])], 7)].copy()}
 
 
 def leaf_strains(tree: Tree, eps_bar, a):

@@ -51,6 +51,22 @@
  *        - dpsi/dz . z_dot, i.e.
  *      D = [-3 K alpha theta tr(eps - eps^n) + sigma_Y(theta) dp] / dt,
  *      Diss = sigma_Y(theta) dp / dt.
+ *  - kind 2, J2 viscoplasticity of Perzyna (overstress) type with the
+ *    accumulated plastic strain rate of Section 4 (eq. for p_dot of the PA66
+ *    model, with linear hardening H p and the reading sigma_Y / eta = 1 / t_visc),
+ *      p_dot = (1 / t_visc) < (q - sigma_Y(theta) - H p) / sigma_Y(theta) >_+^m,
+ *    and temperature-dependent moduli E(theta) = E (1 + dE_dT (theta - theta0)).
+ *    Implicit Euler: dp solves dp = (dt / t_visc) phi^m with
+ *    phi = (q_trial - (3G + H) dp - sigma_Y - H p^n) / sigma_Y (scalar Newton,
+ *    kept inside [0, f_trial / (3G + H)]).  The consistent tangent is the
+ *    radial-return one with H replaced by H + h_v, h_v = sigma_Y / (c m phi^(m-1)),
+ *    c = dt / t_visc.  With C(theta) = r(theta) C0 the paper's coupling term gains
+ *    theta dC/dtheta eps_e : (eps_dot - eps_p_dot) (from d2psi/dtheta deps and
+ *    d2psi/dtheta deps_p), so
+ *      D = [theta (r'/r) sigma : (de - deps_p) - 3 K alpha theta tr(de)
+ *           + sigma_Y dp] / dt,   Diss = sigma_Y dp / dt,
+ *    with de = eps - eps^n the leaf's strain increment; the leaf keeps its
+ *    strain in its internal variables: z = (eps_p (6), p, eps (6)).
  *
  * Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13,
  * sqrt2*12); fourth-order tensors are 6x6 matrices acting on them.
@@ -79,10 +95,17 @@
 /* tree                                                                 */
 /* ------------------------------------------------------------------ */
 
+#define OR_MATW 12 /* material row: kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT 0 */
+#define OR_ZMAX 13 /* internal variables per leaf, at most */
+
 typedef struct {
   int kind;
   double E, nu, alpha, theta0, sy0, dsy_dT, H;
+  double m_rate, t_visc, dE_dT; /* kind 2 only */
 } omat;
+
+/* words of internal variables of a leaf of this kind */
+static int z_words(int kind) { return kind == 1 ? 7 : (kind == 2 ? 13 : 0); }
 
 typedef struct {
   int K, nleaf, nnode;
@@ -147,9 +170,10 @@ static int build_tree(otree *t, int K, const double *leaf_w, const double *norma
   }
   int off = 8 + 3 * t->nnode;
   for (int j = 0; j < t->nleaf; ++j) {
-    if (mats[t->phase[j]].kind == 1) {
+    const int zw = z_words(mats[t->phase[j]].kind);
+    if (zw > 0) {
       t->zoff[j] = off;
-      off += 7;
+      off += zw;
     } else {
       t->zoff[j] = -1;
     }
@@ -183,26 +207,38 @@ typedef struct {
   double d[6];      /* dD/deps                                */
   double g;         /* dD/dtheta (explicit)                   */
   double diss;      /* dissipation                            */
-  double znew[7];   /* eps_p (6), p                           */
+  double znew[OR_ZMAX]; /* eps_p (6), p [, eps (6) for kind 2] */
 } oleaf;
 
 static const double M1[6] = {1, 1, 1, 0, 0, 0};
 
-/* eps: Mandel strain at t^{n+1}; trn: trace of the leaf strain at t^n;
-   zn: 7 internal variables (J2 only) */
+/* eps: Mandel strain at t^{n+1}; trn: trace of the leaf strain at t^n (kinds 0
+   and 1; kind 2 takes its strain at t^n from zn); zn: internal variables of
+   the leaf at t^n (kinds 1 and 2) */
 void oracle_leaf(const double *matp, const double eps[6], double theta, const double *zn,
                  double trn, double dt, double *outp) {
   omat m;
   m.kind = (int)matp[0];
   m.E = matp[1]; m.nu = matp[2]; m.alpha = matp[3]; m.theta0 = matp[4];
   m.sy0 = matp[5]; m.dsy_dT = matp[6]; m.H = matp[7];
+  m.m_rate = matp[8]; m.t_visc = matp[9]; m.dE_dT = matp[10];
   oleaf L;
   memset(&L, 0, sizeof(L));
-  const double Kb = m.E / (3.0 * (1.0 - 2.0 * m.nu));
-  const double G = m.E / (2.0 * (1.0 + m.nu));
+  /* moduli: E(theta) = E r(theta), r = 1 + dE_dT (theta - theta0) for kind 2
+     (floored at 1e-3), r = 1 otherwise */
+  double r = 1.0, dr = 0.0;
+  if (m.kind == 2) {
+    r = 1.0 + m.dE_dT * (theta - m.theta0);
+    dr = m.dE_dT;
+    if (r < 1e-3) { r = 1e-3; dr = 0.0; }
+  }
+  const double Kb = r * m.E / (3.0 * (1.0 - 2.0 * m.nu));
+  const double G = r * m.E / (2.0 * (1.0 + m.nu));
+  const double dKb = dr * m.E / (3.0 * (1.0 - 2.0 * m.nu)); /* dK/dtheta */
+  const double dG = dr * m.E / (2.0 * (1.0 + m.nu));        /* dG/dtheta */
   double ee[6];
   for (int c = 0; c < 6; ++c) ee[c] = eps[c] - M1[c] * m.alpha * (theta - m.theta0);
-  if (m.kind == 1)
+  if (m.kind >= 1)
     for (int c = 0; c < 6; ++c) ee[c] -= zn[c];
   double tr = ee[0] + ee[1] + ee[2];
   double dev[6];
@@ -216,14 +252,25 @@ void oracle_leaf(const double *matp, const double eps[6], double theta, const do
       double p2 = (a == b ? 1.0 : 0.0) - p1;
       L.C[a][b] = 3.0 * Kb * p1 + 2.0 * G * p2;
     }
-  for (int c = 0; c < 6; ++c) L.tau[c] = -3.0 * Kb * m.alpha * M1[c];
-  double treps = eps[0] + eps[1] + eps[2];
-  L.D = -3.0 * Kb * m.alpha * theta * (treps - trn) / dt;
+  /* dsigma/dtheta at fixed strain and internal variables */
+  for (int c = 0; c < 6; ++c)
+    L.tau[c] = -3.0 * Kb * m.alpha * M1[c] + dKb * tr * M1[c] + 2.0 * dG * dev[c];
+  /* strain increment of the step (its trace for kinds 0 and 1) */
+  double de[6] = {0, 0, 0, 0, 0, 0}, trde;
+  if (m.kind == 2) {
+    for (int c = 0; c < 6; ++c) de[c] = eps[c] - zn[7 + c];
+    trde = de[0] + de[1] + de[2];
+  } else {
+    trde = (eps[0] + eps[1] + eps[2]) - trn;
+  }
+  L.D = -3.0 * Kb * m.alpha * theta * trde / dt;
   for (int c = 0; c < 6; ++c) L.d[c] = -3.0 * Kb * m.alpha * theta * M1[c] / dt;
-  L.g = -3.0 * Kb * m.alpha * (treps - trn) / dt;
+  L.g = -3.0 * m.alpha * (Kb + dKb * theta) * trde / dt;
   L.diss = 0.0;
-  if (m.kind == 1) {
+  if (m.kind >= 1) {
     for (int c = 0; c < 7; ++c) L.znew[c] = zn[c];
+    if (m.kind == 2)
+      for (int c = 0; c < 6; ++c) L.znew[7 + c] = eps[c];
     double sy = m.sy0 + m.dsy_dT * (theta - m.theta0);
     double dsy = m.dsy_dT;
     if (sy < 1e-6) { sy = 1e-6; dsy = 0.0; }
@@ -232,33 +279,83 @@ void oracle_leaf(const double *matp, const double eps[6], double theta, const do
     double snorm = sqrt(snorm2);
     double qtr = sqrt(1.5) * snorm;
     double f = qtr - sy - m.H * zn[6];
+    double dp = 0.0, q = qtr, kk = 0.0, ddp_dth = 0.0, N[6] = {0, 0, 0, 0, 0, 0};
     if (f > 0.0) {
-      double dp = f / (3.0 * G + m.H);
-      double N[6];
+      double kinv, phi = 0.0; /* kinv = d dp / d q_trial */
+      if (m.kind == 1) {
+        dp = f / (3.0 * G + m.H);
+        kinv = 1.0 / (3.0 * G + m.H);
+      } else {
+        /* implicit Euler of the Perzyna law: Newton on
+           g(x) = x - c phi(x)^m, phi(x) = (f - (3G + H) x) / sigma_Y, which is
+           increasing and concave on [0, f / (3G + H)], so Newton from x = 0
+           increases monotonically to the root */
+        const double c = dt / m.t_visc, me = m.m_rate, xmax = f / (3.0 * G + m.H);
+        double x = 0.0;
+        for (int it = 0; it < 200; ++it) {
+          phi = (f - (3.0 * G + m.H) * x) / sy;
+          if (phi < 0.0) phi = 0.0;
+          const double gx = x - c * pow(phi, me);
+          const double gp = 1.0 + c * me * pow(phi, me - 1.0) * (3.0 * G + m.H) / sy;
+          double xn = x - gx / gp;
+          if (xn < 0.0) xn = 0.0;
+          if (xn > xmax) xn = xmax;
+          const double step = fabs(xn - x);
+          x = xn;
+          if (step <= 1e-16 * x) break;
+        }
+        dp = x;
+        phi = (f - (3.0 * G + m.H) * dp) / sy;
+        if (phi < 0.0) phi = 0.0;
+        const double cm = c * me * pow(phi, me - 1.0);
+        kinv = cm / (sy + cm * (3.0 * G + m.H)); /* 1 / (3G + H + h_v) */
+      }
       for (int c = 0; c < 6; ++c) N[c] = s[c] / snorm;
       for (int c = 0; c < 6; ++c) {
         L.sig[c] -= 2.0 * G * sqrt(1.5) * dp * N[c];
         L.znew[c] = zn[c] + sqrt(1.5) * dp * N[c];
       }
       L.znew[6] = zn[6] + dp;
+      q = qtr - 3.0 * G * dp;
       double th1 = 1.0 - 3.0 * G * dp / qtr;
-      double thb = 3.0 * G / (3.0 * G + m.H) - 3.0 * G * dp / qtr;
+      double thb = 3.0 * G * kinv - 3.0 * G * dp / qtr;
       for (int a = 0; a < 6; ++a)
         for (int b = 0; b < 6; ++b) {
           double p1 = M1[a] * M1[b] / 3.0;
           double p2 = (a == b ? 1.0 : 0.0) - p1;
           L.C[a][b] = 3.0 * Kb * p1 + 2.0 * G * th1 * p2 - 2.0 * G * thb * N[a] * N[b];
         }
-      double ddp_dth = -dsy / (3.0 * G + m.H);
-      for (int c = 0; c < 6; ++c) L.tau[c] -= 2.0 * G * sqrt(1.5) * ddp_dth * N[c];
+      /* d dp / d theta from the flow equation at fixed strain */
+      const double dqtr = G > 0.0 ? (dG / G) * qtr : 0.0;
+      ddp_dth = (dqtr - 3.0 * dG * dp - dsy - phi * dsy) * kinv;
+      const double dq = dqtr - 3.0 * dG * dp - 3.0 * G * ddp_dth;
+      /* deviatoric part of dsigma/dtheta: sqrt(2/3) dq/dtheta N */
+      for (int c = 0; c < 6; ++c) L.tau[c] += sqrt(2.0 / 3.0) * (dq - dqtr) * N[c];
+      kk = sqrt(1.5) * 2.0 * G * kinv; /* d dp / d eps = kk N */
       L.D += sy * dp / dt;
       L.diss = sy * dp / dt;
-      double kk = sqrt(1.5) * 2.0 * G / (3.0 * G + m.H); /* d dp / d eps = kk N */
       for (int c = 0; c < 6; ++c) L.d[c] += sy * kk * N[c] / dt;
       L.g += (dsy * dp + sy * ddp_dth) / dt;
     }
+    if (m.kind == 2) {
+      /* theta (r'/r) sigma : (de - deps_p) and its derivatives */
+      const double sf = dr / r, dsf = -sf * sf;
+      double v[6], sv = 0.0, tv = 0.0, Cv[6];
+      for (int c = 0; c < 6; ++c) {
+        v[c] = de[c] - sqrt(1.5) * dp * N[c];
+        sv += L.sig[c] * v[c];
+        tv += L.tau[c] * v[c];
+      }
+      for (int a = 0; a < 6; ++a) {
+        Cv[a] = 0.0;
+        for (int b = 0; b < 6; ++b) Cv[a] += L.C[a][b] * v[b];
+      }
+      L.D += theta * sf * sv / dt;
+      for (int c = 0; c < 6; ++c) L.d[c] += theta * sf * (Cv[c] + L.sig[c] - q * kk * N[c]) / dt;
+      L.g += ((sf + theta * dsf) * sv + theta * sf * (tv - q * ddp_dth)) / dt;
+    }
   }
-  /* pack: sig 6, C 36, tau 6, D, d 6, g, diss, znew 7 = 64 */
+  /* pack: sig 6, C 36, tau 6, D, d 6, g, diss, znew 13 = 70 */
   double *o = outp;
   memcpy(o, L.sig, 6 * sizeof(double)); o += 6;
   memcpy(o, L.C, 36 * sizeof(double)); o += 36;
@@ -267,13 +364,14 @@ void oracle_leaf(const double *matp, const double eps[6], double theta, const do
   memcpy(o, L.d, 6 * sizeof(double)); o += 6;
   *o++ = L.g;
   *o++ = L.diss;
-  memcpy(o, L.znew, 7 * sizeof(double));
+  memcpy(o, L.znew, OR_ZMAX * sizeof(double));
 }
 
 static void leaf_eval(const omat *m, const double eps[6], double theta, const double *zn,
                       double trn, double dt, oleaf *L) {
-  double mp[8] = {(double)m->kind, m->E, m->nu, m->alpha, m->theta0, m->sy0, m->dsy_dT, m->H};
-  double o[64];
+  double mp[OR_MATW] = {(double)m->kind, m->E,  m->nu,     m->alpha,  m->theta0, m->sy0,
+                        m->dsy_dT,       m->H,  m->m_rate, m->t_visc, m->dE_dT,  0.0};
+  double o[70];
   oracle_leaf(mp, eps, theta, zn, trn, dt, o);
   memcpy(L->sig, o, 6 * sizeof(double));
   memcpy(L->C, o + 6, 36 * sizeof(double));
@@ -282,7 +380,7 @@ static void leaf_eval(const omat *m, const double eps[6], double theta, const do
   memcpy(L->d, o + 49, 6 * sizeof(double));
   L->g = o[55];
   L->diss = o[56];
-  memcpy(L->znew, o + 57, 7 * sizeof(double));
+  memcpy(L->znew, o + 57, OR_ZMAX * sizeof(double));
 }
 
 /* ------------------------------------------------------------------ */
@@ -760,7 +858,7 @@ static int eval_point(const otree *t, const omat *mats, const oopts *o, const do
   for (int e = 0; e < 3 * nn; ++e) sout[8 + e] = P.a[e];
   for (int j = 0; j < t->nleaf; ++j)
     if (t->zoff[j] >= 0)
-      for (int c = 0; c < 7; ++c) sout[t->zoff[j] + c] = P.leaf[j].znew[c];
+      for (int c = 0; c < z_words(mats[t->phase[j]].kind); ++c) sout[t->zoff[j] + c] = P.leaf[j].znew[c];
   for (int c = 0; c < 57; ++c)
     if (!isfinite(out[c])) status = OPT_NONFINITE;
 
@@ -778,11 +876,13 @@ static int eval_point(const otree *t, const omat *mats, const oopts *o, const do
 
 static int load_mats(const double *mats, int n_mats, omat *m) {
   for (int i = 0; i < n_mats; ++i) {
-    const double *r = mats + 8 * i;
+    const double *r = mats + OR_MATW * i;
     m[i].kind = (int)r[0];
     m[i].E = r[1]; m[i].nu = r[2]; m[i].alpha = r[3]; m[i].theta0 = r[4];
     m[i].sy0 = r[5]; m[i].dsy_dT = r[6]; m[i].H = r[7];
-    if (m[i].kind != 0 && m[i].kind != 1) return -1;
+    m[i].m_rate = r[8]; m[i].t_visc = r[9]; m[i].dE_dT = r[10];
+    if (m[i].kind < 0 || m[i].kind > 2) return -1;
+    if (m[i].kind == 2 && !(m[i].m_rate >= 1.0 && m[i].t_visc > 0.0)) return -1;
   }
   return 0;
 }

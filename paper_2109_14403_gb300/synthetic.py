@@ -21,7 +21,12 @@ stand in for its strain-controlled virtual experiments, Sec. 5.4):
     7 and 8 with independent seeds; strain increments with a direction
     uniform on the unit sphere of R^6 and a magnitude s0 * LogNormal(0, 1),
     so Newton iteration counts vary from point to point; temperature steps as
-    above.
+    above;
+  * viscoplastic matrix (large configuration): the matrix above with a
+    Perzyna overstress rate law, rate exponent 5, viscous time 1e3 s, and
+    moduli falling 0.2 %/K; K = 9 tree (seed 1234 + 9); 100 increments of
+    dt = 0.01 s with strain rates N(0, 1e-2)/s per Mandel component and the
+    temperature ramped 293 -> 393 K (1 K per increment).
 Units: MPa, K, s.  Symmetric tensors are Mandel 6-vectors.
 """
 from __future__ import annotations
@@ -29,15 +34,38 @@ from __future__ import annotations
 import numpy as np
 
 # material table rows: kind, E, nu, alpha, theta0, sy0, dsy_dT, H
+#   (+ for kind 2: rate exponent m, viscous time t_visc (s), dE_dT (1/K), 0)
 KIND_THERMOELASTIC = 0
 KIND_J2_LINEAR = 1
+KIND_J2_PERZYNA = 2
 FIBER = (KIND_THERMOELASTIC, 72000.0, 0.22, 5e-6, 293.0, 0.0, 0.0, 0.0)
 MATRIX = (KIND_J2_LINEAR, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0)
+MATRIX_PERZYNA = (KIND_J2_PERZYNA, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0, 5.0, 1e3, -0.002, 0.0)
 THETA_START = 293.0
+LARGE_K = 9
+LARGE_DT = 0.01
 
 
 def materials():
     return np.array([FIBER, MATRIX], dtype=np.float64)
+
+
+def materials_viscoplastic():
+    """Fiber and the Perzyna matrix as 12-column rows."""
+    fib = np.zeros(12)
+    fib[:8] = FIBER
+    return np.array([fib, MATRIX_PERZYNA], dtype=np.float64)
+
+
+def large_path(n_points=1048576, n_incr=100, seed=42, dtype=np.float64):
+    """Strain-rate path of the large configuration: deps = rate * dt with rates
+    N(0, 1e-2)/s, theta = 293 + k K at increment k (1-based).
+    Returns (deps[n_incr, n, 6], theta[n_incr, n])."""
+    rng = np.random.default_rng(seed)
+    deps = (rng.standard_normal((n_incr, n_points, 6)) * (1e-2 * LARGE_DT)).astype(dtype)
+    theta = (THETA_START + np.arange(1, n_incr + 1, dtype=np.float64)[:, None]
+             * np.ones((1, n_points))).astype(dtype)
+    return deps, theta
 
 
 def tree(K: int, seed: int | None = None):

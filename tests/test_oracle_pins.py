@@ -446,3 +446,179 @@ def test_newton_residual_decreases_and_converges_superlinearly(mats):
     assert st == 0
     assert np.all(np.diff(hist) < 0)
     assert hist[-1] / hist[-2] < 1e-2
+
+
+# ---------------------------------------------------------------- Perzyna matrix
+# kind 2: J2 viscoplasticity with the overstress rate law of Sec. 4 and
+# temperature-dependent moduli E(theta) = E (1 + dE_dT (theta - theta0))
+def _perzyna(m=5.0, t_visc=1e3, dE=-0.002, sy0=50.0):
+    row = np.array(syn.MATRIX_PERZYNA, dtype=np.float64)
+    row[5], row[8], row[9], row[10] = sy0, m, t_visc, dE
+    return row
+
+
+def _perzyna_case():
+    eps, z7 = _plastic_case()
+    zn = np.zeros(13)
+    zn[:7] = z7
+    zn[7:] = eps - np.random.default_rng(3).normal(0, 2e-3, 6)  # leaf strain at t^n
+    return eps, zn
+
+
+def _trial(row, eps, th, zn):
+    """Independent elastic predictor: moduli at theta, q_trial, f_trial."""
+    r = 1 + row[10] * (th - row[4])
+    C, Kb = iso_stiffness_tensor(row[1] * r, row[2])
+    G = row[1] * r / (2 * (1 + row[2]))
+    m = np.array([1, 1, 1, 0, 0, 0.0])
+    ee = eps - row[3] * (th - row[4]) * m - zn[:6]
+    sig = C @ ee
+    dev = sig - sig[:3].mean() * m
+    q = np.sqrt(1.5) * np.linalg.norm(dev)
+    sy = row[5] + row[6] * (th - row[4])
+    return sig, q, q - sy - row[7] * zn[6], G, sy, C
+
+
+@pytest.mark.parametrize("state", ["elastic", "viscoplastic"])
+def test_perzyna_derivatives_finite_difference(state):
+    """dsigma/deps, dsigma/dtheta, dD/deps and dD/dtheta of the Perzyna leaf
+    against central differences of its stress and coupling term."""
+    row = _perzyna(sy0=1e6 if state == "elastic" else 50.0, t_visc=2.0)
+    eps, zn = _perzyna_case()
+    th, dt = 320.0, 0.5
+    r = oracle.leaf(row, eps, th, zn, 0.0, dt)
+    assert (r["znew"][6] > zn[6]) == (state == "viscoplastic")
+    h = 1e-8
+    for c in range(6):
+        e1, e2 = eps.copy(), eps.copy()
+        e1[c] += h
+        e2[c] -= h
+        a, b = oracle.leaf(row, e1, th, zn, 0.0, dt), oracle.leaf(row, e2, th, zn, 0.0, dt)
+        np.testing.assert_allclose((a["sig"] - b["sig"]) / (2 * h), r["C"][:, c], rtol=1e-6,
+                                   atol=1e-6 * np.abs(r["C"]).max())
+        assert (a["D"] - b["D"]) / (2 * h) == pytest.approx(r["d"][c], rel=1e-6, abs=1e-6)
+    ht = 1e-4
+    a, b = oracle.leaf(row, eps, th + ht, zn, 0.0, dt), oracle.leaf(row, eps, th - ht, zn, 0.0, dt)
+    np.testing.assert_allclose((a["sig"] - b["sig"]) / (2 * ht), r["tau"], rtol=1e-6, atol=1e-8)
+    assert (a["D"] - b["D"]) / (2 * ht) == pytest.approx(r["g"], rel=1e-6, abs=1e-9)
+
+
+def test_perzyna_linear_rate_closed_form():
+    """m = 1: the implicit Euler step dp = c phi(dp) is linear in dp, so
+    dp = c f / (sigma_Y + c (3G + H)), c = dt / t_visc."""
+    row = _perzyna(m=1.0, t_visc=3.0)
+    eps, zn = _perzyna_case()
+    th, dt = 330.0, 0.7
+    _, q, f, G, sy, _ = _trial(row, eps, th, zn)
+    assert f > 0
+    c = dt / row[9]
+    dp = c * f / (sy + c * (3 * G + row[7]))
+    r = oracle.leaf(row, eps, th, zn, 0.0, dt)
+    assert r["znew"][6] - zn[6] == pytest.approx(dp, rel=1e-12)
+    # and the returned stress has the radial-return form with that dp
+    sig_tr, *_ = _trial(row, eps, th, zn)
+    m = np.array([1, 1, 1, 0, 0, 0.0])
+    dev = sig_tr - sig_tr[:3].mean() * m
+    np.testing.assert_allclose(r["sig"], sig_tr - 3 * G * dp / q * dev, rtol=1e-12, atol=1e-9)
+
+
+def test_perzyna_limits():
+    """Fast limit (t_visc -> 0): the rate-independent J2 leaf; slow limit
+    (t_visc -> infinity): the elastic predictor.  Moduli held constant.  The
+    overstress vanishes like (dt/t_visc)^(-1/m), so the fast limit is taken
+    with m = 1 (relative gap sigma_Y / (c (3G + H)) ~ 4e-14)."""
+    eps, zn = _perzyna_case()
+    th, dt = 320.0, 0.5
+    fast = oracle.leaf(_perzyna(m=1.0, t_visc=1e-12, dE=0.0), eps, th, zn, 0.0, dt)
+    j2 = oracle.leaf(syn.MATRIX, eps, th, zn[:7], zn[7:10].sum(), dt)
+    np.testing.assert_allclose(fast["sig"], j2["sig"], rtol=1e-7, atol=1e-6)
+    np.testing.assert_allclose(fast["znew"][:7], j2["znew"], rtol=1e-7, atol=1e-10)
+    np.testing.assert_allclose(fast["C"], j2["C"], rtol=1e-5, atol=1e-3)
+    assert fast["D"] == pytest.approx(j2["D"], rel=1e-6)
+    assert fast["diss"] == pytest.approx(j2["diss"], rel=1e-6)
+    slow = oracle.leaf(_perzyna(t_visc=1e20, dE=0.0), eps, th, zn, 0.0, dt)
+    sig_tr, *_ = _trial(_perzyna(dE=0.0), eps, th, zn)
+    np.testing.assert_allclose(slow["sig"], sig_tr, rtol=1e-9, atol=1e-9)
+    assert slow["diss"] < 1e-12
+
+
+def test_perzyna_moduli_follow_temperature():
+    """Below yield the Perzyna leaf is the thermoelastic law with the stiffness
+    of E (1 + dE_dT (theta - theta0)) (Sec. 4 projector form, index notation)."""
+    row = _perzyna(sy0=1e6, dE=-0.002)
+    eps, zn = _perzyna_case()
+    for th in (293.0, 350.0, 393.0):
+        r = oracle.leaf(row, eps, th, zn, 0.0, 0.01)
+        sig, *_ = _trial(row, eps, th, zn)
+        np.testing.assert_allclose(r["sig"], sig, rtol=1e-12, atol=1e-10)
+        C, _ = iso_stiffness_tensor(2500.0 * (1 - 0.002 * (th - 293.0)), 0.38)
+        np.testing.assert_allclose(r["C"], C, rtol=1e-12, atol=1e-9)
+
+
+def test_perzyna_coupling_term_from_free_energy():
+    """The thermal part of D, theta psi_{,theta eps} : eps_dot + theta
+    psi_{,theta z} . z_dot, taken by finite differences of the free energy
+    psi = 1/2 (eps-ep):C(theta)(eps-ep) - (eps-ep):C(theta)[alpha (theta-theta0)]
+    + H p^2/2 with C(theta) = r(theta) C; the remaining, dissipative part is the
+    paper's sigma_Y p_dot (Sec. 4), equal to Diss."""
+    row = _perzyna(t_visc=2.0, dE=-0.002)
+    eps, zn = _perzyna_case()
+    th, dt = 320.0, 0.5
+    r = oracle.leaf(row, eps, th, zn, 0.0, dt)
+    assert r["diss"] > 0
+    m = np.array([1, 1, 1, 0, 0, 0.0])
+
+    def psi(e, T, z):
+        C, _ = iso_stiffness_tensor(2500.0 * (1 - 0.002 * (T - 293.0)), 0.38)
+        ee = e - z[:6]
+        return 0.5 * ee @ C @ ee - ee @ C @ (8e-5 * (T - 293.0) * m) + 0.5 * 300.0 * z[6] ** 2
+
+    z1 = r["znew"][:7]
+    # psi is quadratic in eps and z and its gradient quadratic in theta, so
+    # central differences are exact up to rounding: take wide steps
+    hz, hT = 1e-4, 1e-2
+
+    def grad(T, wrt):
+        g = np.zeros(6 if wrt == "e" else 7)
+        for c in range(g.size):
+            if wrt == "e":
+                a_, b_ = eps.copy(), eps.copy()
+                a_[c] += hz
+                b_[c] -= hz
+                g[c] = (psi(a_, T, z1) - psi(b_, T, z1)) / (2 * hz)
+            else:
+                a_, b_ = z1.copy(), z1.copy()
+                a_[c] += hz
+                b_[c] -= hz
+                g[c] = (psi(eps, T, a_) - psi(eps, T, b_)) / (2 * hz)
+        return g
+
+    d2_te = (grad(th + hT, "e") - grad(th - hT, "e")) / (2 * hT)
+    d2_tz = (grad(th + hT, "z") - grad(th - hT, "z")) / (2 * hT)
+    edot = (eps - zn[7:]) / dt
+    zdot = (z1 - zn[:7]) / dt
+    thermal = th * d2_te @ edot + th * d2_tz @ zdot
+    assert r["D"] - r["diss"] == pytest.approx(thermal, rel=1e-6, abs=1e-9)
+
+
+def test_perzyna_homogeneous_tree_gives_phase_response():
+    """All leaves Perzyna: zero jumps, and the DMN returns the leaf law."""
+    K = 3
+    mats = syn.materials_viscoplastic()
+    t, w, n = make_tree(K, mats, phase=np.ones(2 ** K, np.uint8))
+    s = t.init_state(1, 293.0)
+    eps, _ = _plastic_case()
+    sout, out, st, _ = oracle.eval_batch(t, eps[None], [320.0], 0.5, s)
+    assert st[0] == 0
+    o = oracle.split_out(out[0])
+    r = oracle.leaf(mats[1], eps, 320.0, np.zeros(13), 0.0, 0.5)
+    assert np.abs(sout[0, 8:8 + 3 * t.nnode]).max() < 1e-12
+    np.testing.assert_allclose(o["sig"], r["sig"], rtol=1e-11, atol=1e-9)
+    np.testing.assert_allclose(o["C"], r["C"], rtol=1e-9, atol=1e-7)
+    np.testing.assert_allclose(o["C_theta"], r["tau"], rtol=1e-9, atol=1e-9)
+    assert o["D"] == pytest.approx(r["D"], rel=1e-10)
+    np.testing.assert_allclose(o["D_eps"], r["d"], rtol=1e-9, atol=1e-9)
+    assert o["D_theta"] == pytest.approx(r["g"], rel=1e-9, abs=1e-12)
+    # state: every leaf's z = the leaf law's, including its strain
+    z = sout[0, 8 + 3 * t.nnode:8 + 3 * t.nnode + 13]
+    np.testing.assert_allclose(z, r["znew"], rtol=1e-12, atol=1e-15)
