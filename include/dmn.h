@@ -70,7 +70,13 @@ enum {
 /* phase laws (Sec. 4) */
 enum {
   DMN_MAT_THERMOELASTIC = 0, /* sigma = C[eps - alpha (theta - theta0) I] */
-  DMN_MAT_J2_LINEAR = 1      /* J2 plasticity, linear isotropic hardening  */
+  DMN_MAT_J2_LINEAR = 1,     /* J2 plasticity, linear isotropic hardening  */
+  DMN_MAT_J2_PERZYNA = 2     /* J2 viscoplasticity with the overstress rate
+                                law of Sec. 4 (p_dot = (1/t_visc)
+                                <(q - sigma_Y - H p)/sigma_Y>^m), linear
+                                hardening, moduli E (1 + dE_dT (theta -
+                                theta0)); internal variables eps_p, p and
+                                the leaf strain (13 words)                */
 };
 
 typedef struct {
@@ -84,6 +90,10 @@ typedef struct {
   double dsy_dT;  /* J2: yield-stress slope (MPa/K); sigma_Y is floored at
                      1e-6 MPa                                               */
   double H;       /* J2: linear isotropic hardening modulus (MPa), >= 0     */
+  double m_rate;  /* Perzyna: rate exponent m, an integer in 1..8           */
+  double t_visc;  /* Perzyna: viscous time (s), > 0                         */
+  double dE_dT;   /* Perzyna: relative modulus slope (1/K); the factor
+                     1 + dE_dT (theta - theta0) is floored at 1e-3          */
 } dmn_material;
 
 enum { DMN_PREC_FP64 = 0, DMN_PREC_MIXED = 1 };

@@ -119,6 +119,9 @@ __device__ __forceinline__ double tf_of(double x, double *) { return x; }
 __device__ __forceinline__ float tf_of(dfl x, float *) { return x.hi; }
 __device__ __forceinline__ double hp_d(double x) { return x; }
 __device__ __forceinline__ double hp_d(dfl x) { return double(x.hi); }
+// a + d with d in the condensation precision (float-float + float, or double)
+__device__ __forceinline__ double hp_add_tf(double a, double d) { return a + d; }
+__device__ __forceinline__ dfl hp_add_tf(dfl a, float d) { return a + dfl{d, 0.0f}; }
 __device__ __forceinline__ double hp_zero(double *) { return 0.0; }
 __device__ __forceinline__ dfl hp_zero(dfl *) { return {0.0f, 0.0f}; }
 // x > y exactly (hi dominates lo)

@@ -23,11 +23,47 @@ struct dmn_handle_s {
   double *d_node;        // [N][kNodeWords]
   float *d_node_df;      // [N][kNodeDfl]
   double *d_leafw;       // [nleaf]
-  int nz;                // leaves with internal variables
+  int zw;                // words of internal variables per state block
+  int law;               // largest material kind (1: kinds 0/1, 2: Perzyna leaves)
   uint8_t *d_phase;      // [nleaf]
   int *d_zoff;           // [nleaf]
-  double *d_mat;         // [n_mats][8]
+  double *d_mat;         // [n_mats][kMatWords]
 };
+
+namespace dmn {
+int material_z_words(int kind) {
+  return kind == DMN_MAT_J2_LINEAR ? 7 : (kind == DMN_MAT_J2_PERZYNA ? 13 : 0);
+}
+
+// Sec. 4: K = E/(3(1-2nu)), G = E/(2(1+nu)); the device row holds the moduli at
+// theta0 and, for the Perzyna leaf, m, 1/t_visc and dE_dT
+const char *material_row(const dmn_material &m, double r[kMatWords]) {
+  if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR && m.kind != DMN_MAT_J2_PERZYNA)
+    return "unknown kind";
+  if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
+    return "invalid elastic constants";
+  const bool j2 = m.kind != DMN_MAT_THERMOELASTIC;
+  if (j2 && (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
+    return "invalid J2 constants";
+  const bool vp = m.kind == DMN_MAT_J2_PERZYNA;
+  if (vp && (!(m.m_rate >= 1.0 && m.m_rate <= 8.0) || m.m_rate != floor(m.m_rate) ||
+             !(m.t_visc > 0.0) || !isfinite(m.t_visc) || !isfinite(m.dE_dT)))
+    return "invalid Perzyna constants (m an integer in 1..8, t_visc > 0)";
+  r[0] = m.kind;
+  r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+  r[2] = m.E / (2.0 * (1.0 + m.nu));
+  r[3] = m.alpha;
+  r[4] = m.theta0;
+  r[5] = j2 ? m.sy0 : 0.0;
+  r[6] = j2 ? m.dsy_dT : 0.0;
+  r[7] = j2 ? m.H : 0.0;
+  r[8] = vp ? m.m_rate : 0.0;
+  r[9] = vp ? 1.0 / m.t_visc : 0.0;
+  r[10] = vp ? m.dE_dT : 0.0;
+  r[11] = 0.0;
+  return nullptr;
+}
+}  // namespace dmn
 
 static thread_local char g_err[512] = "";
 
@@ -92,28 +128,13 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
                 o.solve_variant);
   const int nleaf = 1 << K, N = nleaf - 1;
 
-  // materials: derived bulk and shear moduli (Sec. 4: K = E/(3(1-2nu)), G = E/(2(1+nu)))
-  std::vector<double> mat(8 * n_mats);
+  // materials: derived bulk and shear moduli (Sec. 4)
+  std::vector<double> mat(kMatWords * n_mats);
   double Emax = 0.0;
   for (int i = 0; i < n_mats; ++i) {
-    const dmn_material &m = mats[i];
-    if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR)
-      return fail(DMN_ERR_ARG, "dmn_create: material %d has unknown kind %d", i, m.kind);
-    if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
-      return fail(DMN_ERR_ARG, "dmn_create: material %d has invalid elastic constants", i);
-    if (m.kind == DMN_MAT_J2_LINEAR &&
-        (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
-      return fail(DMN_ERR_ARG, "dmn_create: material %d has invalid J2 constants", i);
-    double *r = &mat[8 * i];
-    r[0] = m.kind;
-    r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
-    r[2] = m.E / (2.0 * (1.0 + m.nu));
-    r[3] = m.alpha;
-    r[4] = m.theta0;
-    r[5] = m.kind == DMN_MAT_J2_LINEAR ? m.sy0 : 0.0;
-    r[6] = m.kind == DMN_MAT_J2_LINEAR ? m.dsy_dT : 0.0;
-    r[7] = m.kind == DMN_MAT_J2_LINEAR ? m.H : 0.0;
-    if (m.E > Emax) Emax = m.E;
+    const char *why = material_row(mats[i], &mat[kMatWords * i]);
+    if (why) return fail(DMN_ERR_ARG, "dmn_create: material %d (kind %d): %s", i, mats[i].kind, why);
+    if (mats[i].E > Emax) Emax = mats[i].E;
   }
   if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
 
@@ -173,18 +194,21 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   }
   // z offsets in a state block
   std::vector<int> zoff(nleaf);
-  int off = 8 + 3 * N;
+  int off = 8 + 3 * N, law = 1;
   for (int j = 0; j < nleaf; ++j) {
-    if (mats[phase_map[j]].kind == DMN_MAT_J2_LINEAR) {
+    const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
+    if (kind == DMN_MAT_J2_PERZYNA) law = 2;
+    if (zwl > 0) {
       zoff[j] = off;
-      off += 7;
+      off += zwl;
     } else {
       zoff[j] = -1;
     }
   }
   const int zend = off;
-  const int nz = (zend - (8 + 3 * N)) / 7;
+  const int zw = zend - (8 + 3 * N);
   if (off & 1) off += 1;
+  if (law == 2 && K > 9) return fail(DMN_ERR_ARG, "dmn_create: Perzyna leaves need K <= 9 (K=%d)", K);
 
   dmn_handle h = new dmn_handle_s();
   memset(h, 0, sizeof(*h));
@@ -194,7 +218,8 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   h->SW = off;
   h->zend = zend;
   h->n_mats = n_mats;
-  h->nz = nz;
+  h->zw = zw;
+  h->law = law;
   h->opt = o;
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { free_handle(h); return cuda_fail(e, "cudaGetDevice"); }
@@ -206,11 +231,11 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (solve_smem_bytes(K, nz, n_mats, mixed, o.solve_variant) > (size_t)smem_optin) {
+    if (solve_smem_bytes(K, zw, n_mats, mixed, o.solve_variant, law) > (size_t)smem_optin) {
       free_handle(h);
       return fail(DMN_ERR_ARG, "dmn_create: K=%d does not fit one SM in the requested precision", K);
     }
-    if ((e = prepare_solve(K, nz, n_mats, mixed, o.solve_variant, &h->blocks_per_sm)) != cudaSuccess) {
+    if ((e = prepare_solve(K, zw, n_mats, mixed, o.solve_variant, law, &h->blocks_per_sm)) != cudaSuccess) {
       free_handle(h);
       return cuda_fail(e, "prepare_solve");
     }
@@ -224,7 +249,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (e = cudaMalloc(&h->d_node_df, sizeof(float) * kNodeDfl * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_mat, sizeof(double) * 8 * n_mats)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_mat, sizeof(double) * kMatWords * n_mats)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMalloc");
@@ -234,7 +259,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (e = cudaMemcpy(h->d_node_df, node_df.data(), sizeof(float) * kNodeDfl * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_phase, phase_map, nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_zoff, zoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * 8 * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * kMatWords * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMemcpy");
   }
@@ -313,7 +338,8 @@ static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
   P.node = h->d_node;
   P.leafw = h->d_leafw;
   P.node_df = h->d_node_df;
-  P.nz = h->nz;
+  P.zw = h->zw;
+  P.law = h->law;
   P.phase = h->d_phase;
   P.zoff = h->d_zoff;
   P.mat = h->d_mat;

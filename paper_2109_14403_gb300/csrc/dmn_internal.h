@@ -3,17 +3,27 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/dmn.h"
 #include "dmn_kernels.cuh"
 
 namespace dmn {
-// shared memory of the selected solve kernel (variant as in dmn_options)
-size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed, int variant);
+// shared memory of the selected solve kernel (variant as in dmn_options; law:
+// largest material kind of the tree, 1 or 2; zw: internal-variable words)
+size_t solve_smem_bytes(int K, int zw, int n_mats, bool mixed, int variant, int law);
 bool solve_variant_valid(int variant);
-// the compact solve kernel (dmn_solve_compact.cu), depth K <= 8
+// the compact solve kernel: dmn_solve_compact.cu (kinds 0 and 1, K <= 8) and
+// dmn_solve_compact_vp.cu (also kind 2, K <= 9)
 using KernelFn = void (*)(const SolveParams);
-size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed);
+size_t compact_smem_bytes(int K, int zw, int n_mats, bool mixed);
 KernelFn compact_kernel(int K, bool mixed, int minb);
-cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm);
+KernelFn compact_kernel_vp(int K, bool mixed);
+// host: validate a material and write its device row (kMatWords doubles);
+// returns nullptr or the reason it is invalid
+const char *material_row(const dmn_material &m, double row[kMatWords]);
+// words of internal variables of a leaf of this kind (0, 7 or 13)
+int material_z_words(int kind);
+cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
+                          int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);
 // message returned by dmn_last_error() on this thread
 void set_error_message(const char *msg);

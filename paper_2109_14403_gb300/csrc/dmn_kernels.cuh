@@ -40,14 +40,17 @@ constexpr int kOutWords = 57;
 constexpr int kNodeWords = 12;  // FP64 node table row
 constexpr int kNodeDfl = 20;    // float-float node table row (floats)
 
+constexpr int kMatWords = 12;  // device material row
 struct MatDev {
-  double kind, Kb, G, alpha, theta0, sy0, dsy, H;
+  double kind, Kb, G, alpha, theta0, sy0, dsy, H;  // moduli at theta0
+  double mexp, itv, cE, pad_;  // Perzyna: rate exponent, 1 / t_visc, dE_dT / E
 };
 
 struct SolveParams {
   int K, N, G, SW;         // depth, nodes, threads per point, state words
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
-  int nz, pad2_;                   // number of leaves with internal variables
+  int zw;                          // words of internal variables per state block
+  int law;                         // largest material kind of the tree (1 or 2)
   unsigned long long *queue;       // device counter of points taken (zeroed per launch)
   const float *da0;                // optional warm-start increment [n][3N] (NULL: start at a^n)
   double tol, gamma, res_floor, dt;
@@ -58,7 +61,7 @@ struct SolveParams {
   const double *leafw;     // [2^K] leaf weights
   const uint8_t *phase;    // [2^K]
   const int *zoff;         // [2^K]: offset of the leaf's z in a state block, -1 none
-  const double *mat;       // [n_mats][8] as MatDev
+  const double *mat;       // [n_mats][kMatWords] as MatDev
   int64_t n_points;
   const double *deps, *theta, *sin;
   double *sout, *out;
@@ -110,21 +113,27 @@ constexpr int kRecWords = 40;  // exchange slot in doubles
 // Constants of one material.  The static part is built once per CTA (FP64 is
 // fine there); the part that depends on the point's temperature theta is
 // formed per point in the high-precision type HP, so the mixed path stays on
-// the FP32 pipe.
+// the FP32 pipe.  Kind 2 (Perzyna) scales its moduli with theta per point.
 template <typename TF, typename HP>
 struct MatPt {
   HP Kb, G2, G3, iden, H, a3K, alpha, theta0, sy0, dsy, symin, third, c15, one;
   TF a3K_f, G2_f, G3_f, Kb_f, iden_f, dsy0_f;
-  int j2;
+  int kind, mexp;
+  // kind 2, static: moduli at theta0, modulus slope, c = dt / t_visc, floor of r
+  HP Kb0, G20, G30, a3K0, cE, cvisc, rmin;
+  TF cvisc_f, cE_f, Kb0_f, H_f;
   // per point
   HP ath;        // alpha (theta - theta0)
   HP a3Kth_idt;  // 3 K alpha theta / dt
   HP sy, syidt;  // sigma_Y(theta) (floored at 1e-6 MPa), sigma_Y / dt
   TF a3K_idt_f, dsy_f, sy_f, idt_f;
+  // per point, kind 2
+  HP isy, thsE_idt;  // 1 / sigma_Y, theta (r'/r) / dt
+  TF sE_f, th_f, dKb_f, thsE_idt_f, gj_f, af_f;  // r'/r, theta, dK/dtheta, ..., 3 alpha dK/dtheta theta / dt, 3G + H
 };
 
 template <typename TF, typename HP>
-__device__ __forceinline__ void mat_static(MatPt<TF, HP> &o, const MatDev &m) {
+__device__ __forceinline__ void mat_static(MatPt<TF, HP> &o, const MatDev &m, double dt) {
   HP *tag = nullptr;
   const double den = 3.0 * m.G + m.H;
   o.Kb = hp_from(m.Kb, tag);
@@ -147,12 +156,50 @@ __device__ __forceinline__ void mat_static(MatPt<TF, HP> &o, const MatDev &m) {
   o.Kb_f = TF(m.Kb);
   o.iden_f = TF(1.0 / den);
   o.dsy0_f = TF(m.dsy);
-  o.j2 = m.kind > 0.5;
+  o.kind = int(m.kind + 0.5);
+  o.mexp = int(m.mexp + 0.5);
+  o.Kb0 = o.Kb;
+  o.G20 = o.G2;
+  o.G30 = o.G3;
+  o.a3K0 = o.a3K;
+  o.cE = hp_from(m.cE, tag);
+  o.cvisc = hp_from(dt * m.itv, tag);
+  o.rmin = hp_from(1e-3, tag);
+  o.cvisc_f = TF(dt * m.itv);
+  o.cE_f = TF(m.cE);
+  o.Kb0_f = TF(m.Kb);
+  o.H_f = TF(m.H);
 }
 
-template <typename TF, typename HP>
+template <typename TF, typename HP, int LAW>
 __device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, HP theta, HP idt, TF idt_f) {
   const HP dth = theta - o.theta0;
+  if (LAW >= 2 && o.kind == 2) {
+    // moduli E (1 + dE_dT (theta - theta0)), the factor floored at 1e-3
+    HP r = o.one + o.cE * dth;
+    TF dr = o.cE_f;
+    if (tf_of(r, (TF *)nullptr) < TF(1e-3)) {
+      r = o.rmin;
+      dr = TF(0);
+    }
+    o.Kb = o.Kb0 * r;
+    o.G2 = o.G20 * r;
+    o.G3 = o.G30 * r;
+    o.a3K = o.a3K0 * r;
+    o.Kb_f = tf_of(o.Kb, (TF *)nullptr);
+    o.G2_f = tf_of(o.G2, (TF *)nullptr);
+    o.G3_f = tf_of(o.G3, (TF *)nullptr);
+    o.a3K_f = tf_of(o.a3K, (TF *)nullptr);
+    o.af_f = o.G3_f + o.H_f;
+    o.iden_f = TF(1) / o.af_f;
+    const TF rf = tf_of(r, (TF *)nullptr);
+    o.sE_f = dr / rf;
+    o.th_f = tf_of(theta, (TF *)nullptr);
+    o.dKb_f = o.Kb0_f * dr;
+    o.thsE_idt_f = o.th_f * o.sE_f * idt_f;
+    o.gj_f = TF(3) * tf_of(o.alpha, (TF *)nullptr) * o.dKb_f * o.th_f * idt_f;
+    o.thsE_idt = dr == TF(0) ? hp_zero((HP *)nullptr) : hp_div(o.cE * theta * idt, r);
+  }
   o.ath = o.alpha * dth;
   o.a3Kth_idt = o.a3K * theta * idt;
   HP sy = o.sy0 + o.dsy * dth;
@@ -167,18 +214,28 @@ __device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, HP theta, HP idt, TF
   o.dsy_f = dsy;
   o.sy_f = tf_of(sy, (TF *)nullptr);
   o.idt_f = idt_f;
+  if (LAW >= 2 && o.kind == 2) o.isy = hp_div(o.one, sy);
 }
 
 // Leaf update at strain eps and the point's temperature (Sec. 4).  Stress,
 // coupling term D and dissipation X in HP; derivatives into the TF record.
-// zn = internal variables at t^n (J2 only; eps_p Mandel 6, p), trn = trace of
-// the leaf strain at t^n.  J2 radial return with linear hardening, written as
+// zn = internal variables at t^n (eps_p Mandel 6, p; kind 2 also the leaf
+// strain at t^n), trn = trace of the leaf strain at t^n (kinds 0 and 1).
+// J2 radial return with linear hardening, written as
 // sigma = K tr(ee) I + th1 s_tr, d eps_p = (3/2)(dp/q_tr) s_tr, th1 = 1 - 3G dp/q_tr;
 // the yield test compares squares, so elastic leaves take no square root.
-template <typename TF, typename HP>
+// Kind 2 (LAW >= 2): dp solves the implicit Euler step of the overstress law,
+// dp = c phi^m, phi = (q_tr - (3G + H) dp - sigma_Y - H p^n) / sigma_Y, by
+// Newton in TF (g concave and increasing: monotone from dp = 0) and two
+// Newton corrections in HP; the tangent is the radial-return one with
+// 1/(3G + H) replaced by c m phi^(m-1) / (sigma_Y + c m phi^(m-1) (3G + H));
+// temperature-dependent moduli add theta (r'/r) sigma : (de - d eps_p) / dt
+// to D, de the leaf's strain increment.
+template <typename TF, typename HP, int LAW>
 __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6], const HP *zn,
                                           HP trn, HP sig[6], HP &D, HP &X, Rec<TF> &R, HP *znew) {
-  const bool j2 = m.j2;
+  const bool j2 = m.kind >= 1;
+  const bool vp = LAW >= 2 && m.kind == 2;
   HP ee[6];
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -191,13 +248,24 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
 #pragma unroll
   for (int c = 0; c < 6; ++c) s[c] = m.G2 * (c < 3 ? ee[c] - tr3 : ee[c]);
   const HP pk = m.Kb * tr;
-  const HP treps = eps[0] + eps[1] + eps[2];
-  const HP dtr = treps - trn;
+  HP dtr;
+  HP de[6];
+  if (vp) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) de[c] = eps[c] - zn[7 + c];
+    dtr = de[0] + de[1] + de[2];
+  } else {
+    const HP treps = eps[0] + eps[1] + eps[2];
+    dtr = treps - trn;
+  }
   D = -(m.a3Kth_idt * dtr);
   X = hp_zero((HP *)nullptr);
   TF gg = -m.a3K_idt_f * tf_of(dtr, (TF *)nullptr);
+  if (vp) gg -= m.gj_f * tf_of(dtr, (TF *)nullptr);
   TF th1 = TF(1), thb = TF(0), kd = TF(0), ktau = TF(0);
   TF Nf[6] = {TF(0), TF(0), TF(0), TF(0), TF(0), TF(0)};
+  TF qf = TF(0), kkf = TF(0), ddpf = TF(0);  // kind 2: q, d dp / d eps factor, d dp / d theta
+  HP kzs = hp_zero((HP *)nullptr);           // kind 2: d eps_p = kzs s_tr
   bool plastic = false;
   if (j2) {
     HP sn2 = s[0] * s[0];
@@ -207,9 +275,50 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
     const HP q2 = m.c15 * sn2;
     plastic = hp_gt(q2, yr * yr);
     if (plastic) {
-      const HP q = hp_sqrt(q2);                // q_tr = sqrt(3/2) |s_tr|
-      const HP dp = (q - yr) * m.iden;         // closed-form plastic multiplier
-      const HP kap = hp_div(dp, q);            // dp / q_tr
+      const HP q = hp_sqrt(q2);  // q_tr = sqrt(3/2) |s_tr|
+      HP dp;
+      TF kinv = m.iden_f, phif = TF(0);
+      if (vp) {
+        const HP f = q - yr;
+        const TF ff = tf_of(f, (TF *)nullptr), af = m.af_f, isyf = TF(1) / m.sy_f;
+        const TF cf = m.cvisc_f, xmax = ff / af;
+        const int me = m.mexp;
+        TF x = TF(0), gp = TF(1);
+        for (int it = 0; it < 64; ++it) {
+          TF phi = (ff - af * x) * isyf;
+          if (phi < TF(0)) phi = TF(0);
+          TF pw = TF(1);
+          for (int k = 1; k < me; ++k) pw *= phi;  // phi^(m-1)
+          const TF gx = x - cf * pw * phi;
+          gp = TF(1) + cf * TF(me) * pw * af * isyf;
+          TF xn = x - gx / gp;
+          if (xn < TF(0)) xn = TF(0);
+          if (xn > xmax) xn = xmax;
+          const TF step = fabs(xn - x);
+          x = xn;
+          if (!(step > TF(sizeof(TF) == 4 ? 1e-7 : 1e-15) * x)) break;
+        }
+        // two corrections in HP with the TF derivative
+        dp = hp_add_tf(hp_zero((HP *)nullptr), x);
+        const TF igp = TF(1) / gp;
+        for (int k2 = 0; k2 < 2; ++k2) {
+          HP ph = (f - (m.G3 + m.H) * dp) * m.isy;
+          if (tf_of(ph, (TF *)nullptr) < TF(0)) ph = hp_zero((HP *)nullptr);
+          HP pwm = ph;
+          for (int k = 1; k < me; ++k) pwm = pwm * ph;  // phi^m
+          const HP g = dp - m.cvisc * pwm;
+          dp = dp - g * igp;
+        }
+        phif = tf_of((f - (m.G3 + m.H) * dp) * m.isy, (TF *)nullptr);
+        if (phif < TF(0)) phif = TF(0);
+        TF pw = TF(1);
+        for (int k = 1; k < me; ++k) pw *= phif;
+        const TF cm = cf * TF(me) * pw;
+        kinv = cm / (m.sy_f + cm * af);  // 1 / (3G + H + h_v)
+      } else {
+        dp = (q - yr) * m.iden;  // closed-form plastic multiplier
+      }
+      const HP kap = hp_div(dp, q);  // dp / q_tr
       const HP th1h = m.one - m.G3 * kap;
       const HP kz = m.c15 * kap;
 #pragma unroll
@@ -218,21 +327,35 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
         znew[c] = zn[c] + kz * s[c];
       }
       znew[6] = zn[6] + dp;
+      kzs = kz;
       const HP dis = m.syidt * dp;
       D = D + dis;
       X = dis;
       const TF kapf = tf_of(kap, (TF *)nullptr), dpf = tf_of(dp, (TF *)nullptr);
       th1 = TF(1) - m.G3_f * kapf;
-      thb = m.G3_f * m.iden_f - m.G3_f * kapf;
+      thb = m.G3_f * kinv - m.G3_f * kapf;
       const TF isn = TF(1) / sqrt(tf_of(sn2, (TF *)nullptr));
 #pragma unroll
       for (int c = 0; c < 6; ++c) Nf[c] = tf_of(s[c], (TF *)nullptr) * isn;
-      ktau = m.G2_f * TF(1.2247448713915890491) * m.dsy_f * m.iden_f;
-      kd = m.sy_f * TF(1.2247448713915890491) * m.G2_f * m.iden_f * m.idt_f;
-      gg += (m.dsy_f * dpf - m.sy_f * m.dsy_f * m.iden_f) * m.idt_f;
+      if (vp) {
+        qf = tf_of(q, (TF *)nullptr) - m.G3_f * dpf;  // updated equivalent stress
+        ddpf = (m.sE_f * qf - m.dsy_f * (TF(1) + phif)) * kinv;
+        ktau = TF(0.81649658092772603273) * (m.sE_f * qf - m.G3_f * ddpf);  // sqrt(2/3) dq/dtheta
+        kkf = TF(1.2247448713915890491) * m.G2_f * kinv;
+        kd = m.sy_f * kkf * m.idt_f;
+        gg += (m.dsy_f * dpf + m.sy_f * ddpf) * m.idt_f;
+      } else {
+        ktau = m.G2_f * TF(1.2247448713915890491) * m.dsy_f * m.iden_f;
+        kd = m.sy_f * TF(1.2247448713915890491) * m.G2_f * m.iden_f * m.idt_f;
+        gg += (m.dsy_f * dpf - m.sy_f * m.dsy_f * m.iden_f) * m.idt_f;
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 7; ++c) znew[c] = zn[c];
+    }
+    if (vp) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) znew[7 + c] = eps[c];
     }
   }
   if (!plastic) {
@@ -248,13 +371,46 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
 #pragma unroll
     for (int j = i; j < 6; ++j)
       R.C[sidx(i, j)] = (i < 3 && j < 3 ? cP1 : TF(0)) + (i == j ? cI : TF(0)) - cN * Nf[i] * Nf[j];
-  const TF ta = -m.a3K_f;
+  TF ta = -m.a3K_f;
+  if (vp) ta += m.dKb_f * tf_of(tr, (TF *)nullptr);
   const TF da_ = -tf_of(m.a3Kth_idt, (TF *)nullptr);
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     R.tau[c] = (c < 3 ? ta : TF(0)) + ktau * Nf[c];
     R.dd[c] = (c < 3 ? da_ : TF(0)) + kd * Nf[c];
     R.ds[c] = TF(0);
+  }
+  if (vp) {
+    // elastic leaf: the deviatoric stress scales with the moduli
+    if (!plastic) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) R.tau[c] += m.sE_f * tf_of(s[c], (TF *)nullptr);
+    }
+    // theta (r'/r) sigma : v / dt with v = de - d eps_p, and its derivatives
+    HP v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = plastic ? de[c] - kzs * s[c] : de[c];
+    HP sv = sig[0] * v[0];
+#pragma unroll
+    for (int c = 1; c < 6; ++c) sv = sv + sig[c] * v[c];
+    D = D + m.thsE_idt * sv;
+    TF vf[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) vf[c] = tf_of(v[c], (TF *)nullptr);
+    const TF mv = vf[0] + vf[1] + vf[2];
+    TF Nv = TF(0), tv = TF(0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      Nv += Nf[c] * vf[c];
+      tv += R.tau[c] * vf[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const TF Cv = (c < 3 ? cP1 * mv : TF(0)) + cI * vf[c] - cN * Nf[c] * Nv;
+      R.dd[c] += m.thsE_idt_f * (Cv + tf_of(sig[c], (TF *)nullptr) - qf * kkf * Nf[c]);
+    }
+    const TF svf = tf_of(sv, (TF *)nullptr);
+    gg += m.sE_f * (TF(1) - m.th_f * m.sE_f) * svf * m.idt_f + m.thsE_idt_f * (tv - qf * ddpf);
   }
   R.gg = gg;
 }

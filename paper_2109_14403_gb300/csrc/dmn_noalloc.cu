@@ -83,27 +83,12 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
 
   const int nleaf = 1 << K, N = nleaf - 1;
   // ---- host tables (fixed-size arrays on the stack: no heap either) ----
-  double mat[8 * kMaxMats];
+  double mat[kMatWords * kMaxMats];
   double Emax = 0.0;
   for (int i = 0; i < n_mats; ++i) {
-    const dmn_material &m = mats[i];
-    if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR)
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has unknown kind %d", i, m.kind);
-    if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has invalid elastic constants", i);
-    if (m.kind == DMN_MAT_J2_LINEAR &&
-        (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d has invalid J2 constants", i);
-    double *r = &mat[8 * i];
-    r[0] = m.kind;
-    r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
-    r[2] = m.E / (2.0 * (1.0 + m.nu));
-    r[3] = m.alpha;
-    r[4] = m.theta0;
-    r[5] = m.kind == DMN_MAT_J2_LINEAR ? m.sy0 : 0.0;
-    r[6] = m.kind == DMN_MAT_J2_LINEAR ? m.dsy_dT : 0.0;
-    r[7] = m.kind == DMN_MAT_J2_LINEAR ? m.H : 0.0;
-    if (m.E > Emax) Emax = m.E;
+    const char *why = material_row(mats[i], &mat[kMatWords * i]);
+    if (why) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d (kind %d): %s", i, mats[i].kind, why);
+    if (mats[i].E > Emax) Emax = mats[i].E;
   }
   if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
   double ws = 0.0;
@@ -160,17 +145,19 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
     q[17] = (float)r[6];
   }
   int zoff[LMAX];
-  int off = 8 + 3 * N;
+  int off = 8 + 3 * N, law = 1;
   for (int j = 0; j < nleaf; ++j) {
-    if (mats[phase_map[j]].kind == DMN_MAT_J2_LINEAR) {
+    const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
+    if (kind == DMN_MAT_J2_PERZYNA) law = 2;
+    if (zwl > 0) {
       zoff[j] = off;
-      off += 7;
+      off += zwl;
     } else {
       zoff[j] = -1;
     }
   }
   const int zend = off;
-  const int nz = (zend - (8 + 3 * N)) / 7;
+  const int zw = zend - (8 + 3 * N);
   if (off & 1) off += 1;
   const int SW = off;
   const size_t sbytes = sizeof(double) * (size_t)SW * (size_t)n_points;
@@ -188,7 +175,7 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   const size_t o_phase = align256(o_leafw + sizeof(double) * nleaf);
   const size_t o_zoff = align256(o_phase + nleaf);
   const size_t o_mat = align256(o_zoff + sizeof(int) * nleaf);
-  const size_t used = o_mat + sizeof(double) * 8 * n_mats;
+  const size_t used = o_mat + sizeof(double) * kMatWords * n_mats;
   if (used > kScratchBytes)
     return na_fail(DMN_ERR_INTERNAL, "dmn_eval_noalloc: tables need %zu bytes of scratch", used);
 
@@ -210,9 +197,9 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   int num_sms = 0, smem_optin = 0, blocks_per_sm = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (solve_smem_bytes(K, nz, n_mats, mixed, o.solve_variant) > (size_t)smem_optin)
+  if (solve_smem_bytes(K, zw, n_mats, mixed, o.solve_variant, law) > (size_t)smem_optin)
     return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: K=%d does not fit one SM in this precision", K);
-  e = prepare_solve(K, nz, n_mats, mixed, o.solve_variant, &blocks_per_sm);
+  e = prepare_solve(K, zw, n_mats, mixed, o.solve_variant, law, &blocks_per_sm);
   if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "prepare_solve: %s", cudaGetErrorString(e));
   if (blocks_per_sm < 1) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: kernel does not fit one SM");
 
@@ -228,7 +215,7 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
             {o_leafw, leaf_w, sizeof(double) * nleaf},
             {o_phase, phase_map, (size_t)nleaf},
             {o_zoff, zoff, sizeof(int) * nleaf},
-            {o_mat, mat, sizeof(double) * 8 * n_mats}};
+            {o_mat, mat, sizeof(double) * kMatWords * n_mats}};
   for (const auto &u : up) {
     e = cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
@@ -254,7 +241,8 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   P.phase = reinterpret_cast<const uint8_t *>(base + o_phase);
   P.zoff = reinterpret_cast<const int *>(base + o_zoff);
   P.mat = reinterpret_cast<const double *>(base + o_mat);
-  P.nz = nz;
+  P.zw = zw;
+  P.law = law;
   P.queue = reinterpret_cast<unsigned long long *>(base + o_queue);  // zeroed by launch_solve
   P.n_points = n_points;
   P.deps = d_deps;

@@ -82,7 +82,7 @@ __device__ __forceinline__ void back_substitute(const SolveParams &P, TF *da_s, 
 template <typename TF, typename HP, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
+  const int K = P.K, N = P.N, G = P.G, ZW = P.zw;
   const int t = threadIdx.x;
   const int nslot = G >= 64 ? G / 64 : 1;
   HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   // consecutive levels: level k lives in the buffer of its parity
   HP *esK = a_s + 3 * N;                       // 6G   levels K, K-2, ...
   HP *esO = esK + 6 * G;                       // 3G   levels K-1, K-3, ...
-  HP *zn_s = esO + 3 * G;                      // 7 NZ internal variables at t^n
-  HP *zw_s = zn_s + 7 * NZ;                    // 7 NZ internal variables of the last pass
-  HP *eb = zw_s + 7 * NZ;                      // 12: eps_bar^{n+1}, deps
+  HP *zn_s = esO + 3 * G;                      // ZW internal variables at t^n
+  HP *zw_s = zn_s + ZW;                        // ZW internal variables of the last pass
+  HP *eb = zw_s + ZW;                          // 12: eps_bar^{n+1}, deps
   HP *redD = eb + 12;                          // 32
   HP *redX = redD + 32;                        // 32
   HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   };
 
   for (int i = t; i < P.n_mats; i += G)
-    mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
+    mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i), P.dt);
   if (t == 0) misc[0] = hp_from(1.0 / P.dt, tag);
   const TF idt_f = TF(1.0 / P.dt);
   const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
@@ -157,14 +157,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
     double *sout = P.sout + pt * P.SW;
     const double theta = P.theta[pt];
     for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
-    for (int i = t; i < 7 * NZ; i += G) zn_s[i] = hp_load(sin[8 + 3 * N + i], tag);
+    for (int i = t; i < ZW; i += G) zn_s[i] = hp_load(sin[8 + 3 * N + i], tag);
     for (int c = t; c < 6; c += G) {  // a point may have fewer than 6 threads
       const double d = P.deps[pt * 6 + c];
       eb[c] = hp_load(sin[c] + d, tag);
       eb[6 + c] = hp_load(d, tag);
     }
     __syncthreads();  // misc[0] (first point) and the static material part
-    for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
+    for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP, 1>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
     if (t == 0) {
       ctrl->first = 1;
       ctrl->it = 0;
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
         }
         HP sl[6], sr[6], DL, DR, XL, XR;
         Rec<TF> rr;
-        leaf_eval<TF, HP>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
-        leaf_eval<TF, HP>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
+        leaf_eval<TF, HP, 1>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+        leaf_eval<TF, HP, 1>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
         Dsum = wL * DL + wR * DR;
         Xsum = wL * XL + wR * XR;
         HP dsh[6];
@@ -425,17 +425,17 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
     for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
       sout[c] = c < 6 ? sin[c] + P.deps[pt * 6 + c] : (c == 6 ? theta : 0.0);
     for (int i = t; i < 3 * N; i += G) sout[8 + i] = hp_to(a_s[i]);
-    for (int i = t; i < 7 * NZ; i += G) sout[8 + 3 * N + i] = hp_to(zw_s[i]);
+    for (int i = t; i < ZW; i += G) sout[8 + 3 * N + i] = hp_to(zw_s[i]);
     for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
     __syncthreads();
   }
 }
 
-static size_t owner_smem_bytes(int K, int nz, int n_mats, bool mixed) {
+static size_t owner_smem_bytes(int K, int zw, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const int nslot = G >= 64 ? G / 64 : 1;
   const size_t hp = 8;  // double or float-float
-  size_t b = hp * (3 * N + 9 * G + 14 * nz + 12 + 64 + 4) + sizeof(double) * (nslot * kRecWords);
+  size_t b = hp * (3 * N + 9 * G + 2 * zw + 12 + 64 + 4) + sizeof(double) * (nslot * kRecWords);
   b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
   b = (b + 15) & ~size_t(15);
   b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
@@ -446,15 +446,20 @@ static size_t owner_smem_bytes(int K, int nz, int n_mats, bool mixed) {
 // kernel variants: (form, precision, threads bound, CTAs per SM requested).
 // 0 = default; 2..4 = owner-mapped mixed kernel for that many CTAs per SM;
 // 10 + m = compact kernel (dmn_solve_compact.cu), mixed compiled for m = 2, 3
-// or 4 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 always takes the
-// owner-mapped 512-thread kernel.
+// or 4 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 takes the
+// owner-mapped 512-thread kernel.  A tree with Perzyna leaves (law 2) always
+// takes the compact instances that include that leaf law
+// (dmn_solve_compact_vp.cu, K <= 9), whatever the variant.
 bool solve_variant_valid(int variant) {
   return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 14);
 }
-static bool is_compact(int K, int variant) { return K <= 8 && variant >= 11; }
+static bool is_compact(int K, int variant, int law) {
+  return law >= 2 ? K <= 9 : (K <= 8 && variant >= 11);
+}
 
-static KernelFn pick(int K, bool mixed, int variant) {
-  if (is_compact(K, variant)) return compact_kernel(K, mixed, variant - 10);
+static KernelFn pick(int K, bool mixed, int variant, int law) {
+  if (law >= 2) return compact_kernel_vp(K, mixed);
+  if (is_compact(K, variant, law)) return compact_kernel(K, mixed, variant - 10);
   if (K > 8) return mixed ? dmn_solve_kernel<float, dfl, 512, 1> : dmn_solve_kernel<double, double, 512, 1>;
   if (!mixed) return dmn_solve_kernel<double, double, 128, 1>;
   switch (variant) {
@@ -464,14 +469,15 @@ static KernelFn pick(int K, bool mixed, int variant) {
   }
 }
 
-size_t solve_smem_bytes(int K, int nz, int n_mats, bool mixed, int variant) {
-  return is_compact(K, variant) ? compact_smem_bytes(K, nz, n_mats, mixed)
-                                : owner_smem_bytes(K, nz, n_mats, mixed);
+size_t solve_smem_bytes(int K, int zw, int n_mats, bool mixed, int variant, int law) {
+  return is_compact(K, variant, law) ? compact_smem_bytes(K, zw, n_mats, mixed)
+                                     : owner_smem_bytes(K, zw, n_mats, mixed);
 }
 
-cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, int *blocks_per_sm) {
-  const size_t smem = solve_smem_bytes(K, nz, n_mats, mixed, variant);
-  KernelFn f = pick(K, mixed, variant);
+cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
+                          int *blocks_per_sm) {
+  const size_t smem = solve_smem_bytes(K, zw, n_mats, mixed, variant, law);
+  KernelFn f = pick(K, mixed, variant, law);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem)) != cudaSuccess)
@@ -501,10 +507,10 @@ cudaError_t prepare_solve(int K, int nz, int n_mats, bool mixed, int variant, in
 }
 
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s) {
-  const size_t smem = solve_smem_bytes(P.K, P.nz, P.n_mats, mixed, variant);
+  const size_t smem = solve_smem_bytes(P.K, P.zw, P.n_mats, mixed, variant, P.law);
   cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  pick(P.K, mixed, variant)<<<grid, P.G, smem, s>>>(P);
+  pick(P.K, mixed, variant, P.law)<<<grid, P.G, smem, s>>>(P);
   return cudaGetLastError();
 }
 

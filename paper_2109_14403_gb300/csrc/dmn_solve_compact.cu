@@ -1,645 +1,14 @@
-// dmn_solve_compact.cu -- second form of the Algorithm 1 solve (arXiv
-// 2109.14403, Sec. 3.3): one CTA per Gauss point, G = 2^(K-1) threads, with
-//  * incremental strains: the strains of the bottom laminates live in shared
-//    memory and are updated after each Newton step by adding, in the high
-//    precision HP (float-float in the mixed path), the strain increments the
-//    exact FP32 jump increments da cause (eq. DMN kinematics);
-//  * strain sums instead of level sweeps: a bottom laminate's strain (or
-//    increment) is the root value plus one term per ancestor; all terms are
-//    formed at once, one node per thread, and summed per laminate after a
-//    single barrier;
-//  * compact levels: the laminates just above the bottom pair neighbouring
-//    lanes by shuffle; every higher level puts node j of the level on one
-//    thread, with the children's condensed records and stress sums in shared
-//    memory, so a level of at most 32 nodes occupies one warp (the CTA's
-//    leader warp, with warp barriers only) while the other warps go ahead;
-//  * the back-substitution of the Newton increment, a chain through the
-//    levels, in the condensation precision TF on the same compact mapping.
-// The leader warp is picked from the CTA's warp slot so that the CTAs resident
-// on one SM run their single-warp phases on different SM sub-partitions.
-// The condensation, the residual and the leaf laws are those of
-// dmn_kernels.cuh.  The internal variables of the current pass are parked in
-// the caller's output state (same 8-byte slots) and converted at the end.
-#include "dmn_internal.h"
-#include "solve_common.cuh"
+// dmn_solve_compact.cu -- instances of the compact solve (solve_compact.cuh)
+// for thermoelastic and J2 leaves, depth K <= 8, and its shared-memory size.
+#include "solve_compact.cuh"
 
 namespace dmn {
 
-namespace {
-constexpr int RS = 41;  // record stride in shared memory (40 values, odd)
-
-template <typename TF>
-__device__ __forceinline__ void rec_put(TF *s, const Rec<TF> &r) {
-#pragma unroll
-  for (int q = 0; q < 21; ++q) s[q] = r.C[q];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    s[21 + c] = r.ds[c];
-    s[27 + c] = r.tau[c];
-    s[33 + c] = r.dd[c];
-  }
-  s[39] = r.gg;
-}
-template <typename TF>
-__device__ __forceinline__ void rec_get(Rec<TF> &r, const TF *s) {
-#pragma unroll
-  for (int q = 0; q < 21; ++q) r.C[q] = s[q];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    r.ds[c] = s[21 + c];
-    r.tau[c] = s[27 + c];
-    r.dd[c] = s[33 + c];
-  }
-  r.gg = s[39];
-}
-
-// Shared scratch region, in 8-byte words, used in turn by the condensation
-// (stress sums and records of the levels K-1, K-2, ..., two parities), by the
-// Newton back-substitution (TF strain increments of two level parities, level
-// K: 6G values) and by the strain sums (14 HP words per non-bottom node).
-struct Scratch {
-  int GX, GY;          // entries of the two condensation parities
-  int sx, sy, rx, ry;  // offsets: S sums in HP words, records in TF words from rx
-  int words;           // size of the region in 8-byte words
-};
-__host__ __device__ inline Scratch scratch_layout(int G, int tf_bytes) {
-  Scratch c;
-  c.GX = G >= 2 ? G / 2 : 1;  // level K-1 has G/2 nodes
-  c.GY = G >= 4 ? G / 4 : 1;  // level K-2
-  c.sx = 0;
-  c.sy = 6 * c.GX;
-  const int rx_tf = (6 * c.GX + 6 * c.GY) * (8 / tf_bytes);  // records start after the sums
-  c.rx = rx_tf;
-  c.ry = rx_tf + ((RS * c.GX + 1) & ~1);
-  const int cond_words = (c.ry + RS * c.GY) * tf_bytes / 8 + 1;
-  const int chain_words = (9 * G * tf_bytes + 7) / 8;
-  const int sum_words = 14 * (G - 1);
-  c.words = cond_words;
-  if (chain_words > c.words) c.words = chain_words;
-  if (sum_words > c.words) c.words = sum_words;
-  return c;
-}
-}  // namespace
-
-template <typename TF, typename HP, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = P.K, N = P.N, G = P.G, NZ = P.nz;
-  const int t = threadIdx.x;
-  const Scratch sc_ = scratch_layout(G, int(sizeof(TF)));
-  HP *a_s = reinterpret_cast<HP *>(smem_raw);  // 3N   jump vectors
-  HP *eK = a_s + 3 * N;                        // 6G   strains of the bottom laminates
-  HP *zn_s = eK + 6 * G;                       // 7 NZ internal variables at t^n
-  HP *eb = zn_s + 7 * NZ;                      // 18: eps_bar^{n+1}, deps (HP), eps_bar^{n+1} (FP64)
-  double *ebd = reinterpret_cast<double *>(eb + 12);
-  HP *sroot = eb + 18;                         // 6: sigma_bar of the last pass
-  HP *redD = sroot + 6;                        // 32
-  HP *redX = redD + 32;                        // 32
-  HP *misc = redX + 32;                        // 4: 1/dt, D_bar, X_bar
-  HP *scr = misc + 4;                          // scratch region (Scratch)
-  MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(scr + sc_.words);
-  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(
-      (reinterpret_cast<uintptr_t>(mp_s + P.n_mats) + 15) & ~uintptr_t(15));
-  TF *red = reinterpret_cast<TF *>(ctrl + 1);  // 32
-  TF *orec = red + 32;                         // 40
-  TF *da_s = orec + 40;                        // 3N  Newton increment
-  TF *gh_s = da_s + 3 * N;                     // 21N G_p, h_p
-  HP *tag = nullptr;
-  // condensation: stress sums and records of levels K-1, K-2, ...; level k
-  // in X if (K-1-k) is even
-  HP *Sx = scr + sc_.sx, *Sy = scr + sc_.sy;
-  TF *recX = reinterpret_cast<TF *>(scr) + sc_.rx, *recY = reinterpret_cast<TF *>(scr) + sc_.ry;
-  auto recbuf = [&](int k) { return ((K - 1 - k) & 1) ? recY : recX; };
-  auto sbuf = [&](int k) { return ((K - 1 - k) & 1) ? Sy : Sx; };
-  // back-substitution (the same region): TF strain increments, level k in X
-  // if (K - k) is even (level K: G entries of 6)
-  TF *tX = reinterpret_cast<TF *>(scr), *tY = tX + 6 * G;
-  auto tbuf = [&](int k) { return ((K - k) & 1) ? tY : tX; };
-  HP *anc = scr;  // strain sums: per non-bottom node c2 B x, c1 B x, c2 tr, c1 tr
-
-  const unsigned mask = group_mask(G);
-  const int W = group_width(G);
-  const int lane = t & 31, warp = t >> 5, nwarp = (G + 31) >> 5;
-  if (t == 0) {
-    // a warp slot's sub-partition is slot mod 4 and a CTA's warps take
-    // consecutive slots: rotate the leader by the CTA's slot group
-    unsigned wid;
-    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
-    ctrl->lead = nwarp > 1 ? int(((wid >> 2) - wid) & unsigned(nwarp - 1)) : 0;
-  }
-  __syncthreads();
-  const int L = ctrl->lead;
-  // node of level k handled by this thread, or -1: a level of more than 32
-  // nodes on threads 0.., one of at most 32 nodes on the lanes of warp L
-  auto node_at = [&](int k) -> int {
-    const int cnt = 1 << (k - 1);
-    if (cnt > 32) return t < cnt ? t : -1;
-    return (warp == L && lane < cnt) ? lane : -1;
-  };
-  // thread that ends the bottom-up sweep with the root record (level K-1 is
-  // condensed by shuffles, on threads 0, 2, ..)
-  const int root_t = K >= 3 ? 32 * L : 0;
-
-  for (int i = t; i < P.n_mats; i += G)
-    mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + 8 * i));
-  if (t == 0) misc[0] = hp_from(1.0 / P.dt, tag);
-  const TF idt_f = TF(1.0 / P.dt);
-  const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
-
-  const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
-  const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
-  const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
-  const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
-
-  // Strains of the bottom laminates by ancestor sums (eq. DMN kinematics):
-  // laminate t's strain is the root strain plus, for every ancestor p on its
-  // path, +c2 B x_p (the path goes through child 1) or -c1 B x_p (child 2).
-  // The two terms of every non-bottom node are formed at once, one node per
-  // thread; after one barrier each thread adds its K-1 ancestors' terms root
-  // first, the order (and rounding) of a level-by-level top-down sweep.
-  //   SW_PLAIN: eK = eps_bar^{n+1} + sum of the B a terms
-  //   SW_WARM:  a += da (da_s) on the way; eK as SW_PLAIN at the new a, and
-  //             the trace of the strain at (eps_bar^n = tr_root, a^n) of
-  //             laminate t is returned (tr B a = a . n)
-  //   SW_STEP:  eK += sum of the B da terms (the Newton increment in da_s)
-  // Ends with a barrier: eK is complete and the scratch region free again.
-  enum { SW_PLAIN = 0, SW_WARM = 1, SW_STEP = 2 };
-  auto sweep = [&](int mode, HP tr_root) -> HP {
-    for (int q = t; q < G - 1; q += G) {
-      const int p = G + q;
-      NodeHP<HP> nd;
-      load_node(P, p, nd);
-      HP x[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-        x[r] = mode == SW_STEP ? hp_add_tf(hp_zero(tag), da_s[3 * p + r]) : a_s[3 * p + r];
-      HP *ent = anc + 14 * q;
-      if (mode == SW_WARM) {
-        const HP trj = x[0] * nd.n[0] + x[1] * nd.n[1] + x[2] * nd.n[2];
-        ent[12] = nd.c2 * trj;
-        ent[13] = nd.c1 * trj;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          x[r] = hp_add_tf(x[r], da_s[3 * p + r]);
-          a_s[3 * p + r] = x[r];
-        }
-      }
-      HP J[6];
-      bvec_hp(nd, x, J);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        ent[c] = nd.c2 * J[c];
-        ent[6 + c] = nd.c1 * J[c];
-      }
-    }
-    __syncthreads();
-    HP e[6], tr = tr_root;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = mode == SW_STEP ? hp_zero(tag) : eb[c];
-    for (int k = 1; k <= K - 1; ++k) {
-      const int p = (1 << K) - (1 << k) + (t >> (K - k));
-      const HP *ent = anc + 14 * (p - G);
-      if ((t >> (K - k - 1)) & 1) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = e[c] - ent[6 + c];
-        if (mode == SW_WARM) tr = tr - ent[13];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = e[c] + ent[c];
-        if (mode == SW_WARM) tr = tr + ent[12];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) eK[6 * t + c] = mode == SW_STEP ? eK[6 * t + c] + e[c] : e[c];
-    __syncthreads();
-    return tr;
-  };
-
-  // n doubles from global memory into HP in shared memory, U loads in flight
-  auto load_hp = [&](HP *dst, const double *src, int n) {
-    constexpr int U = 8;
-    for (int i0 = t; i0 < n; i0 += U * G) {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = i0 + u * G < n ? ld_stream(src + i0 + u * G) : 0.0;
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (i0 + u * G < n) dst[i0 + u * G] = hp_load(v[u], tag);
-    }
-  };
-
-  for (;;) {
-    if (t == 0) ctrl->next = atomicAdd(P.queue, 1ull);
-    __syncthreads();
-    const int64_t pt = int64_t(ctrl->next);
-    if (pt >= P.n_points) break;
-    const double *sin = P.sin + pt * P.SW;
-    double *sout = P.sout + pt * P.SW;
-    HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
-    const double theta = P.theta[pt];
-    {
-      // one wave of loads: jumps (3N < 8G), the first 8G internal variables,
-      // the predicted increment, eps_bar^n and deps
-      constexpr int U = 8;
-      double va[U], vz[U], ve = 0.0, vd = 0.0;
-      float vp[U];
-      const float *d0 = P.da0 ? P.da0 + pt * (3 * N) : nullptr;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = t + u * G;
-        va[u] = i < 3 * N ? ld_stream(sin + 8 + i) : 0.0;
-        vz[u] = i < 7 * NZ ? ld_stream(sin + 8 + 3 * N + i) : 0.0;
-        vp[u] = d0 && i < 3 * N ? ld_stream(d0 + i) : 0.0f;
-      }
-      if (G >= 8 && t < 6) {
-        ve = ld_stream(sin + t);
-        vd = ld_stream(P.deps + pt * 6 + t);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = t + u * G;
-        if (i < 3 * N) {
-          a_s[i] = hp_load(va[u], tag);
-          if (d0) da_s[i] = TF(vp[u]);
-        }
-        if (i < 7 * NZ) zn_s[i] = hp_load(vz[u], tag);
-      }
-      if (7 * NZ > U * G) load_hp(zn_s + U * G, sin + 8 + 3 * N + U * G, 7 * NZ - U * G);
-      if (G >= 8) {
-        if (t < 6) {
-          ebd[t] = ve + vd;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
-          eb[t] = hp_load(ve + vd, tag);
-          eb[6 + t] = hp_load(vd, tag);
-        }
-      } else {
-        for (int c = t; c < 6; c += G) {
-          const double d = P.deps[pt * 6 + c], e1 = sin[c] + d;
-          ebd[c] = e1;
-          eb[c] = hp_load(e1, tag);
-          eb[6 + c] = hp_load(d, tag);
-        }
-      }
-    }
-    __syncthreads();
-    for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
-    if (t == 0) {
-      ctrl->first = 1;
-      ctrl->it = 0;
-      ctrl->bt = 0;
-      ctrl->gi = TF(1);
-      ctrl->res_old = TF(0);
-      ctrl->status = 0;
-    }
-    const HP *zn0 = zq0 >= 0 ? zn_s + zq0 : nullptr;
-    const HP *zn1 = zq1 >= 0 ? zn_s + zq1 : nullptr;
-    HP *zw0 = zq0 >= 0 ? zw + zq0 : nullptr;
-    HP *zw1 = zq1 >= 0 ? zw + zq1 : nullptr;
-
-    HP trn0 = hp_zero(tag), trn1 = hp_zero(tag);
-    bool first = true;  // the first pass also yields the traces of eps^n
-    if (P.da0) {
-      // warm start a^n + da0; the traces of eps^n come with the same sweep
-      const HP tre =
-          sweep(SW_WARM, hp_load(sin[0], tag) + hp_load(sin[1], tag) + hp_load(sin[2], tag));
-      NodeHP<HP> nd;
-      load_node(P, t, nd);
-      const HP an[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};  // still a^n
-      const HP trj = an[0] * nd.n[0] + an[1] * nd.n[1] + an[2] * nd.n[2];
-      trn0 = tre + nd.c2 * trj;
-      trn1 = tre - nd.c1 * trj;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) a_s[3 * t + r] = hp_add_tf(an[r], da_s[3 * t + r]);
-      first = false;  // thread t alone uses a_s[3t..] until the next barrier
-    } else {
-      sweep(SW_PLAIN, hp_zero(tag));  // strains of the bottom laminates at a^n
-    }
-    int attempt = 0, it_total = 0;
-    HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
-    Rec<TF> rec;
-    for (;;) {
-      // ---- R2: leaves and laminate t ----
-      TF r2;
-      HP S[6];
-      {
-        NodeHP<HP> nd;
-        load_node(P, t, nd);
-        HP el[6], er[6];
-        {
-          const HP av[3] = {a_s[3 * t], a_s[3 * t + 1], a_s[3 * t + 2]};
-          HP J[6];
-          bvec_hp(nd, av, J);
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const HP e = eK[6 * t + c];
-            el[c] = e + nd.c2 * J[c];
-            er[c] = e - nd.c1 * J[c];
-          }
-        }
-        if (first) {  // at a = a^n: eps^n = eps - deps
-          const HP trd = eb[6] + eb[7] + eb[8];
-          trn0 = (el[0] + el[1] + el[2]) - trd;
-          trn1 = (er[0] + er[1] + er[2]) - trd;
-        }
-        HP sl[6], sr[6], DL, DR, XL, XR;
-        Rec<TF> rr;
-        leaf_eval<TF, HP>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
-        leaf_eval<TF, HP>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
-        Dsum = wL * DL + wR * DR;
-        Xsum = wL * XL + wR * XR;
-        HP dsh[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          S[c] = wL * sl[c] + wR * sr[c];
-          dsh[c] = sl[c] - sr[c];
-        }
-        HP rbh[3];
-        btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_t / (w c1 c2)
-        TF n[3], c1, c2, iwcc, wcc;
-        load_node_tf(P, t, n, c1, c2, iwcc, wcc);
-        const TF rbv[3] = {tf_of(rbh[0], (TF *)nullptr), tf_of(rbh[1], (TF *)nullptr),
-                           tf_of(rbh[2], (TF *)nullptr)};
-        r2 = wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
-        combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t);
-      }
-      // ---- level K-1: neighbouring lanes (2j, 2j+1) ----
-      if (K >= 2) {
-        Rec<TF> other;
-        rec_shfl_down(other, rec, 1, mask, W);
-        HP So[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) So[c] = hp_shfl_down(mask, S[c], 1, W);
-        if ((t & 1) == 0) {
-          const int j = t >> 1;
-          const int p = (1 << K) - (1 << (K - 1)) + j;
-          NodeHP<HP> nd;
-          load_node(P, p, nd);
-          HP dh[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            dh[c] = nd.c2 * S[c] - nd.c1 * So[c];
-            S[c] = S[c] + So[c];
-          }
-          HP rh[3];
-          btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
-          TF n[3], c1, c2, iwcc, wcc;
-          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
-          const TF rv[3] = {tf_of(rh[0], (TF *)nullptr), tf_of(rh[1], (TF *)nullptr),
-                            tf_of(rh[2], (TF *)nullptr)};
-          r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
-          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
-          if (K >= 3) {
-            rec_put(recX + RS * j, rec);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) Sx[6 * j + c] = S[c];
-          }
-        }
-      }
-      // ---- levels K-2 .. 1: node j of the level on one thread.  Once the
-      //      producers of the level below all sit in warp L, warp L goes on
-      //      alone with warp barriers and the other warps move to the
-      //      reduction barrier ----
-      for (int k = K - 2; k >= 1; --k) {
-        const int prod = k + 1 == K - 1 ? G : (1 << k);  // threads that wrote level k+1
-        if (prod > 32) {
-          __syncthreads();
-        } else {
-          if (warp != L) break;
-          __syncwarp(mask);
-        }
-        const int j = node_at(k);
-        if (j >= 0) {
-          const int p = (1 << K) - (1 << k) + j;
-          const TF *rc = recbuf(k + 1) + RS * (2 * j);
-          const HP *sc = sbuf(k + 1) + 12 * j;
-          Rec<TF> other;
-          rec_get(rec, rc);
-          rec_get(other, rc + RS);
-          NodeHP<HP> nd;
-          load_node(P, p, nd);
-          HP dh[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const HP SL = sc[c], SR = sc[6 + c];
-            S[c] = SL + SR;
-            dh[c] = nd.c2 * SL - nd.c1 * SR;
-          }
-          HP rh[3];
-          btvec_hp(nd, dh, rh);
-          TF n[3], c1, c2, iwcc, wcc;
-          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
-          const TF rv[3] = {tf_of(rh[0], (TF *)nullptr), tf_of(rh[1], (TF *)nullptr),
-                            tf_of(rh[2], (TF *)nullptr)};
-          r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
-          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
-          if (k > 1) {
-            rec_put(recbuf(k) + RS * j, rec);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sbuf(k)[6 * j + c] = S[c];
-          }
-        }
-      }
-      if (t == root_t) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sroot[c] = S[c];
-      }
-      // ---- residual norm, decision (Algorithm 1) ----
-      r2 = warp_sum(r2, mask, W);
-      if (lane == 0) red[warp] = r2;
-      __syncthreads();
-      if (t == 0) {
-        TF s = TF(0);
-        for (int w = 0; w < nwarp; ++w) s += red[w];
-        TF sn = TF(0);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const TF v = tf_of(sroot[c], (TF *)nullptr);
-          sn += v * v;
-        }
-        TF den = sqrt(sn);
-        if (den < res_floor) den = res_floor;
-        const TF res = sqrt(s) / (TF(N) * den);
-        Ctrl<TF> &c = *ctrl;
-        const bool accept = c.first || (res < c.res_old) || (c.bt >= P.maxbt);
-        int action;
-        if (accept) {
-          if (!isfinite(res)) {
-            c.status = 2;
-            action = ACT_DONE;
-          } else if (!c.first && res < tol) {
-            c.status = 0;
-            action = ACT_DONE;
-          } else if (c.it >= P.maxit) {
-            c.status = 1;
-            action = ACT_DONE;
-          } else {
-            c.res_old = res;
-            c.it += 1;
-            c.bt = 0;
-            c.gi = TF(1);
-            action = ACT_STEP;
-          }
-          c.first = 0;
-        } else {
-          action = ACT_BACK;
-        }
-        c.res = res;
-        c.action = action;
-      }
-      first = false;
-      __syncthreads();
-      const int action = ctrl->action;
-      if (action == ACT_DONE) {
-        if (P.da0 && attempt == 0 && ctrl->status != 0) {
-          // warm-started iteration failed: run Algorithm 1 again from a^n
-          attempt = 1;
-          it_total = ctrl->it;
-          for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(sin[8 + i], tag);
-          __syncthreads();  // every thread has read ctrl->status and ctrl->it
-          if (t == 0) {
-            ctrl->first = 1;
-            ctrl->it = 0;
-            ctrl->bt = 0;
-            ctrl->gi = TF(1);
-            ctrl->res_old = TF(0);
-            ctrl->status = 0;
-          }
-          sweep(SW_PLAIN, hp_zero(tag));  // its barriers order the reset before later reads
-          continue;
-        }
-        break;
-      }
-      if (action == ACT_STEP) {
-        // ---- back-substitution in TF, node j of level k on one thread:
-        //      da_p = -(G_p de_p + h_p); children de + c2 B da, de - c1 B da;
-        //      then the bottom strains take the high-precision sum of the
-        //      B da terms of their ancestors
-        for (int k = 1; k <= K; ++k) {
-          const int j = node_at(k);  // level K: j = t
-          if (j >= 0) {
-            const int p = (1 << K) - (1 << k) + j;
-            TF de[6];
-            if (k == 1) {
-#pragma unroll
-              for (int c = 0; c < 6; ++c) de[c] = TF(0);
-            } else {
-              const TF *src = tbuf(k) + 6 * j;
-#pragma unroll
-              for (int c = 0; c < 6; ++c) de[c] = src[c];
-            }
-            const TF *g = gh_s + 21 * p;
-            TF da[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              TF sum = g[18 + r];
-#pragma unroll
-              for (int c = 0; c < 6; ++c) sum += g[6 * r + c] * de[c];
-              da[r] = -sum;
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              da_s[3 * p + r] = da[r];
-              a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
-            }
-            if (k < K) {
-              TF n[3], c1, c2, iwcc, wcc;
-              load_node_tf(P, p, n, c1, c2, iwcc, wcc);
-              TF J[6];
-              bvec(n, da, J);
-              TF *dst = tbuf(k + 1) + 12 * j;
-#pragma unroll
-              for (int c = 0; c < 6; ++c) {
-                dst[c] = de[c] + c2 * J[c];
-                dst[6 + c] = de[c] - c1 * J[c];
-              }
-            }
-          }
-          // level k+1 is read by threads < 2^k: a warp barrier while they
-          // all sit in warp L (the other warps wait at the next block barrier)
-          if (k == K || (1 << k) > 32) __syncthreads();
-          else if (warp == L) __syncwarp(mask);
-        }
-        sweep(SW_STEP, hp_zero(tag));
-      } else {
-        // ---- backtracking (rare): a -= f da, strains from a new sweep ----
-        const TF f = ctrl->gi * (TF(1) - gamma);
-        for (int i = t; i < 3 * N; i += G) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
-        __syncthreads();
-        sweep(SW_PLAIN, hp_zero(tag));  // its barriers also order the reads of ctrl->gi above
-        if (t == 0) {
-          ctrl->gi *= gamma;
-          ctrl->bt += 1;
-        }
-      }
-    }
-
-    // ---- outputs and state (the last pass is at the final a; its coupling
-    //      term and dissipation sums are still in the registers) ----
-    {
-      const HP ds_ = warp_sum(Dsum, mask, W), xs_ = warp_sum(Xsum, mask, W);
-      if (lane == 0) {
-        redD[warp] = ds_;
-        redX[warp] = xs_;
-      }
-    }
-    __syncthreads();
-    if (t == root_t) {
-#pragma unroll
-      for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        orec[21 + c] = rec.tau[c];
-        orec[27 + c] = rec.dd[c];
-      }
-      orec[33] = rec.gg;
-      HP Db = redD[0], Xb = redX[0];
-      for (int w = 1; w < nwarp; ++w) {
-        Db = Db + redD[w];
-        Xb = Xb + redX[w];
-      }
-      misc[1] = Db;
-      misc[2] = Xb;
-    }
-    __syncthreads();
-    int bad = 0;
-    for (int c = t; c < kOutWords; c += G) {
-      double v;
-      if (c < 6) v = hp_to(sroot[c]);
-      else if (c < 42) v = double(sget(orec, (c - 6) / 6, (c - 6) % 6));
-      else if (c < 48) v = double(orec[21 + c - 42]);
-      else if (c == 48) v = hp_to(misc[1]);
-      else if (c < 55) v = double(orec[27 + c - 49]);
-      else if (c == 55) v = double(orec[33]);
-      else v = hp_to(misc[2]);
-      if (!isfinite(v)) bad = 1;
-      __stcs(P.out + pt * kOutWords + c, v);
-    }
-    bad = __syncthreads_or(bad);
-    if (t == 0) {
-      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
-      P.iters[pt] = ctrl->it + it_total;
-    }
-    for (int c = t; c < 8; c += G) sout[c] = c < 6 ? ebd[c] : (c == 6 ? theta : 0.0);
-    for (int i = t; i < 3 * N; i += G) __stcs(sout + 8 + i, hp_to(a_s[i]));
-    for (int i0 = t; i0 < 7 * NZ; i0 += 8 * G) {  // parked internal variables -> FP64 in place
-      HP v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < 7 * NZ ? ld_once(zw + i0 + u * G) : hp_zero(tag);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (i0 + u * G < 7 * NZ) __stcs(sout + 8 + 3 * N + i0 + u * G, hp_to(v[u]));
-    }
-    for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
-    __syncthreads();
-  }
-}
-
-size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed) {
+size_t compact_smem_bytes(int K, int zw, int n_mats, bool mixed) {
   const int N = (1 << K) - 1, G = 1 << (K - 1);
   const size_t hp = 8, tf = mixed ? 4 : 8;
   const Scratch sc = scratch_layout(G, int(tf));
-  size_t b = hp * (3 * N + 6 * G + 7 * nz + 18 + 6 + 64 + 4 + sc.words);
+  size_t b = hp * (3 * N + 6 * G + zw + 18 + 6 + 4 + sc.words);
   b += (mixed ? sizeof(MatPt<float, dfl>) : sizeof(MatPt<double, double>)) * n_mats;
   b = (b + 15) & ~size_t(15);
   b += mixed ? sizeof(Ctrl<float>) : sizeof(Ctrl<double>);
@@ -649,9 +18,9 @@ size_t compact_smem_bytes(int K, int nz, int n_mats, bool mixed) {
 
 KernelFn compact_kernel(int K, bool mixed, int minb) {
   (void)K;  // depth <= 8: at most 128 threads
-  if (!mixed) return dmn_solve_compact<double, double, 128, 1>;
-  if (minb >= 4) return dmn_solve_compact<float, dfl, 128, 4>;
-  return minb == 3 ? dmn_solve_compact<float, dfl, 128, 3> : dmn_solve_compact<float, dfl, 128, 2>;
+  if (!mixed) return dmn_solve_compact<double, double, 128, 1, 1>;
+  if (minb >= 4) return dmn_solve_compact<float, dfl, 128, 4, 1>;
+  return minb == 3 ? dmn_solve_compact<float, dfl, 128, 3, 1> : dmn_solve_compact<float, dfl, 128, 2, 1>;
 }
 
 }  // namespace dmn

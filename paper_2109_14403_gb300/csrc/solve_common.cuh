@@ -117,8 +117,6 @@ __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, float 
   iwcc = ld_keep(r + 16);
   wcc = ld_keep(r + 17);
 }
-__device__ __forceinline__ double hp_add_tf(double a, double d) { return a + d; }
-__device__ __forceinline__ dfl hp_add_tf(dfl a, float d) { return a + dfl{d, 0.0f}; }
 
 // B a = sym(a (x) n) with the pre-scaled normal ns = n / sqrt2
 template <typename HP>

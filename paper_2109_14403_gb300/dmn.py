@@ -24,7 +24,8 @@ _lib = None
 class dmn_material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("E", ctypes.c_double),
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("theta0", ctypes.c_double),
-                ("sy0", ctypes.c_double), ("dsy_dT", ctypes.c_double), ("H", ctypes.c_double)]
+                ("sy0", ctypes.c_double), ("dsy_dT", ctypes.c_double), ("H", ctypes.c_double),
+                ("m_rate", ctypes.c_double), ("t_visc", ctypes.c_double), ("dE_dT", ctypes.c_double)]
 
 
 class dmn_options(ctypes.Structure):
@@ -117,13 +118,18 @@ def _dev(t, dtype, shape, name):
 
 
 def materials_from_rows(rows):
-    """Material table rows (kind, E, nu, alpha, theta0, sy0, dsy_dT, H) -> ctypes array."""
-    rows = np.asarray(rows, np.float64).reshape(-1, 8)
+    """Material table rows (kind, E, nu, alpha, theta0, sy0, dsy_dT, H[, m_rate,
+    t_visc, dE_dT, 0]) -> ctypes array; rows of 8 leave the Perzyna fields 0."""
+    rows = np.atleast_2d(np.asarray(rows, np.float64))
+    if rows.shape[1] not in (8, 11, 12):
+        raise ValueError("material rows have 8 or 12 columns")
     arr = (dmn_material * rows.shape[0])()
     for i, r in enumerate(rows):
         arr[i].kind = int(r[0])
         arr[i].E, arr[i].nu, arr[i].alpha, arr[i].theta0 = r[1], r[2], r[3], r[4]
         arr[i].sy0, arr[i].dsy_dT, arr[i].H = r[5], r[6], r[7]
+        if rows.shape[1] > 8:
+            arr[i].m_rate, arr[i].t_visc, arr[i].dE_dT = r[8], r[9], r[10]
     return arr
 
 
