@@ -43,8 +43,8 @@ UNIT = "GP-evals/s"
 TOL = 1e-12  # the paper's tolerance: mixed-path stress within 1e-8 of FP64
 
 
-def state_words(K, n_j2):
-    w = 8 + 3 * ((1 << K) - 1) + 7 * n_j2
+def state_words(K, n_j2, z_per_leaf=7):
+    w = 8 + 3 * ((1 << K) - 1) + z_per_leaf * n_j2
     return w + (w & 1)
 
 
@@ -64,9 +64,10 @@ def whole_job_rate(units_per_rank, world, steps, t_ms):
     return world * units_per_rank * steps / (t_ms / 1e3)
 
 
-def algorithmic_bytes_per_eval(K):
-    """State in + state out + inputs (deps 6, theta 1) + outputs (57) + status + iters."""
-    sw = state_words(K, (1 << K) // 2)
+def algorithmic_bytes_per_eval(K, z_per_leaf=7):
+    """State in + state out + inputs (deps 6, theta 1) + outputs (57) + status + iters
+    (half the leaves carry z_per_leaf internal variables)."""
+    sw = state_words(K, (1 << K) // 2, z_per_leaf)
     return 8 * (2 * sw + 7 + 57) + 8
 
 
@@ -288,6 +289,205 @@ def run_uneven(args):
         d.close()
 
 
+def run_large(args):
+    """The large configuration: a K = 9 DMN (512 leaves, 1533 unknowns) whose
+    matrix is the Perzyna viscoplastic leaf with moduli falling 0.2 %/K, on
+    1,048,576 points; dt = 0.01 s, strain rates N(0, 1e-2)/s per component,
+    +1 K per increment from 293 K.  Mixed precision, learned warm start (the
+    network trained on pairs of the FP64 solver for the first 65,536 points)
+    and the persistent compact solve, as in the default workload."""
+    import torch
+
+    from paper_2109_14403_gb300 import DMN, synthetic as syn
+    from paper_2109_14403_gb300.mlp import MLP
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    K, dt = syn.LARGE_K, syn.LARGE_DT
+    n = (1 << 20) if args.points == N_POINTS else args.points
+    n_train = min(n, 65536)
+    steps, warm = args.steps, args.warmup
+    n_gen = 6
+    first = n_gen + warm
+    deps_h, theta_h = syn.large_path(n_points=n, n_incr=first + steps, seed=42 + rank)
+    D = torch.tensor(deps_h, device=dev)
+    T = torch.tensor(theta_h, device=dev)
+    del deps_h
+    w, nrm, ph = syn.tree(K)
+    mats = syn.materials_viscoplastic()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- network: pairs of the plain FP64 solver on the first n_train points
+    t0 = time.perf_counter()
+    fp64 = DMN(K, w, nrm, ph, mats, tol=TOL, precision="fp64")
+    net = MLP(K=K, hidden=512, n_hidden=3, max_batch=n, seed=0)
+    sp, sc = None, fp64.init_state(torch.full((n_train,), syn.THETA_START, dtype=torch.float64, device=dev))
+    feats, tgts = [], []
+    for k in range(n_gen):
+        s1, _, _, _ = fp64.eval(D[k, :n_train], T[k, :n_train], dt, sc)
+        feats.append(net.features(D[k, :n_train], T[k, :n_train], sc, sp))
+        tgts.append(net.targets(sc, s1))
+        sp, sc = sc, s1
+    F, Tg = torch.cat(feats), torch.cat(tgts)
+    del feats, tgts, sp, sc
+    net.fit_normalization(F, Tg)
+    X, Y = net.normalize_features(F), net.normalize_targets(Tg)
+    del F, Tg
+    perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    X, Y = X[perm].contiguous(), Y[perm].contiguous()
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    B, epochs = 4096, 12
+    for ep in range(epochs):
+        for i in range(0, X.shape[0] - B + 1, B):
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
+    torch.cuda.synchronize()
+    train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
+                  "gen_and_train_s": time.perf_counter() - t0}
+    del X, Y
+
+    # ---- the full batch: history by the plain mixed solve, then warm steps
+    mixed = DMN(K, w, nrm, ph, mats, tol=TOL, precision="mixed")
+    st0 = mixed.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+    bufs = [torch.empty_like(st0), st0, torch.empty_like(st0)]
+    out = torch.empty((n, 57), dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    it = torch.empty(n, dtype=torch.int32, device=dev)
+    xin = torch.empty((n, net.n_in_pad), dtype=torch.bfloat16, device=dev)
+    da = torch.empty((n, net.n_out), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for k in range(n_gen):
+        p, c, nx = bufs
+        mixed.eval(D[k], T[k], dt, c, nx, out, st, it)
+        bufs[0], bufs[1], bufs[2] = c, nx, p
+    have_prev = n_gen >= 2
+
+    def warm_step(k, it_out, ev=None):
+        p, c, nx = bufs
+        net.input(D[k], T[k], c, p if have_prev else None, out=xin)
+        net.predict(xin, out=da)
+        if ev is not None:
+            ev[0].record(stream)
+        mixed.eval_warm(D[k], T[k], dt, c, da, nx, out, st, it_out)
+        if ev is not None:
+            ev[1].record(stream)
+        bufs[0], bufs[1], bufs[2] = c, nx, p
+
+    for k in range(n_gen, first):
+        warm_step(k, it)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(steps)]
+    iters = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for j in range(steps):
+            itj = torch.empty(n, dtype=torch.int32, device=dev)
+            warm_step(first + j, itj, kev[j])
+            iters.append(itj)
+        ev1.record(stream)
+        barrier()
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    solve_ms = statistics.mean(kev[j][0].elapsed_time(kev[j][1]) for j in range(steps))
+    itc = torch.cat(iters)
+    hist = torch.bincount(itc.cpu().long()).tolist()
+    mean_iters = float(itc.float().mean().item())
+    nonconv = int(((st & 3) != 0).sum().item())
+    fallback_rate = float(((st & 4) != 0).float().mean().item())
+    # accuracy of the last timed increment on the first n_train points against
+    # the FP64 solution at tol 1e-13 from the same state
+    ref = DMN(K, w, nrm, ph, mats, tol=1e-13, precision="fp64")
+    kl = first + steps - 1
+    _, oref, _, _ = ref.eval(D[kl, :n_train], T[kl, :n_train], dt, bufs[0][:n_train].contiguous())
+    sig, sref = out[:n_train, :6], oref[:, :6]
+    acc_err = ((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item()
+    ref.close()
+    variants = {}
+    if not args.no_variants:
+        # the same increments without the network (mixed, all points) and the FP64 path
+        # (the first n_train points)
+        for name, dmn, m in (("mixed_plain", mixed, n), ("fp64_plain", fp64, n_train)):
+            sa = bufs[0][:m].clone()
+            sb = torch.empty_like(sa)
+            barrier()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            its = []
+            v0.record(stream)
+            for j in range(steps):
+                itv = torch.empty(m, dtype=torch.int32, device=dev)
+                dmn.eval(D[first + j, :m], T[first + j, :m], dt, sa, sb, out[:m], st[:m], itv)
+                sa, sb = sb, sa
+                its.append(itv)
+            v1.record(stream)
+            barrier()
+            ms = max_over_ranks(v0.elapsed_time(v1), world, dev)
+            variants[name] = {"value": whole_job_rate(m, world, steps, ms), "ms_per_step": ms / steps,
+                              "points": m, "mean_iters": float(torch.cat(its).float().mean().item())}
+            del sa, sb
+    fp64.close()
+    mixed.close()
+    net.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    bpe = algorithmic_bytes_per_eval(K, 13) + 4 * 3 * ((1 << K) - 1)
+    peak, how = measured_peaks()
+    passes = mean_iters + 1.0
+    flops = alu_flops_per_pass(K) * passes * n / (solve_ms / 1e3) / 1e12
+    hbm = bpe * n / (solve_ms / 1e3) / 1e9
+    line = {"metric": "Gauss-pt DMN evals/s, K=9 Perzyna matrix, mixed + learned warm start",
+            "value": whole_job_rate(n, world, steps, t_ms), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 + float-float (2xf32) + bf16 MLP", "data": "synthetic",
+            "config": {"workload": f"K=9 DMN, Perzyna matrix (m 5, t_visc 1e3 s, moduli -0.2 %/K), {n} points, "
+                                   f"dt {dt} s, strain rates N(0,1e-2)/s, +1 K per increment; increments "
+                                   f"{first}-{first + steps - 1}",
+                       "tol": TOL, "state_bytes_per_buffer": int(8 * state_words(K, 256, 13) * n),
+                       "parallelism": f"replicas x{world} (independent points)"},
+            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "reference": "FP64 path at tol 1e-13",
+                         "points": n_train},
+            "iter_hist": hist, "mean_iters": mean_iters, "nonconverged": nonconv,
+            "fallback_rate": fallback_rate, "warm_start_training": train_info, "variants": variants,
+            "solve_kernel_ms": solve_ms,
+            "roofline": {"bound": "alu", "achieved": flops, "peak": 73.2, "unit": "TFLOP/s", "frac": flops / 73.2,
+                         "traffic": None, "kernel": "dmn_solve_compact<float, dfl, 256, 1, 2>",
+                         "flops_per_pass": alu_flops_per_pass(K), "passes_per_eval": passes,
+                         "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+                                 "peak_source": how, "bytes_per_eval": bpe}},
+            "clocks": clk.summary(), "gpu_launches": 6 * steps}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_large()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_large(n_points=64, threads=None):
+    """FP64 oracle on the host cores: the first increment of the large
+    configuration's path on n_points points."""
+    import oracle
+    from paper_2109_14403_gb300 import synthetic as syn
+    threads = threads or os.cpu_count() or 1
+    w, nrm, ph = syn.tree(syn.LARGE_K)
+    tree = oracle.Tree(syn.LARGE_K, w, nrm, ph, syn.materials_viscoplastic())
+    deps, theta = syn.large_path(n_points=n_points, n_incr=1)
+    s = tree.init_state(n_points, syn.THETA_START)
+    t0 = time.perf_counter()
+    oracle.eval_batch(tree, deps[0], theta[0], syn.LARGE_DT, s, tol=TOL, threads=threads)
+    dtm = time.perf_counter() - t0
+    return {"value": n_points / dtm, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n_points} points x the first increment of the K=9 Perzyna path, tol {TOL}"}
+
+
 def run_mlp(args):
     """Inference of the warm-start network alone (4 tcgen05 GEMMs with fused
     bias/SiLU/de-normalisation epilogues) on 65,536 points: the tensor path."""
@@ -350,7 +550,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="uneven workload only")
-    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven", "mlp"])
+    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven", "mlp", "large"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -362,6 +562,9 @@ def main():
         return
     if args.workload == "mlp":
         run_mlp(args)
+        return
+    if args.workload == "large":
+        run_large(args)
         return
 
     import torch

@@ -31,7 +31,7 @@ extern "C" {
 
 typedef struct dmn_mlp_s *dmn_mlp;
 
-/* Create a network for trees of depth K (1..8), hidden width a multiple of 128,
+/* Create a network for trees of depth K (1..9), hidden width a multiple of 128,
    n_hidden >= 1 hidden layers, batches up to max_batch rows; weights drawn from
    U(-1/sqrt(fan_in), 1/sqrt(fan_in)) with the given seed, biases 0.
    Allocates weights, optimiser state and workspace on the current device. */

@@ -377,7 +377,7 @@ extern "C" dmn_status dmn_mlp_create(dmn_mlp *out, int32_t K, int32_t hidden, in
   set_error_message("");
   if (!out) return fail(DMN_ERR_ARG, "dmn_mlp_create: out is NULL");
   *out = nullptr;
-  if (K < 1 || K > 8) return fail(DMN_ERR_ARG, "dmn_mlp_create: K=%d outside 1..8", K);
+  if (K < 1 || K > 9) return fail(DMN_ERR_ARG, "dmn_mlp_create: K=%d outside 1..9", K);
   if (hidden < 128 || hidden % 128 || hidden > 4096)
     return fail(DMN_ERR_ARG, "dmn_mlp_create: hidden=%d not a multiple of 128 in 128..4096", hidden);
   if (n_hidden < 1 || n_hidden > 8) return fail(DMN_ERR_ARG, "dmn_mlp_create: n_hidden=%d", n_hidden);

@@ -198,3 +198,59 @@ def test_warm_start_gain_on_the_k8_random_walk():
     plain.close()
     mixed.close()
     net.close()
+
+
+def test_warm_start_k9_perzyna():
+    """K = 9 with the Perzyna matrix (1541 network inputs, 1533 outputs): the
+    network trained on FP64 pairs warm-starts the mixed solve, which stays
+    within the stopping-criterion bound of the FP64 solution (tol 1e-13) and
+    takes no more Newton iterations than the plain start.  Algorithm 1 stops
+    at |r| < tol N |sigma_bar|, N = 511 here, so the stress can be off by about
+    tol N (stiffness contrast ~30) = 1.5e-8; the bound allows a factor 4."""
+    from paper_2109_14403_gb300 import DMN
+    from paper_2109_14403_gb300.mlp import MLP
+    dev = _dev()
+    K, n, n_train = 9, 8192, 5
+    w, nrm, ph = syn.tree(K)
+    mats = syn.materials_viscoplastic()
+    deps, theta = syn.large_path(n_points=n, n_incr=n_train + 1, seed=12)
+    deps *= 30.0  # strain rates large enough for viscoplastic flow
+    D = torch.tensor(deps, device=dev)
+    T = torch.tensor(theta, device=dev)
+    dt = syn.LARGE_DT
+    plain = DMN(K, w, nrm, ph, mats, precision="fp64", tol=1e-13)
+    net = MLP(K=K, hidden=256, n_hidden=2, max_batch=n, seed=0)
+    assert net.n_in == 8 + 3 * 511 and net.n_out == 3 * 511
+    s_prev, s = None, plain.init_state(torch.full((n,), 293.0, dtype=torch.float64, device=dev))
+    feats, tgts = [], []
+    for k in range(n_train):
+        s1, _, _, _ = plain.eval(D[k], T[k], dt, s)
+        feats.append(net.features(D[k], T[k], s, s_prev))
+        tgts.append(net.targets(s, s1))
+        s_prev, s = s, s1
+    F, Tg = torch.cat(feats), torch.cat(tgts)
+    net.fit_normalization(F, Tg)
+    X, Y = net.normalize_features(F), net.normalize_targets(Tg)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    for ep in range(20):
+        for i in range(0, X.shape[0] - 2048 + 1, 2048):
+            net.train_step(X[i:i + 2048], Y[i:i + 2048], 1e-3, loss)
+    k = n_train
+    _, ref, st_r, _ = plain.eval(D[k], T[k], dt, s)
+    mixed = DMN(K, w, nrm, ph, mats, precision="mixed", tol=1e-12)
+    da = net.predict(net.input(D[k], T[k], s, s_prev))
+    _, op, stp, itp = mixed.eval(D[k], T[k], dt, s)
+    _, ow, stw, itw = mixed.eval_warm(D[k], T[k], dt, s, da)
+    torch.cuda.synchronize()
+    assert (st_r.cpu() == 0).all() and (stp.cpu() == 0).all() and ((stw.cpu() & 3) == 0).all()
+    r = ref.cpu().numpy()[:, :6]
+    bound = 4 * 1e-12 * 511 * 30
+    for o in (op, ow):
+        g = o.cpu().numpy()[:, :6]
+        assert (np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1)).max() < bound
+    ip, iw = itp.cpu().numpy(), itw.cpu().numpy()
+    print(f"\nK=9 warm start: mean Newton iterations {ip.mean():.3f} -> {iw.mean():.3f}")
+    assert iw.mean() <= ip.mean()
+    plain.close()
+    mixed.close()
+    net.close()
