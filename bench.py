@@ -15,7 +15,7 @@ from the plain FP64 solver.  The plain mixed and plain FP64 GPU paths are timed
 on the same increments ("variants"); tolerance 1e-12.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload random_walk|uneven]
+                       [--workload random_walk|uneven|mlp|large|cyclic]
 --impl reference times the FP64 CPU oracle on the host cores (a bounded
 sample of the same workload per step).
 """
@@ -472,6 +472,88 @@ def run_large(args):
         torch.distributed.destroy_process_group()
 
 
+def run_cyclic(args):
+    """Stress-controlled adiabatic cyclic loading (dmn_eval_mixed): K = 8 DMN
+    whose matrix is the Perzyna leaf with the PA66 rate law's m and viscous
+    time, 65,536 points, uniaxial sinusoidal stress (amplitudes 20-80 MPa,
+    11 or 22 direction, 10 Hz, 20 increments per cycle, dt = 5 ms); every
+    increment is an outer Newton over Algorithm 1 evaluations (mixed
+    precision, each one warm-started from the previous one's jumps) until the
+    prescribed stresses and the heat balance hold to 1e-10."""
+    import torch
+
+    from paper_2109_14403_gb300 import DMN, synthetic as syn
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n, steps, warm = args.points, args.steps, args.warmup
+    n_cycles = (warm + steps + syn.CYCLE_STEPS - 1) // syn.CYCLE_STEPS
+    mask_h, tgt_h, dt, amp, direction = syn.cyclic_stress(n, n_cycles, seed=42 + rank)
+    w, nrm, ph = syn.tree(K_DEPTH)
+    c_heat = syn.effective_heat_capacity(w, ph)
+    d = DMN(K_DEPTH, w, nrm, ph, syn.materials_cyclic(), tol=TOL, precision=args.precision)
+    mask = torch.tensor(mask_h, device=dev)
+    tgt = torch.tensor(tgt_h[:warm + steps], device=dev)
+    deps = torch.zeros((n, 6), dtype=torch.float64, device=dev)
+    theta = torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev)
+    s = d.init_state(theta.clone())
+    tol_outer = 1e-10
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for k in range(warm):
+        s, out, st, it, outer = d.eval_mixed(mask, tgt[k], deps, theta, dt, c_heat, s, tol_outer=tol_outer)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    outers, stats = [], []
+    with ClockSampler(local) as clk:
+        e0.record()
+        for k in range(warm, warm + steps):
+            s, out, st, it, outer = d.eval_mixed(mask, tgt[k], deps, theta, dt, c_heat, s,
+                                                 tol_outer=tol_outer)
+            outers.append(outer)
+            stats.append(st)
+        e1.record()
+        barrier()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    oc = torch.stack(outers)
+    evals = int(oc.max(dim=1).values.sum().item())  # solve launches (settled points are skipped)
+    failed = int(((torch.stack(stats) & 0xB) != 0).sum().item())
+    dT = (theta - syn.THETA_START).cpu().numpy()
+    d.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {"metric": "stress-controlled adiabatic Gauss-pt increments/s, K=8 (outer Newton over Algorithm 1)",
+            "value": whole_job_rate(n, world, steps, t_ms), "unit": "GP-increments/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32 + float-float (2xf32); f64 outer Newton",
+            "data": "synthetic",
+            "config": {"workload": f"K=8 DMN, Perzyna matrix (m 2, t_visc 74/15.5 s), {n} points, uniaxial "
+                                   "sinusoidal stress 20-80 MPa at 10 Hz, 20 increments per cycle, adiabatic; "
+                                   f"increments {warm}-{warm + steps - 1}",
+                       "precision": args.precision, "tol": TOL, "tol_outer": tol_outer,
+                       "heat_capacity_MPa_per_K": c_heat,
+                       "parallelism": f"replicas x{world} (independent points)"},
+            "solve_launches_per_increment": evals / steps, "mean_outer": float(oc.float().mean().item()),
+            "not_converged": failed,
+            "temperature_change_K": {"min": float(dT.min()), "max": float(dT.max())},
+            "clocks": clk.summary(), "gpu_launches": 2 * evals + 2 * steps}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def cpu_baseline_large(n_points=64, threads=None):
     """FP64 oracle on the host cores: the first increment of the large
     configuration's path on n_points points."""
@@ -550,8 +632,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="uneven workload only")
-    ap.add_argument("--workload", default="random_walk", choices=["random_walk", "uneven", "mlp", "large"])
+                    help="uneven and cyclic workloads only")
+    ap.add_argument("--workload", default="random_walk",
+                    choices=["random_walk", "uneven", "mlp", "large", "cyclic"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -563,6 +646,9 @@ def main():
         return
     if args.workload == "mlp":
         run_mlp(args)
+        return
+    if args.workload == "cyclic":
+        run_cyclic(args)
         return
     if args.workload == "large":
         run_large(args)

@@ -64,7 +64,9 @@ enum {
   DMN_PT_OK = 0,            /* residual < tol                              */
   DMN_PT_NOT_CONVERGED = 1, /* maxit Newton iterations without res < tol   */
   DMN_PT_NONFINITE = 2,     /* a residual or an output was NaN or Inf      */
-  DMN_PT_FALLBACK_USED = 4  /* bit: warm start failed, re-run from a^n     */
+  DMN_PT_FALLBACK_USED = 4, /* bit: warm start failed, re-run from a^n     */
+  DMN_PT_OUTER_NOT_CONVERGED = 8 /* bit (dmn_eval_mixed): the prescribed
+                                    stresses / heat balance were not met    */
 };
 
 /* phase laws (Sec. 4) */
@@ -221,6 +223,48 @@ dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const double *norma
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *dmn_last_error(void);
+
+/*
+ * Mixed strain / stress control with optional adiabatic heating: one load
+ * increment at every point.  No function of the paper has this form; it
+ * closes, around Algorithm 1, the conditions of the paper's validation runs
+ * (Sec. 5.4: mixed boundary conditions, stress-free perpendicular to the
+ * load; Sec. 5.5: stress-controlled cyclic loading under adiabatic
+ * conditions).
+ *   d_mask     n uint8 (device): bit c (0..5) set = Mandel stress component c
+ *              is prescribed, clear = the strain increment of component c
+ *              is; bit 6 set = adiabatic, theta^{n+1} solves
+ *              c_heat (theta^{n+1} - theta^n) / dt = D_bar; clear = theta^{n+1}
+ *              is prescribed
+ *   d_target   n x 6: the prescribed sigma_bar_c (MPa) or deps_c per component
+ *   d_deps     n x 6, in: a start for the unknown increments (the prescribed
+ *              ones are taken from d_target); out: the increments found
+ *   d_theta    n, in: theta^{n+1} if prescribed, else a start; out: found
+ *   dt, c_heat time increment (s) and volumetric heat capacity (MPa/K, i.e.
+ *              1e-6 J/(m^3 K)), both > 0
+ *   max_outer  evaluations at most (>= 1); tol_outer (> 0): a point is done
+ *              when every prescribed stress is within tol_outer max(|sigma_bar|,
+ *              1 MPa) of its target and the heat balance within
+ *              tol_outer c_heat (1 K) / dt
+ *   d_state_in, d_state_out, d_out, d_status, d_iters: as dmn_eval, holding
+ *              the point's last evaluation; d_status also gets
+ *              DMN_PT_OUTER_NOT_CONVERGED
+ *   d_outer    n int32: evaluations of the point until it was settled (met
+ *              the conditions, or was given up); later evaluations skip it
+ *   d_work     NULL, or n x 3(2^K-1) floats of scratch: each evaluation after
+ *              the first then starts from the previous one's jumps
+ *              (dmn_eval_warm), else from a^n
+ * Outer Newton on x = (unknown strain increments, theta^{n+1} if adiabatic)
+ * with the algorithmic tangents d sigma_bar/d eps_bar, d sigma_bar/d theta,
+ * d D_bar/d eps_bar and d D_bar/d theta (FP64 LU with partial pivoting, one
+ * system of at most 7 unknowns per point).  The stream is synchronised once
+ * per evaluation to stop when every point is done.
+ */
+dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_points, const uint8_t *d_mask,
+                          const double *d_target, double *d_deps, double *d_theta, double dt,
+                          double c_heat, int32_t max_outer, double tol_outer,
+                          const double *d_state_in, double *d_state_out, double *d_out,
+                          int32_t *d_status, int32_t *d_iters, int32_t *d_outer, float *d_work);
 
 #ifdef __cplusplus
 }

@@ -183,3 +183,81 @@ def split_out(out):
     return {"sig": out[..., 0:6], "C": out[..., 6:42].reshape(out.shape[:-1] + (6, 6)),
             "C_theta": out[..., 42:48], "D": out[..., 48], "D_eps": out[..., 49:55],
             "D_theta": out[..., 55], "diss": out[..., 56]}
+
+
+def eval_mixed(tree: Tree, mask, target, deps, theta, dt, c_heat, state_in, *, max_outer=20,
+               tol_outer=1e-10, tol=1e-12, threads=None):
+    """One increment under mixed control, by a plain outer Newton on eval_batch.
+
+    Per point, bit c (0..5) of ``mask`` prescribes the Mandel stress component
+    sigma_bar_c = target_c instead of the strain increment deps_c = target_c;
+    bit 6 replaces the prescribed theta^{n+1} by the implicit-Euler form of the
+    macroscopic heat equation (Sec. 2, eq. macro_heat) without heat source and
+    flux (adiabatic): c_heat (theta^{n+1} - theta^n) / dt = D_bar.  The
+    unknowns are solved with the algorithmic tangents d sigma_bar / d eps_bar,
+    d sigma_bar / d theta, d D_bar / d eps_bar and d D_bar / d theta (Sec. 3.3)
+    and numpy.linalg.solve.  ``deps`` and ``theta`` are starting values.
+    Returns (deps, theta, state_out, out, status, outer): status 8 = the
+    conditions were not met within max_outer evaluations.
+    """
+    mask = np.asarray(mask, np.uint8).ravel()
+    n = mask.size
+    target = np.asarray(target, np.float64).reshape(n, 6)
+    x_eps = np.array(deps, np.float64).reshape(n, 6)
+    x_th = np.array(np.broadcast_to(np.asarray(theta, np.float64), (n,)))
+    sin = np.asarray(state_in, np.float64).reshape(n, tree.state_words)
+    theta_n = sin[:, 6]
+    for c in range(6):
+        strain = ((mask >> c) & 1) == 0
+        x_eps[strain, c] = target[strain, c]
+    outer = np.zeros(n, np.int32)
+    failed = np.zeros(n, bool)
+    open_ = np.ones(n, bool)
+    sout = np.zeros_like(sin)
+    out = np.zeros((n, OUT_WORDS))
+    st = np.zeros(n, np.int32)
+    for k in range(max_outer):
+        idx = np.nonzero(open_)[0]
+        if idx.size == 0:
+            break
+        so, o, s, _ = eval_batch(tree, x_eps[idx], x_th[idx], dt, sin[idx], tol=tol,
+                                 threads=threads)
+        sout[idx], out[idx], st[idx] = so, o, s
+        for q, i in enumerate(idx):
+            sig, C, C_th = o[q, 0:6], o[q, 6:42].reshape(6, 6), o[q, 42:48]
+            D, D_eps, D_th = o[q, 48], o[q, 49:55], o[q, 55]
+            if s[q] & 3:
+                failed[i], open_[i], outer[i] = True, False, k + 1
+                continue
+            stress = [c for c in range(6) if (mask[i] >> c) & 1]
+            adiabatic = bool((mask[i] >> 6) & 1)
+            scale = max(1.0, np.abs(sig).max())
+            r = [sig[c] - target[i, c] for c in stress]
+            done = all(abs(v) <= tol_outer * scale for v in r)
+            if adiabatic:
+                rh = c_heat * (x_th[i] - theta_n[i]) / dt - D
+                r.append(rh)
+                done = done and abs(rh) <= tol_outer * c_heat / dt
+            if done:
+                open_[i], outer[i] = False, k + 1
+                continue
+            if k + 1 == max_outer:
+                failed[i], open_[i], outer[i] = True, False, k + 1
+                continue
+            J = np.zeros((len(r), len(r)))
+            for a, c in enumerate(stress):
+                for b, e in enumerate(stress):
+                    J[a, b] = C[c, e]
+                if adiabatic:
+                    J[a, -1] = C_th[c]
+            if adiabatic:
+                for b, e in enumerate(stress):
+                    J[-1, b] = -D_eps[e]
+                J[-1, -1] = c_heat / dt - D_th
+            step = np.linalg.solve(J, -np.asarray(r))
+            for a, c in enumerate(stress):
+                x_eps[i, c] += step[a]
+            if adiabatic:
+                x_th[i] += step[-1]
+    st = st | np.where(failed, 8, 0).astype(np.int32)
+    return x_eps, x_th, sout, out, st, outer

@@ -20,6 +20,7 @@ struct dmn_handle_s {
   int device, num_sms;
   int blocks_per_sm;     // resident CTAs per SM of the selected kernel variant
   unsigned long long *d_queue;  // work-queue counter (one per handle)
+  unsigned long long *d_open;   // dmn_eval_mixed: points still iterating
   double *d_node;        // [N][kNodeWords]
   float *d_node_df;      // [N][kNodeDfl]
   double *d_leafw;       // [nleaf]
@@ -104,6 +105,7 @@ static void free_handle(dmn_handle h) {
   cudaFree(h->d_zoff);
   cudaFree(h->d_mat);
   cudaFree(h->d_queue);
+  cudaFree(h->d_open);
   delete h;
 }
 
@@ -250,7 +252,8 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_mat, sizeof(double) * kMatWords * n_mats)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess) {
+      (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_open, sizeof(unsigned long long))) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMalloc");
   }
@@ -306,7 +309,8 @@ extern "C" dmn_status dmn_state_init(dmn_handle h, double *d_state, int64_t n_po
 static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
                             const double *d_deps, const double *d_theta, double dt,
                             const double *d_state_in, double *d_state_out, double *d_out,
-                            int32_t *d_status, int32_t *d_iters, const float *d_da) {
+                            int32_t *d_status, int32_t *d_iters, const float *d_da,
+                            const int32_t *d_skip = nullptr) {
   g_err[0] = 0;
   if (!h) return fail(DMN_ERR_ARG, "dmn_eval: NULL handle");
   if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_eval: n_points < 0");
@@ -353,6 +357,7 @@ static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
   P.iters = d_iters;
   P.queue = h->d_queue;
   P.da0 = d_da;
+  P.skip = d_skip;
   int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm;
   if (grid > n_points) grid = n_points;
   cudaError_t e = launch_solve(P, mixed, h->opt.solve_variant, (int)grid, (cudaStream_t)stream);
@@ -375,4 +380,51 @@ extern "C" dmn_status dmn_eval_warm(dmn_handle h, dmn_stream stream, int64_t n_p
   if (!d_da && n_points > 0) return fail(DMN_ERR_ARG, "dmn_eval_warm: d_da is NULL");
   return eval_impl(h, stream, n_points, d_deps, d_theta, dt, d_state_in, d_state_out, d_out,
                    d_status, d_iters, d_da);
+}
+
+// Outer Newton of dmn_eval_mixed: evaluate, update the unknown increments and
+// temperatures on the device, read back how many points still iterate.
+extern "C" dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_points,
+                                     const uint8_t *d_mask, const double *d_target, double *d_deps,
+                                     double *d_theta, double dt, double c_heat, int32_t max_outer,
+                                     double tol_outer, const double *d_state_in,
+                                     double *d_state_out, double *d_out, int32_t *d_status,
+                                     int32_t *d_iters, int32_t *d_outer, float *d_work) {
+  g_err[0] = 0;
+  if (!h) return fail(DMN_ERR_ARG, "dmn_eval_mixed: NULL handle");
+  if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_eval_mixed: n_points < 0");
+  if (n_points == 0) return DMN_OK;
+  if (!d_mask || !d_target || !d_deps || !d_theta || !d_outer)
+    return fail(DMN_ERR_ARG, "dmn_eval_mixed: NULL pointer");
+  if (!(c_heat > 0.0) || !isfinite(c_heat)) return fail(DMN_ERR_ARG, "dmn_eval_mixed: c_heat must be > 0");
+  if (max_outer < 1) return fail(DMN_ERR_ARG, "dmn_eval_mixed: max_outer must be >= 1");
+  if (!(tol_outer > 0.0) || !isfinite(tol_outer))
+    return fail(DMN_ERR_ARG, "dmn_eval_mixed: tol_outer must be > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = mixed_prepare(s, n_points, d_mask, d_target, d_deps, d_outer);
+  if (e != cudaSuccess) return cuda_fail(e, "dmn_eval_mixed prepare");
+  for (int it = 0; it < max_outer; ++it) {
+    const float *da = (it > 0 && d_work) ? d_work : nullptr;
+    // points settled in an earlier evaluation (d_outer != 0) keep its results
+    const dmn_status st = eval_impl(h, stream, n_points, d_deps, d_theta, dt, d_state_in,
+                                    d_state_out, d_out, d_status, d_iters, da,
+                                    it > 0 ? d_outer : nullptr);
+    if (st != DMN_OK) return st;
+    if ((e = cudaMemsetAsync(h->d_open, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+      return cuda_fail(e, "dmn_eval_mixed memset");
+    const bool last = it + 1 == max_outer;
+    e = mixed_update(s, n_points, h->SW, 3 * h->N, d_mask, d_target, d_deps, d_theta, dt, c_heat,
+                     tol_outer, d_state_in, d_state_out, d_out, d_status, d_outer, it, last,
+                     last ? nullptr : d_work, h->d_open);
+    if (e != cudaSuccess) return cuda_fail(e, "dmn_eval_mixed update");
+    if (last) break;
+    unsigned long long open = 0;
+    if ((e = cudaMemcpyAsync(&open, h->d_open, sizeof(open), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "dmn_eval_mixed read-back");
+    if (open == 0) break;
+  }
+  e = mixed_finish(s, n_points, d_status, d_outer);
+  if (e != cudaSuccess) return cuda_fail(e, "dmn_eval_mixed finish");
+  return DMN_OK;
 }

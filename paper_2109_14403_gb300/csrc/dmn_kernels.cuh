@@ -53,6 +53,7 @@ struct SolveParams {
   int law;                         // largest material kind of the tree (1 or 2)
   unsigned long long *queue;       // device counter of points taken (zeroed per launch)
   const float *da0;                // optional warm-start increment [n][3N] (NULL: start at a^n)
+  const int *skip;                 // optional [n]: points with skip[i] != 0 are left untouched
   double tol, gamma, res_floor, dt;
   const double *node;      // [N][kNodeWords]: n0 n1 n2 c1 c2 w w*c1*c2 1/(w*c1*c2)
                            //   n0/sqrt2 n1/sqrt2 n2/sqrt2 0

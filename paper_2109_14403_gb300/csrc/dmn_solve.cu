@@ -149,7 +149,11 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
   for (;;) {
-    if (t == 0) ctrl->next = atomicAdd(P.queue, 1ull);
+    if (t == 0) {
+      unsigned long long q = atomicAdd(P.queue, 1ull);
+      while (P.skip && q < (unsigned long long)P.n_points && P.skip[q] != 0) q = atomicAdd(P.queue, 1ull);
+      ctrl->next = q;
+    }
     __syncthreads();
     const int64_t pt = int64_t(ctrl->next);
     if (pt >= P.n_points) break;

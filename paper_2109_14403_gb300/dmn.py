@@ -15,6 +15,8 @@ from . import _build
 
 DMN_OK, DMN_ERR_ARG = 0, 1
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE, PT_FALLBACK_USED = 0, 1, 2, 4
+PT_OUTER_NOT_CONVERGED = 8
+MIXED_ADIABATIC = 1 << 6  # dmn_eval_mixed mask bit: theta from the heat balance
 PREC_FP64, PREC_MIXED = 0, 1
 OUT_WORDS = 57
 
@@ -66,6 +68,8 @@ SIGNATURES = {
     "dmn_mlp_get_normalization": (_I32, [_P, _P, _P, _P, _P]),
     "dmn_gemm_bf16_tn": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
     "dmn_eval_warm": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P]),
+    "dmn_eval_mixed": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _D, _D, _I32, _D, _P, _P, _P, _P, _P,
+                              _P, _P]),
 }
 
 
@@ -207,6 +211,36 @@ class DMN:
                              _dev(status, torch.int32, (n,), "status"),
                              _dev(iters, torch.int32, (n,), "iters")), "dmn_eval")
         return state_out, out, status, iters
+
+    def eval_mixed(self, mask, target, deps, theta, dt, c_heat, state_in, *, max_outer=10,
+                   tol_outer=1e-10, warm=True, stream=None):
+        """``dmn_eval_mixed``: prescribed stresses (mask bits 0..5) and adiabatic
+        temperature (bit 6).  ``deps`` and ``theta`` are updated in place.
+        Returns (state_out, out, status, iters, outer)."""
+        import torch
+        n = deps.shape[0]
+        dev = deps.device
+        state_out = torch.empty_like(state_in)
+        out = torch.empty((n, OUT_WORDS), dtype=torch.float64, device=dev)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        iters = torch.empty(n, dtype=torch.int32, device=dev)
+        outer = torch.empty(n, dtype=torch.int32, device=dev)
+        work = torch.empty((n, 3 * self.nnode), dtype=torch.float32, device=dev) if warm else None
+        _check(_lib.dmn_eval_mixed(self._h, _stream_ptr(stream), n,
+                                   _dev(mask, torch.uint8, (n,), "mask"),
+                                   _dev(target, torch.float64, (n, 6), "target"),
+                                   _dev(deps, torch.float64, (n, 6), "deps"),
+                                   _dev(theta, torch.float64, (n,), "theta"), float(dt),
+                                   float(c_heat), int(max_outer), float(tol_outer),
+                                   _dev(state_in, torch.float64, (n, self.state_words), "state_in"),
+                                   _dev(state_out, torch.float64, (n, self.state_words), "state_out"),
+                                   _dev(out, torch.float64, (n, OUT_WORDS), "out"),
+                                   _dev(status, torch.int32, (n,), "status"),
+                                   _dev(iters, torch.int32, (n,), "iters"),
+                                   _dev(outer, torch.int32, (n,), "outer"),
+                                   None if work is None else
+                                   _dev(work, torch.float32, None, "work")), "dmn_eval_mixed")
+        return state_out, out, status, iters, outer
 
     def eval_warm(self, deps, theta, dt, state_in, da, state_out=None, out=None, status=None,
                   iters=None, stream=None):

@@ -26,7 +26,16 @@ stand in for its strain-controlled virtual experiments, Sec. 5.4):
     Perzyna overstress rate law, rate exponent 5, viscous time 1e3 s, and
     moduli falling 0.2 %/K; K = 9 tree (seed 1234 + 9); 100 increments of
     dt = 0.01 s with strain rates N(0, 1e-2)/s per Mandel component and the
-    temperature ramped 293 -> 393 K (1 K per increment).
+    temperature ramped 293 -> 393 K (1 K per increment);
+  * stress-controlled cyclic loading (Sec. 5.4, cyclic validation): uniaxial
+    sinusoidal stress sigma_ampl sin(2 pi t / T_c) in the 11 or the 22
+    direction, all other stress components 0, adiabatic; T_c = 0.1 s (10 Hz),
+    20 increments per cycle, amplitudes 20, 40, 60 and 80 MPa; each point
+    draws its amplitude and direction; volumetric heat capacities 2.1 MPa/K
+    (E-glass) and 1.9 MPa/K (PA66), the paper's material tables, averaged
+    with the leaf weights; the matrix is the Perzyna matrix with the PA66
+    rate law's exponent m = 2 and viscous time eta_0 / sigma_Y0 = 74/15.5 s
+    and, as the PA66's, moduli that do not depend on the temperature.
 Units: MPa, K, s.  Symmetric tensors are Mandel 6-vectors.
 """
 from __future__ import annotations
@@ -42,6 +51,14 @@ FIBER = (KIND_THERMOELASTIC, 72000.0, 0.22, 5e-6, 293.0, 0.0, 0.0, 0.0)
 MATRIX = (KIND_J2_LINEAR, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0)
 MATRIX_PERZYNA = (KIND_J2_PERZYNA, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0, 5.0, 1e3, -0.002, 0.0)
 THETA_START = 293.0
+# volumetric heat capacity c_0 (MPa/K = 1e6 J m^-3 K^-1) of the rows of
+# materials(): E-glass fiber and PA66 matrix (Sec. 4, material tables)
+HEAT_CAPACITY = (2.1, 1.9)
+CYCLE_PERIOD = 0.1
+CYCLE_STEPS = 20
+CYCLE_AMPLITUDES = (20.0, 40.0, 60.0, 80.0)
+# dmn_eval_mixed mask: all six stress components prescribed, adiabatic
+MASK_STRESS_ADIABATIC = 0x7F
 LARGE_K = 9
 LARGE_DT = 0.01
 
@@ -55,6 +72,13 @@ def materials_viscoplastic():
     fib = np.zeros(12)
     fib[:8] = FIBER
     return np.array([fib, MATRIX_PERZYNA], dtype=np.float64)
+
+
+def materials_cyclic():
+    """Fiber and the matrix of the cyclic workload as 12-column rows."""
+    m = materials_viscoplastic()
+    m[1, 8], m[1, 9], m[1, 10] = 2.0, 74.0 / 15.5, 0.0
+    return m
 
 
 def large_path(n_points=1048576, n_incr=100, seed=42, dtype=np.float64):
@@ -123,3 +147,25 @@ def uneven_batch(n_points=262144, n_incr=50, s0=1e-3, seed=42):
 
 def uneven_trees():
     return [tree(K, seed=2000 + K) for K in UNEVEN_DEPTHS]
+
+
+def effective_heat_capacity(w, phase, c_by_material=HEAT_CAPACITY):
+    """Leaf-weighted mean of the phases' heat capacities (MPa/K)."""
+    return float(np.sum(np.asarray(w) * np.asarray(c_by_material)[np.asarray(phase)]))
+
+
+def cyclic_stress(n_points, n_cycles=1, seed=42, steps_per_cycle=CYCLE_STEPS, period=CYCLE_PERIOD,
+                  amplitudes=CYCLE_AMPLITUDES):
+    """Stress-controlled adiabatic cyclic loading.  Returns (mask[n] uint8,
+    target[n_incr, n, 6] prescribed Mandel stresses, dt, amplitude[n],
+    direction[n] in {0, 1} = 11 or 22)."""
+    rng = np.random.default_rng(seed)
+    amp = np.asarray(amplitudes, np.float64)[rng.integers(0, len(amplitudes), n_points)]
+    direction = rng.integers(0, 2, n_points)
+    dt = period / steps_per_cycle
+    t = dt * np.arange(1, n_cycles * steps_per_cycle + 1)
+    target = np.zeros((t.size, n_points, 6))
+    target[:, np.arange(n_points), direction] = np.sin(2.0 * np.pi * t / period)[:, None] * amp
+    mask = np.full(n_points, MASK_STRESS_ADIABATIC, np.uint8)
+    return mask, target, dt, amp, direction
+
