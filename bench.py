@@ -140,9 +140,13 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def solve_kernel_name(variant, precision):
-    """Template instance the solve launches for K = 8 and thermoelastic / J2
-    leaves (see dmn_solve.cu)."""
+def solve_kernel_name(variant, precision, law=1):
+    """Template instance the solve launches for K = 8: thermoelastic / J2
+    leaves (law 1, by variant) or with Perzyna leaves (law 2, always the
+    compact form; see dmn_solve.cu)."""
+    if law == 2:
+        return ("dmn_solve_compact<double, double, 128, 1, 2>" if precision == "fp64"
+                else "dmn_solve_compact<float, dfl, 128, 3, 2>")
     if variant >= 11:
         if precision == "fp64":
             return "dmn_solve_compact<double, double, 128, 1, 1>"
@@ -478,8 +482,9 @@ def run_cyclic(args):
     time, 65,536 points, uniaxial sinusoidal stress (amplitudes 20-80 MPa,
     11 or 22 direction, 10 Hz, 20 increments per cycle, dt = 5 ms); every
     increment is an outer Newton over Algorithm 1 evaluations (mixed
-    precision, each one warm-started from the previous one's jumps) until the
-    prescribed stresses and the heat balance hold to 1e-10."""
+    precision, each one warm-started from the previous one's jumps), started
+    from the previous increment's tangent prediction, until the prescribed
+    stresses and the heat balance hold to 1e-10."""
     import torch
 
     from paper_2109_14403_gb300 import DMN, synthetic as syn
@@ -509,21 +514,34 @@ def run_cyclic(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for k in range(warm):
-        s, out, st, it, outer = d.eval_mixed(mask, tgt[k], deps, theta, dt, c_heat, s, tol_outer=tol_outer)
+    out = torch.empty((n, 57), dtype=torch.float64, device=dev)
+    for k in range(warm):  # from the second increment on: the tangent predictor
+        s, out, st, it, outer = d.eval_mixed(mask, tgt[k], deps, theta, dt, c_heat, s, tol_outer=tol_outer,
+                                             out=out, predict=k > 0)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     outers, stats = [], []
     with ClockSampler(local) as clk:
         e0.record()
         for k in range(warm, warm + steps):
+            s_in = s
             s, out, st, it, outer = d.eval_mixed(mask, tgt[k], deps, theta, dt, c_heat, s,
-                                                 tol_outer=tol_outer)
+                                                 tol_outer=tol_outer, out=out, predict=True)
             outers.append(outer)
             stats.append(st)
         e1.record()
         barrier()
     t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    # one representative solve launch (the first evaluation of the last
+    # increment, from a^n at its converged strains), timed on its own
+    stream = torch.cuda.current_stream()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    _, _, _, it1 = d.eval(deps, theta, dt, s_in)
+    r1.record(stream)
+    barrier()
+    solve_ms = r0.elapsed_time(r1)
+    passes = float(it1.float().mean().item()) + 1.0
     oc = torch.stack(outers)
     evals = int(oc.max(dim=1).values.sum().item())  # solve launches (settled points are skipped)
     failed = int(((torch.stack(stats) & 0xB) != 0).sum().item())
@@ -533,6 +551,10 @@ def run_cyclic(args):
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    flops = alu_flops_per_pass(K_DEPTH) * passes * n / (solve_ms / 1e3) / 1e12
+    bpe = algorithmic_bytes_per_eval(K_DEPTH, 13)
+    hbm = bpe * n / (solve_ms / 1e3) / 1e9
+    peak, how = measured_peaks()
     line = {"metric": "stress-controlled adiabatic Gauss-pt increments/s, K=8 (outer Newton over Algorithm 1)",
             "value": whole_job_rate(n, world, steps, t_ms), "unit": "GP-increments/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True,
@@ -548,10 +570,37 @@ def run_cyclic(args):
             "solve_launches_per_increment": evals / steps, "mean_outer": float(oc.float().mean().item()),
             "not_converged": failed,
             "temperature_change_K": {"min": float(dT.min()), "max": float(dT.max())},
+            "roofline": {"bound": "alu", "achieved": flops, "peak": 73.2, "unit": "TFLOP/s", "frac": flops / 73.2,
+                         "traffic": None, "kernel": solve_kernel_name(d.solve_variant, args.precision, law=2),
+                         "launch": "one plain evaluation of the last increment from a^n, timed alone",
+                         "launch_ms": solve_ms, "flops_per_pass": alu_flops_per_pass(K_DEPTH),
+                         "passes_per_eval": passes,
+                         "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+                                 "peak_source": how, "bytes_per_eval": bpe}},
             "clocks": clk.summary(), "gpu_launches": 2 * evals + 2 * steps}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_cyclic(n_points=256)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_cyclic(n_points=256, threads=None):
+    """FP64 oracle's outer Newton on the host cores: the first increment of the
+    cyclic workload on n_points points."""
+    import oracle
+    from paper_2109_14403_gb300 import synthetic as syn
+    threads = threads or os.cpu_count() or 1
+    w, nrm, ph = syn.tree(K_DEPTH)
+    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials_cyclic())
+    mask, tgt, dt, _, _ = syn.cyclic_stress(n_points, 1, seed=42)
+    s = tree.init_state(n_points, syn.THETA_START)
+    t0 = time.perf_counter()
+    oracle.eval_mixed(tree, mask, tgt[0], np.zeros((n_points, 6)), syn.THETA_START, dt,
+                      syn.effective_heat_capacity(w, ph), s, tol_outer=1e-10, tol=TOL, threads=threads)
+    dtm = time.perf_counter() - t0
+    return {"value": n_points / dtm, "unit": "GP-increments/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_points} points x the first increment of the cyclic path, tol {TOL}, tol_outer 1e-10"}
 
 
 def cpu_baseline_large(n_points=64, threads=None):

@@ -254,17 +254,25 @@ const char *dmn_last_error(void);
  *   d_work     NULL, or n x 3(2^K-1) floats of scratch: each evaluation after
  *              the first then starts from the previous one's jumps
  *              (dmn_eval_warm), else from a^n
+ *   flags      0 or DMN_MIXED_PREDICT: d_out holds, on entry, the outputs of
+ *              the increment that ended in d_state_in; the first evaluation
+ *              then starts from the solution of the linear model its stress
+ *              and tangents give (sigma^n + C deps + C_theta (theta -
+ *              theta^n), D ~ D_eps . deps + D_theta (theta - theta^n)) instead
+ *              of the d_deps / d_theta given
  * Outer Newton on x = (unknown strain increments, theta^{n+1} if adiabatic)
  * with the algorithmic tangents d sigma_bar/d eps_bar, d sigma_bar/d theta,
  * d D_bar/d eps_bar and d D_bar/d theta (FP64 LU with partial pivoting, one
  * system of at most 7 unknowns per point).  The stream is synchronised once
  * per evaluation to stop when every point is done.
  */
+enum { DMN_MIXED_PREDICT = 1 };
 dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_points, const uint8_t *d_mask,
                           const double *d_target, double *d_deps, double *d_theta, double dt,
                           double c_heat, int32_t max_outer, double tol_outer,
                           const double *d_state_in, double *d_state_out, double *d_out,
-                          int32_t *d_status, int32_t *d_iters, int32_t *d_outer, float *d_work);
+                          int32_t *d_status, int32_t *d_iters, int32_t *d_outer, float *d_work,
+                          int32_t flags);
 
 #ifdef __cplusplus
 }

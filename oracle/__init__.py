@@ -186,7 +186,7 @@ def split_out(out):
 
 
 def eval_mixed(tree: Tree, mask, target, deps, theta, dt, c_heat, state_in, *, max_outer=20,
-               tol_outer=1e-10, tol=1e-12, threads=None):
+               tol_outer=1e-10, tol=1e-12, threads=None, out_prev=None):
     """One increment under mixed control, by a plain outer Newton on eval_batch.
 
     Per point, bit c (0..5) of ``mask`` prescribes the Mandel stress component
@@ -196,7 +196,11 @@ def eval_mixed(tree: Tree, mask, target, deps, theta, dt, c_heat, state_in, *, m
     flux (adiabatic): c_heat (theta^{n+1} - theta^n) / dt = D_bar.  The
     unknowns are solved with the algorithmic tangents d sigma_bar / d eps_bar,
     d sigma_bar / d theta, d D_bar / d eps_bar and d D_bar / d theta (Sec. 3.3)
-    and numpy.linalg.solve.  ``deps`` and ``theta`` are starting values.
+    and numpy.linalg.solve.  ``deps`` and ``theta`` are starting values; with
+    ``out_prev`` (the outputs of the increment that ended in ``state_in``) the
+    start is instead the solution of the linearisation at that state,
+    sigma_bar ~ sigma_bar^n + C deps + C_theta (theta - theta^n) and
+    D_bar ~ D_eps . deps + D_theta (theta - theta^n).
     Returns (deps, theta, state_out, out, status, outer): status 8 = the
     conditions were not met within max_outer evaluations.
     """
@@ -210,6 +214,29 @@ def eval_mixed(tree: Tree, mask, target, deps, theta, dt, c_heat, state_in, *, m
     for c in range(6):
         strain = ((mask >> c) & 1) == 0
         x_eps[strain, c] = target[strain, c]
+    if out_prev is not None:
+        op = np.asarray(out_prev, np.float64).reshape(n, OUT_WORDS)
+        for i in range(n):
+            stress = [c for c in range(6) if (mask[i] >> c) & 1]
+            adiabatic = bool((mask[i] >> 6) & 1)
+            if not stress and not adiabatic:
+                continue
+            # linear model: unknowns u = (stress components' deps, theta - theta^n)
+            C, C_th, D_eps, D_th = op[i, 6:42].reshape(6, 6), op[i, 42:48], op[i, 49:55], op[i, 55]
+            known = np.array([0.0 if c in stress else x_eps[i, c] for c in range(6)])
+            dth = 0.0 if adiabatic else x_th[i] - theta_n[i]
+            rows, rhs = [], []
+            for c in stress:
+                rows.append([C[c, e] for e in stress] + ([C_th[c]] if adiabatic else []))
+                rhs.append(target[i, c] - op[i, c] - C[c] @ known - C_th[c] * dth)
+            if adiabatic:
+                rows.append([-D_eps[e] for e in stress] + [c_heat / dt - D_th])
+                rhs.append(D_eps @ known)
+            u = np.linalg.solve(np.array(rows), np.array(rhs))
+            for a, c in enumerate(stress):
+                x_eps[i, c] = u[a]
+            if adiabatic:
+                x_th[i] = theta_n[i] + u[-1]
     outer = np.zeros(n, np.int32)
     failed = np.zeros(n, bool)
     open_ = np.ones(n, bool)

@@ -389,7 +389,8 @@ extern "C" dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_
                                      double *d_theta, double dt, double c_heat, int32_t max_outer,
                                      double tol_outer, const double *d_state_in,
                                      double *d_state_out, double *d_out, int32_t *d_status,
-                                     int32_t *d_iters, int32_t *d_outer, float *d_work) {
+                                     int32_t *d_iters, int32_t *d_outer, float *d_work,
+                                     int32_t flags) {
   g_err[0] = 0;
   if (!h) return fail(DMN_ERR_ARG, "dmn_eval_mixed: NULL handle");
   if (n_points < 0) return fail(DMN_ERR_ARG, "dmn_eval_mixed: n_points < 0");
@@ -400,8 +401,11 @@ extern "C" dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_
   if (max_outer < 1) return fail(DMN_ERR_ARG, "dmn_eval_mixed: max_outer must be >= 1");
   if (!(tol_outer > 0.0) || !isfinite(tol_outer))
     return fail(DMN_ERR_ARG, "dmn_eval_mixed: tol_outer must be > 0");
+  if (flags & ~DMN_MIXED_PREDICT) return fail(DMN_ERR_ARG, "dmn_eval_mixed: unknown flags");
+  if (!d_state_in || !d_out) return fail(DMN_ERR_ARG, "dmn_eval_mixed: NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = mixed_prepare(s, n_points, d_mask, d_target, d_deps, d_outer);
+  cudaError_t e = mixed_prepare(s, n_points, h->SW, d_mask, d_target, d_deps, d_theta, dt, c_heat,
+                                d_state_in, d_out, (flags & DMN_MIXED_PREDICT) != 0, d_outer);
   if (e != cudaSuccess) return cuda_fail(e, "dmn_eval_mixed prepare");
   for (int it = 0; it < max_outer; ++it) {
     const float *da = (it > 0 && d_work) ? d_work : nullptr;

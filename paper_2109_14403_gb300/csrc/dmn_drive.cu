@@ -7,17 +7,6 @@
 namespace dmn {
 namespace {
 
-__global__ void k_mixed_prepare(int64_t n, const uint8_t *mask, const double *target, double *deps,
-                                int32_t *outer) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const unsigned m = mask[i];
-    for (int c = 0; c < 6; ++c)
-      if (!((m >> c) & 1u)) deps[i * 6 + c] = target[i * 6 + c];
-    outer[i] = 0;
-  }
-}
-
 // LU with partial pivoting on an m x m system (m <= 7), in place; false when
 // a pivot vanishes
 __device__ bool small_solve(double A[7][7], double b[7], int m) {
@@ -54,6 +43,88 @@ __device__ bool small_solve(double A[7][7], double b[7], int m) {
   return true;
 }
 
+// Unknowns of a point under mask m: the stress-prescribed components (bits
+// 0..5) in order, then theta when adiabatic (bit 6); returns their number.
+__device__ int unknowns(unsigned m, int unk[7]) {
+  int nu = 0;
+  for (int c = 0; c < 6; ++c)
+    if ((m >> c) & 1u) unk[nu++] = c;
+  if ((m >> 6) & 1u) unk[nu++] = 6;
+  return nu;
+}
+
+// One Newton step on the unknowns: r holds the residuals (stress rows, then
+// the heat balance c (theta - theta^n)/dt - D_bar), o the outputs whose
+// tangents form the Jacobian.  Adds the step to deps / theta; false when the
+// system is singular (nothing changed).
+__device__ bool newton_step(const int unk[7], int nu, const double *o, double c_heat, double dt,
+                            const double r[7], double *deps, double *theta) {
+  double A[7][7], b[7];
+  for (int a = 0; a < nu; ++a) {
+    for (int q = 0; q < nu; ++q) {
+      const int ra = unk[a], cq = unk[q];
+      double v;
+      if (ra < 6) v = cq < 6 ? o[6 + 6 * ra + cq] : o[42 + ra];  // d sigma / d eps, d sigma / d theta
+      else v = cq < 6 ? -o[49 + cq] : c_heat / dt - o[55];       // heat balance
+      A[a][q] = v;
+    }
+    b[a] = -r[a];
+  }
+  if (!small_solve(A, b, nu)) return false;
+  for (int a = 0; a < nu; ++a)
+    if (!isfinite(b[a])) return false;
+  for (int a = 0; a < nu; ++a) {
+    if (unk[a] < 6) deps[unk[a]] += b[a];
+    else *theta += b[a];
+  }
+  return true;
+}
+
+// Prescribed strain components and outer = 0.  With predict, the outputs in
+// out are those of the increment that ended in state_in (stress and tangents
+// at theta^n); the start is the solution of the linear model they give,
+//   sigma ~ sigma^n + C deps + C_theta (theta - theta^n),
+//   D ~ D_eps . deps + D_theta (theta - theta^n),
+// for the prescribed stresses and the heat balance.
+__global__ void k_mixed_prepare(int64_t n, int sw, const uint8_t *mask, const double *target,
+                                double *deps, double *theta, double dt, double c_heat,
+                                const double *sin, const double *out, int predict, int32_t *outer) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned m = mask[i];
+    double *e = deps + i * 6;
+    const double *tg = target + i * 6;
+    for (int c = 0; c < 6; ++c)
+      if (!((m >> c) & 1u)) e[c] = tg[c];
+    outer[i] = 0;
+    int unk[7];
+    const int nu = unknowns(m, unk);
+    if (!predict || nu == 0) continue;
+    const double *o = out + i * 57;
+    const double thn = sin[i * sw + 6];
+    const bool adiabatic = (m >> 6) & 1u;
+    double x[6], th = adiabatic ? thn : theta[i];
+    for (int c = 0; c < 6; ++c) x[c] = ((m >> c) & 1u) ? 0.0 : tg[c];
+    double r[7];
+    for (int a = 0; a < nu; ++a) {
+      const int c = unk[a];
+      double v;
+      if (c < 6) {
+        v = o[c] - tg[c] + o[42 + c] * (th - thn);
+        for (int q = 0; q < 6; ++q) v += o[6 + 6 * c + q] * x[q];
+      } else {
+        v = (c_heat / dt - o[55]) * (th - thn);
+        for (int q = 0; q < 6; ++q) v -= o[49 + q] * x[q];
+      }
+      r[a] = v;
+    }
+    if (newton_step(unk, nu, o, c_heat, dt, r, x, &th)) {
+      for (int c = 0; c < 6; ++c) e[c] = x[c];
+      theta[i] = th;
+    }
+  }
+}
+
 // Residuals of the prescribed stresses and of the heat balance at the last
 // evaluation; a point that meets them is done (outer = +evaluations), one that
 // cannot go on is given up (outer = -evaluations), any other takes one Newton
@@ -78,20 +149,19 @@ __global__ void k_mixed_update(int64_t n, int sw, int n3, const uint8_t *mask, c
     }
     double smax = 1.0;
     for (int c = 0; c < 6; ++c) smax = fmax(smax, fabs(o[c]));
-    int unk[7], nu = 0;
+    int unk[7];
+    const int nu = unknowns(m, unk);
     double r[7];
     bool ok = true;
-    for (int c = 0; c < 6; ++c)
-      if ((m >> c) & 1u) {
-        r[nu] = o[c] - target[i * 6 + c];
-        if (!(fabs(r[nu]) <= tol * smax)) ok = false;
-        unk[nu++] = c;
+    for (int a = 0; a < nu; ++a) {
+      const int c = unk[a];
+      if (c < 6) {
+        r[a] = o[c] - target[i * 6 + c];
+        if (!(fabs(r[a]) <= tol * smax)) ok = false;
+      } else {
+        r[a] = c_heat * (theta[i] - sin[i * sw + 6]) / dt - o[48];
+        if (!(fabs(r[a]) <= tol * c_heat / dt)) ok = false;
       }
-    const double thn = sin[i * sw + 6];
-    if ((m >> 6) & 1u) {
-      r[nu] = c_heat * (theta[i] - thn) / dt - o[48];
-      if (!(fabs(r[nu]) <= tol * c_heat / dt)) ok = false;
-      unk[nu++] = 6;
     }
     if (ok) {
       outer[i] = it + 1;
@@ -101,24 +171,9 @@ __global__ void k_mixed_update(int64_t n, int sw, int n3, const uint8_t *mask, c
       outer[i] = -(it + 1);
       continue;
     }
-    double A[7][7], b[7];
-    for (int a = 0; a < nu; ++a) {
-      for (int q = 0; q < nu; ++q) {
-        const int ra = unk[a], cq = unk[q];
-        double v;
-        if (ra < 6) v = cq < 6 ? o[6 + 6 * ra + cq] : o[42 + ra];      // d sigma / d eps, d sigma / d theta
-        else v = cq < 6 ? -o[49 + cq] : c_heat / dt - o[55];           // heat balance
-        A[a][q] = v;
-      }
-      b[a] = -r[a];
-    }
-    if (!small_solve(A, b, nu)) {
+    if (!newton_step(unk, nu, o, c_heat, dt, r, deps + i * 6, theta + i)) {
       outer[i] = -(it + 1);
       continue;
-    }
-    for (int a = 0; a < nu; ++a) {
-      if (unk[a] < 6) deps[i * 6 + unk[a]] += b[a];
-      else theta[i] += b[a];
     }
     atomicAdd(open, 1ull);
   }
@@ -141,9 +196,12 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t mixed_prepare(cudaStream_t s, int64_t n, const uint8_t *mask, const double *target,
-                          double *deps, int32_t *outer) {
-  k_mixed_prepare<<<blocks_for(n), 128, 0, s>>>(n, mask, target, deps, outer);
+cudaError_t mixed_prepare(cudaStream_t s, int64_t n, int sw, const uint8_t *mask,
+                          const double *target, double *deps, double *theta, double dt,
+                          double c_heat, const double *sin, const double *out, bool predict,
+                          int32_t *outer) {
+  k_mixed_prepare<<<blocks_for(n), 128, 0, s>>>(n, sw, mask, target, deps, theta, dt, c_heat, sin,
+                                                out, predict ? 1 : 0, outer);
   return cudaGetLastError();
 }
 

@@ -25,11 +25,13 @@ int material_z_words(int kind);
 cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
                           int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);
-// dmn_eval_mixed (dmn_drive.cu): prescribed strain components and outer = 0;
-// one outer Newton update after an evaluation; the status bit of the points
-// given up
-cudaError_t mixed_prepare(cudaStream_t s, int64_t n, const uint8_t *mask, const double *target,
-                          double *deps, int32_t *outer);
+// dmn_eval_mixed (dmn_drive.cu): prescribed strain components, outer = 0 and
+// optionally the tangent predictor; one outer Newton update after an
+// evaluation; the status bit of the points given up
+cudaError_t mixed_prepare(cudaStream_t s, int64_t n, int sw, const uint8_t *mask,
+                          const double *target, double *deps, double *theta, double dt,
+                          double c_heat, const double *sin, const double *out, bool predict,
+                          int32_t *outer);
 cudaError_t mixed_update(cudaStream_t s, int64_t n, int sw, int n3, const uint8_t *mask,
                          const double *target, double *deps, double *theta, double dt, double c_heat,
                          double tol, const double *sin, const double *sout, const double *out,

@@ -17,6 +17,7 @@ DMN_OK, DMN_ERR_ARG = 0, 1
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE, PT_FALLBACK_USED = 0, 1, 2, 4
 PT_OUTER_NOT_CONVERGED = 8
 MIXED_ADIABATIC = 1 << 6  # dmn_eval_mixed mask bit: theta from the heat balance
+MIXED_PREDICT = 1  # dmn_eval_mixed flag: start from the previous outputs' linear model
 PREC_FP64, PREC_MIXED = 0, 1
 OUT_WORDS = 57
 
@@ -69,7 +70,7 @@ SIGNATURES = {
     "dmn_gemm_bf16_tn": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
     "dmn_eval_warm": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P]),
     "dmn_eval_mixed": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _D, _D, _I32, _D, _P, _P, _P, _P, _P,
-                              _P, _P]),
+                              _P, _P, _I32]),
 }
 
 
@@ -213,15 +214,20 @@ class DMN:
         return state_out, out, status, iters
 
     def eval_mixed(self, mask, target, deps, theta, dt, c_heat, state_in, *, max_outer=10,
-                   tol_outer=1e-10, warm=True, stream=None):
+                   tol_outer=1e-10, warm=True, out=None, predict=False, stream=None):
         """``dmn_eval_mixed``: prescribed stresses (mask bits 0..5) and adiabatic
-        temperature (bit 6).  ``deps`` and ``theta`` are updated in place.
-        Returns (state_out, out, status, iters, outer)."""
+        temperature (bit 6).  ``deps`` and ``theta`` are updated in place.  With
+        ``predict``, ``out`` must hold the outputs of the increment that ended
+        in ``state_in``; it is overwritten.  Returns (state_out, out, status,
+        iters, outer)."""
         import torch
         n = deps.shape[0]
         dev = deps.device
         state_out = torch.empty_like(state_in)
-        out = torch.empty((n, OUT_WORDS), dtype=torch.float64, device=dev)
+        if predict and out is None:
+            raise ValueError("predict needs the previous increment's out")
+        if out is None:
+            out = torch.empty((n, OUT_WORDS), dtype=torch.float64, device=dev)
         status = torch.empty(n, dtype=torch.int32, device=dev)
         iters = torch.empty(n, dtype=torch.int32, device=dev)
         outer = torch.empty(n, dtype=torch.int32, device=dev)
@@ -239,7 +245,8 @@ class DMN:
                                    _dev(iters, torch.int32, (n,), "iters"),
                                    _dev(outer, torch.int32, (n,), "outer"),
                                    None if work is None else
-                                   _dev(work, torch.float32, None, "work")), "dmn_eval_mixed")
+                                   _dev(work, torch.float32, None, "work"),
+                                   MIXED_PREDICT if predict else 0), "dmn_eval_mixed")
         return state_out, out, status, iters, outer
 
     def eval_warm(self, deps, theta, dt, state_in, da, state_out=None, out=None, status=None,

@@ -158,10 +158,12 @@ def test_composite_parity(K, prec):
     d.close()
 
 
+@pytest.mark.parametrize("predict", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_cyclic_self_heating_path(prec):
+def test_cyclic_self_heating_path(prec, predict):
     """One load cycle (20 increments) of the stress-controlled adiabatic
-    cyclic workload, GPU and oracle each on their own trajectory."""
+    cyclic workload, GPU and oracle each on their own trajectory (with the
+    tangent predictor on both sides, or on neither)."""
     dev = _dev()
     K = 5
     d, tree, c = make(K, syn.materials_cyclic(), prec)
@@ -172,19 +174,27 @@ def test_cyclic_self_heating_path(prec):
     deps_g = np.zeros((n, 6))
     th_g = np.full(n, TH0)
     deps_o, th_o = deps_g.copy(), th_g.copy()
+    out, out_o = None, None
+    evals = 0
     for k in range(target.shape[0]):
         thn_o = so[:, 6].copy()
-        de, th, s, out, st, outer = gpu_step(d, mask, target[k], deps_g, th_g, dt, c, s)
+        pred = predict and out is not None
+        de, th, s, out, st, outer = gpu_step(d, mask, target[k], deps_g, th_g, dt, c, s,
+                                             out=out if pred else None, predict=pred)
         deps_g, th_g = de.cpu().numpy(), th.cpu().numpy()
         assert ((st.cpu().numpy() & ~4) == 0).all()
+        evals += int(outer.sum().item())
         deps_o, th_o, so, out_o, st_o, _ = oracle.eval_mixed(tree, mask, target[k], deps_o, th_o, dt,
-                                                             c, so, tol_outer=TOL_OUTER)
+                                                             c, so, tol_outer=TOL_OUTER,
+                                                             out_prev=out_o if pred else None)
         assert (st_o == 0).all()
         check_against(prec, deps_g, th_g, out.cpu().numpy(), deps_o, th_o, out_o, thn_o, mask,
                       target[k], scale=20.0)
         eb = s[:, :6].cpu().numpy()
         emax = np.maximum(np.abs(so[:, :6]).max(axis=1), 1e-6)
         assert (np.abs(eb - so[:, :6]).max(axis=1) <= 20 * RTOL[prec] * emax).all()
+    if predict:  # the predictor leaves about 2.3 evaluations per increment
+        assert evals <= 2.6 * n * target.shape[0]
     # self-heating after one cycle grows with the amplitude
     rise = th_g - TH0
     for a_lo, a_hi in zip(syn.CYCLE_AMPLITUDES[:-1], syn.CYCLE_AMPLITUDES[1:]):
@@ -220,6 +230,34 @@ def test_cyclic_full_batch_sampled(prec):
         check_against(prec, de[idx_d].cpu().numpy(), th[idx_d].cpu().numpy(),
                       out[idx_d].cpu().numpy(), deps_o, th_o, out_o, thn_o, mask[idx],
                       target[k][idx], scale=3.0)
+    d.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_predictor_is_exact_for_linear_phases(prec):
+    """Linear thermoelastic phases, isothermal mixed control: the tangent
+    predictor's start already meets the conditions (one evaluation)."""
+    dev = _dev()
+    mats = [[0, 72000.0, 0.22, 5e-6, TH0, 0, 0, 0], [0, 2500.0, 0.38, 8e-5, TH0, 0, 0, 0]]
+    d, tree, c = make(6, mats, prec)
+    m = 16
+    rng = np.random.default_rng(11)
+    s0 = d.init_state(torch.full((m,), TH0, dtype=torch.float64, device=dev))
+    s1, o1, st1, _ = d.eval(_t(rng.normal(0, 1e-3, (m, 6))), _t(np.full(m, 300.0)), 1.0, s0)
+    mask = MASKS[np.arange(m) % 4]  # 0x7F, 0x3F, 0x06, 0x46
+    mask = np.where(mask & ADIABATIC, mask & ALL_STRESS, mask).astype(np.uint8)
+    target = rng.normal(0, 30.0, (m, 6))
+    strain = ((mask[:, None] >> np.arange(6)) & 1) == 0
+    target[strain] = rng.normal(0, 1e-3, strain.sum())
+    tol = 1e-9 if prec == "fp64" else 1e-7
+    so, out, st, it, outer = d.eval_mixed(_t(mask, torch.uint8), _t(target), _t(np.zeros((m, 6))),
+                                          _t(np.full(m, 310.0)), 1.0, 2.0, s1, out=o1.clone(),
+                                          predict=True, tol_outer=tol)
+    # FP64 tangents make the linear model exact to rounding; the mixed path's
+    # come from the FP32 condensation (relative error up to ~1e-5), which
+    # leaves one more evaluation
+    assert (st.cpu().numpy() == 0).all()
+    assert (outer.cpu().numpy() == 1).all() if prec == "fp64" else (outer.cpu().numpy() <= 2).all()
     d.close()
 
 

@@ -16,7 +16,10 @@ carries the same isotropic material and the DMN reduces to that material.
     solved by bracketing (scipy.optimize.brentq);
   * an all-strain mask reproduces eval_batch bit for bit;
   * a composite tree: the returned state meets every prescribed stress and the
-    heat balance when evaluated again with eval_batch.
+    heat balance when evaluated again with eval_batch;
+  * the tangent predictor: exact (one evaluation) for a linear thermoelastic
+    composite under isothermal mixed control; on the cyclic path the same
+    solution with fewer evaluations.
 """
 import numpy as np
 import pytest
@@ -148,3 +151,46 @@ def test_not_converged_flag():
     de, th, so, out, st, outer = oracle.eval_mixed(t, [ALL_STRESS], uniaxial(80.0), np.zeros((1, 6)),
                                                    TH0, 1.0, 1.9, t.init_state(1, TH0), max_outer=2)
     assert st[0] == 8 and outer[0] == 2
+
+
+def test_predictor_is_exact_for_linear_phases():
+    K = 4
+    w, n, ph = syn.tree(K)
+    t = oracle.Tree(K, w, n, ph, [[0, 72000.0, 0.22, 5e-6, TH0, 0, 0, 0],
+                                  [0, 2500.0, 0.38, 8e-5, TH0, 0, 0, 0]])
+    m = 4
+    s0 = t.init_state(m, TH0)
+    # previous increment: a strain-controlled step to a nonzero state
+    rng = np.random.default_rng(11)
+    d1 = rng.normal(0, 1e-3, (m, 6))
+    s1, o1, st1, _ = oracle.eval_batch(t, d1, 300.0, 1.0, s0)
+    mask = np.array([ALL_STRESS, 0x06, 0x3E, 0x01], np.uint8)
+    target = rng.normal(0, 30.0, (m, 6))
+    strain = ((mask[:, None] >> np.arange(6)) & 1) == 0
+    target[strain] = rng.normal(0, 1e-3, strain.sum())
+    de, th, so, out, st, outer = oracle.eval_mixed(t, mask, target, np.zeros((m, 6)), 310.0, 1.0,
+                                                   2.0, s1, out_prev=o1, tol_outer=1e-9)
+    assert (st == 0).all() and (outer == 1).all()
+
+
+def test_predictor_saves_evaluations_on_the_cyclic_path():
+    K = 4
+    w, n, ph = syn.tree(K)
+    t = oracle.Tree(K, w, n, ph, syn.materials_cyclic())
+    c = syn.effective_heat_capacity(w, ph)
+    mask, target, dt, amp, direction = syn.cyclic_stress(6, 1, seed=5)
+    runs = []
+    for predict in (False, True):
+        s = t.init_state(mask.size, TH0)
+        de, th, out = np.zeros((mask.size, 6)), np.full(mask.size, TH0), None
+        total = 0
+        for k in range(target.shape[0]):
+            de, th, s, out, st, outer = oracle.eval_mixed(
+                t, mask, target[k], de, th, dt, c, s, tol_outer=1e-11,
+                out_prev=out if predict else None)
+            assert (st == 0).all()
+            total += outer.sum()
+        runs.append((total, de, th))
+    assert runs[1][0] < runs[0][0]
+    np.testing.assert_allclose(runs[1][1], runs[0][1], rtol=0, atol=1e-9 * np.abs(runs[0][1]).max())
+    np.testing.assert_allclose(runs[1][2], runs[0][2], rtol=0, atol=1e-9)
