@@ -23,12 +23,16 @@ _lock = threading.Lock()
 
 OUT_WORDS = 57
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE = 0, 1, 2
-MAT_WORDS = 12  # kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT 0
-Z_WORDS = {0: 0, 1: 7, 2: 13}  # internal variables per leaf, by material kind
+# material row: kinds 0-2: kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT 0 (rows of 8
+# or 12 are padded); kind 3 (PA66): kind E_inf nu alpha0 theta0 sy0 k n m eta0 beta1 beta2
+# theta_ref C1 C2 0, E_1..E_12, tau_1..tau_12
+MAT_WORDS = 40
+Z_WORDS = {0: 0, 1: 7, 2: 13, 3: 79}  # internal variables per leaf, by material kind
+Z_MAX = 79
 
 
 def mat_rows(mats):
-    """Material table as n x 12 rows; rows of 8 (kinds 0 and 1) are padded with 0."""
+    """Material table as n x 40 rows; shorter rows (kinds 0-2) are padded with 0."""
     m = np.atleast_2d(np.asarray(mats, np.float64))
     if m.shape[1] < MAT_WORDS:
         m = np.hstack([m, np.zeros((m.shape[0], MAT_WORDS - m.shape[1]))])
@@ -80,8 +84,7 @@ def _c(a, dtype):
 class Tree:
     """DMN description: depth K, leaf weights (2^K), normals ((2^K-1) x 3 in the
     paper's order: bottom level first, root last), phase map (2^K) and a material
-    table (n_mats x 12: kind, E, nu, alpha, theta0, sy0, dsy_dT, H, m, t_visc,
-    dE_dT, 0; rows of 8 are padded)."""
+    table (n_mats x 40 rows as in ``mat_rows``)."""
 
     def __init__(self, K, w, normals, phase, mats):
         self.K = int(K)
@@ -154,11 +157,11 @@ def leaf(mat_row, eps, theta, zn=None, trn=0.0, dt=1.0):
     """One phase-law evaluation.  Returns a dict with sig, C, tau, D, d, g, diss, znew."""
     m = mat_rows(mat_row).reshape(MAT_WORDS)
     e = _c(eps, np.float64).reshape(6)
-    z = np.zeros(13, np.float64)
+    z = np.zeros(Z_MAX, np.float64)
     if zn is not None:
         zn = np.asarray(zn, np.float64).ravel()
         z[:zn.size] = zn
-    o = np.zeros(70, np.float64)
+    o = np.zeros(57 + Z_MAX, np.float64)
     _load().oracle_leaf(_ptr(m), _ptr(e), float(theta), _ptr(z), float(trn), float(dt), _ptr(o))
     return {"sig": o[0:6].copy(), "C": o[6:42].reshape(6, 6).copy(), "tau": o[42:48].copy(),
             "D": float(o[48]), "d": o[49:55].copy(), "g": float(o[55]), "diss": float(o[56]),

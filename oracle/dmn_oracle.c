@@ -67,6 +67,25 @@
  *           + sigma_Y dp] / dt,   Diss = sigma_Y dp / dt,
  *    with de = eps - eps^n the leaf's strain increment; the leaf keeps its
  *    strain in its internal variables: z = (eps_p (6), p, eps (6)).
+ *  - kind 3, the PA66 matrix of Section 4 (after Krairi et al.): eq. (PA66 psi)
+ *    with a long-term branch C_inf and N <= 12 Maxwell branches C_i (constant
+ *    nu), thermorheologically simple viscosities V_i = a_theta (3 K_i tau_K,i P1
+ *    + 2 G_i tau_G,i P2), tau_K,i = tau_i E_i / K_i, tau_G,i = tau_i E_i / G_i,
+ *    WLF shift log10 a_theta = -C1 (theta - theta_ref) / (C2 + theta - theta_ref),
+ *    J2 viscoplasticity with p_dot = (sigma_Y / eta) <(q - sigma_Y - H) / sigma_Y>_+^m,
+ *    sigma_Y = Gamma(theta, beta1) sigma_Y0, H = Gamma(theta, beta1) k p^n,
+ *    eta = Gamma(theta, beta2) eta0, Gamma = exp(-beta (theta - theta_ref)), and the
+ *    coupling term D and dissipation of the PA66 model.  Every evolution equation
+ *    is integrated by implicit Euler; for a trial dp the viscoplastic strain moves
+ *    along the trial deviator (the flow direction of the J2 law), every Maxwell
+ *    strain is updated in closed form, the stress is summed over the branches,
+ *    and dp is found by bisection of dp = dt p_dot(dp).  Rates in D are
+ *    (x^{n+1} - x^n) / dt.  The derivatives d sigma/d eps, d sigma/d theta,
+ *    dD/d eps and dD/d theta are taken by the complex-step method (Squire and
+ *    Trapp 1998): the law is evaluated in complex arithmetic with one input
+ *    perturbed by i h, and the derivative is Im(out) / h, exact to rounding;
+ *    dp is carried into the complex plane by Newton steps on the same equation.
+ *    z = (eps_vp (6), p, eps_v,1 (6), ..., eps_v,12 (6)): 79 words.
  *
  * Symmetric tensors are Mandel 6-vectors (11, 22, 33, sqrt2*23, sqrt2*13,
  * sqrt2*12); fourth-order tensors are 6x6 matrices acting on them.
@@ -82,6 +101,7 @@
  * phases, free thermal expansion, Hill-Mandel, finite-difference tangents,
  * dense-versus-sparse agreement); the paper prints no worked example.
  */
+#include <complex.h>
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -95,17 +115,25 @@
 /* tree                                                                 */
 /* ------------------------------------------------------------------ */
 
-#define OR_MATW 12 /* material row: kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT 0 */
-#define OR_ZMAX 13 /* internal variables per leaf, at most */
+/* material row, 40 words:
+   kinds 0-2: kind E nu alpha theta0 sy0 dsy_dT H m t_visc dE_dT, then 0
+   kind 3:    kind E_inf nu alpha0 theta0 sy0 k n m eta0 beta1 beta2 theta_ref C1 C2 0,
+              E_1..E_12, tau_1..tau_12 */
+#define OR_MATW 40
+#define OR_NMAX 12 /* Maxwell branches of kind 3 */
+#define OR_ZMAX 79 /* internal variables per leaf, at most */
 
 typedef struct {
   int kind;
   double E, nu, alpha, theta0, sy0, dsy_dT, H;
   double m_rate, t_visc, dE_dT; /* kind 2 only */
+  double row[OR_MATW];          /* the row as given */
 } omat;
 
 /* words of internal variables of a leaf of this kind */
-static int z_words(int kind) { return kind == 1 ? 7 : (kind == 2 ? 13 : 0); }
+static int z_words(int kind) {
+  return kind == 1 ? 7 : (kind == 2 ? 13 : (kind == 3 ? 7 + 6 * OR_NMAX : 0));
+}
 
 typedef struct {
   int K, nleaf, nnode;
@@ -207,16 +235,225 @@ typedef struct {
   double d[6];      /* dD/deps                                */
   double g;         /* dD/dtheta (explicit)                   */
   double diss;      /* dissipation                            */
-  double znew[OR_ZMAX]; /* eps_p (6), p [, eps (6) for kind 2] */
+  double znew[OR_ZMAX]; /* eps_p (6), p [, eps (6) for kind 2; Maxwell strains for kind 3] */
 } oleaf;
 
 static const double M1[6] = {1, 1, 1, 0, 0, 0};
+
+/* ------------------------------------------------------------ kind 3: PA66 */
+
+typedef double complex ocx;
+
+typedef struct {
+  double Einf, nu, alpha, theta0, sy0, k, n, m, eta0, beta1, beta2, theta_ref, C1, C2;
+  double Ei[OR_NMAX], taui[OR_NMAX];
+} opa66;
+
+static void pa66_params(const double *r, opa66 *P) {
+  P->Einf = r[1]; P->nu = r[2]; P->alpha = r[3]; P->theta0 = r[4]; P->sy0 = r[5];
+  P->k = r[6]; P->n = r[7]; P->m = r[8]; P->eta0 = r[9]; P->beta1 = r[10]; P->beta2 = r[11];
+  P->theta_ref = r[12]; P->C1 = r[13]; P->C2 = r[14];
+  for (int i = 0; i < OR_NMAX; ++i) { P->Ei[i] = r[16 + i]; P->taui[i] = r[28 + i]; }
+}
+
+/* everything the PA66 law returns for one (complex) input */
+typedef struct {
+  ocx sig[6], D, diss, znew[OR_ZMAX];
+} opa66_out;
+
+/* mean and deviator of a Mandel vector: x = mean m + dev */
+static void split(const ocx x[6], ocx *mean, ocx dev[6]) {
+  *mean = (x[0] + x[1] + x[2]) / 3.0;
+  for (int c = 0; c < 6; ++c) dev[c] = x[c] - M1[c] * (*mean);
+}
+
+/* The law at strain eps and temperature theta with the viscoplastic increment
+   dp given: eps_vp = eps_vp^n + dp (3/2) N_tr / |N_tr| sqrt(2/3)... i.e. along
+   the unit trial deviator ntr (d eps_vp = sqrt(3/2) dp ntr); the Maxwell strains
+   follow by implicit Euler.  Returns q = sqrt(3/2) |dev sigma| in *q and fills
+   out (stress, D, dissipation, new internal variables). */
+static void pa66_at(const opa66 *P, const ocx eps[6], ocx theta, const double *zn, double trn,
+                    double dt, ocx dp, const ocx ntr[6], ocx *q, opa66_out *o) {
+  const ocx x = theta - P->theta_ref;
+  const ocx a = cpow(10.0, -P->C1 * x / (P->C2 + x));       /* WLF shift a_theta */
+  const ocx G1 = cexp(-P->beta1 * x), G2 = cexp(-P->beta2 * x);
+  const ocx sy = G1 * P->sy0;
+  const double Kinf = P->Einf / (3.0 * (1.0 - 2.0 * P->nu)), Ginf = P->Einf / (2.0 * (1.0 + P->nu));
+  ocx evp[6], es[6];
+  for (int c = 0; c < 6; ++c) {
+    evp[c] = zn[c] + sqrt(1.5) * dp * ntr[c];
+    es[c] = eps[c] - evp[c] - M1[c] * P->alpha * (theta - P->theta0); /* eps - eps_vp - alpha dtheta I */
+  }
+  ocx es_m, es_d[6];
+  split(es, &es_m, es_d);
+  /* long-term branch */
+  ocx sig[6];
+  for (int c = 0; c < 6; ++c) sig[c] = 3.0 * Kinf * es_m * M1[c] + 2.0 * Ginf * es_d[c];
+  /* Maxwell branches: d eps_v / dt = F_i sigma_v,i, F_i the pseudo-inverse of V_i */
+  ocx trdev_sum = 0.0; /* sum_i 3 K_i alpha tr(d eps - d eps_v,i) */
+  ocx visc = 0.0;      /* sum_i sigma_v,i : d eps_v,i */
+  const double treps_n = trn;
+  const ocx treps = eps[0] + eps[1] + eps[2];
+  for (int i = 0; i < OR_NMAX; ++i) {
+    const double *vn = zn + 7 + 6 * i;
+    ocx *vnew = o->znew + 7 + 6 * i;
+    if (!(P->Ei[i] > 0.0)) {
+      for (int c = 0; c < 6; ++c) vnew[c] = vn[c];
+      continue;
+    }
+    const double Ki = P->Ei[i] / (3.0 * (1.0 - 2.0 * P->nu)), Gi = P->Ei[i] / (2.0 * (1.0 + P->nu));
+    const double tauK = P->taui[i] * P->Ei[i] / Ki, tauG = P->taui[i] * P->Ei[i] / Gi;
+    /* V_i = a (3 K_i tauK P1 + 2 G_i tauG P2): F_i = P1 / (3 a K_i tauK) + P2 / (2 a G_i tauG);
+       F_i C_i = P1 / (a tauK) + P2 / (a tauG) */
+    const ocx lv = 1.0 / (a * tauK), ld = 1.0 / (a * tauG);
+    double vnd[6];
+    ocx vn_m;
+    {
+      ocx t6[6], td[6];
+      for (int c = 0; c < 6; ++c) t6[c] = vn[c];
+      split(t6, &vn_m, td);
+      for (int c = 0; c < 6; ++c) vnd[c] = creal(td[c]);
+    }
+    /* implicit Euler: v^{n+1} = v^n + dt lambda (e* - v^{n+1}) per projector */
+    const ocx vm = (vn_m + dt * lv * es_m) / (1.0 + dt * lv);
+    ocx vd[6];
+    for (int c = 0; c < 6; ++c) vd[c] = (vnd[c] + dt * ld * es_d[c]) / (1.0 + dt * ld);
+    ocx sv[6], dv[6];
+    for (int c = 0; c < 6; ++c) {
+      vnew[c] = vm * M1[c] + vd[c];
+      dv[c] = vnew[c] - vn[c];
+      sv[c] = 3.0 * Ki * (es_m - vm) * M1[c] + 2.0 * Gi * (es_d[c] - vd[c]); /* sigma_v,i */
+      sig[c] += sv[c];
+    }
+    const ocx trdv = dv[0] + dv[1] + dv[2];
+    trdev_sum += 3.0 * Ki * P->alpha * ((treps - treps_n) - trdv);
+    for (int c = 0; c < 6; ++c) visc += sv[c] * dv[c];
+  }
+  ocx sm, sd[6];
+  split(sig, &sm, sd);
+  ocx s2 = 0.0;
+  for (int c = 0; c < 6; ++c) s2 += sd[c] * sd[c];
+  *q = csqrt(1.5 * s2);
+  const ocx p1 = zn[6] + dp;
+  const ocx H = creal(p1) > 0.0 ? G1 * P->k * cpow(p1, P->n) : 0.0;
+  const ocx dH_dth = -P->beta1 * H;
+  for (int c = 0; c < 6; ++c) { o->sig[c] = sig[c]; o->znew[c] = evp[c]; }
+  o->znew[6] = p1;
+  (void)G2;
+  o->D = (-theta * (3.0 * Kinf * P->alpha * (treps - treps_n) + trdev_sum) + theta * dH_dth * dp +
+          sy * dp + visc) / dt;
+  o->diss = (sy * dp + visc) / dt;
+}
+
+/* residual of the viscoplastic step: g(dp) = dp - dt p_dot(q(dp), p^n + dp) */
+static ocx pa66_g(const opa66 *P, const ocx eps[6], ocx theta, const double *zn, double trn,
+                  double dt, ocx dp, const ocx ntr[6], opa66_out *o) {
+  ocx q;
+  pa66_at(P, eps, theta, zn, trn, dt, dp, ntr, &q, o);
+  const ocx x = theta - P->theta_ref;
+  const ocx G1 = cexp(-P->beta1 * x), G2 = cexp(-P->beta2 * x);
+  const ocx sy = G1 * P->sy0, eta = G2 * P->eta0;
+  const ocx p1 = zn[6] + dp;
+  const ocx H = creal(p1) > 0.0 ? G1 * P->k * cpow(p1, P->n) : 0.0;
+  ocx phi = (q - sy - H) / sy;
+  if (creal(phi) < 0.0) phi = 0.0;
+  return dp - dt * (sy / eta) * cpow(phi, P->m);
+}
+
+/* the PA66 law for one complex input: trial at dp = 0, then the return */
+static void pa66_eval(const opa66 *P, const ocx eps[6], ocx theta, const double *zn, double trn,
+                      double dt, int *plastic_io, opa66_out *o) {
+  const ocx zero6[6] = {0, 0, 0, 0, 0, 0};
+  ocx q;
+  pa66_at(P, eps, theta, zn, trn, dt, 0.0, zero6, &q, o);
+  const ocx x = theta - P->theta_ref;
+  const ocx G1 = cexp(-P->beta1 * x);
+  const ocx sy = G1 * P->sy0;
+  const ocx Hn = zn[6] > 0.0 ? G1 * P->k * cpow(zn[6], P->n) : 0.0;
+  /* the decision elastic / viscoplastic is taken once, on the real input */
+  if (*plastic_io < 0) *plastic_io = creal(q - sy - Hn) > 0.0;
+  if (!*plastic_io) return;
+  /* unit trial deviator */
+  ocx sm, sd[6], ntr[6];
+  split(o->sig, &sm, sd);
+  ocx s2 = 0.0;
+  for (int c = 0; c < 6; ++c) s2 += sd[c] * sd[c];
+  const ocx sn = csqrt(s2);
+  for (int c = 0; c < 6; ++c) ntr[c] = sd[c] / sn;
+  /* bracket and bisect on the real parts: g is increasing in dp */
+  double lo = 0.0, hi = 1e-8;
+  opa66_out tmp;
+  const ocx epsr[6] = {creal(eps[0]), creal(eps[1]), creal(eps[2]), creal(eps[3]), creal(eps[4]),
+                       creal(eps[5])};
+  const ocx ntrr[6] = {creal(ntr[0]), creal(ntr[1]), creal(ntr[2]), creal(ntr[3]), creal(ntr[4]),
+                       creal(ntr[5])};
+  const ocx thr = creal(theta);
+  for (int it = 0; it < 200 && creal(pa66_g(P, epsr, thr, zn, trn, dt, hi, ntrr, &tmp)) <= 0.0; ++it)
+    hi *= 2.0;
+  for (int it = 0; it < 300 && hi - lo > 1e-17 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (creal(pa66_g(P, epsr, thr, zn, trn, dt, mid, ntrr, &tmp)) > 0.0) hi = mid;
+    else lo = mid;
+  }
+  ocx dp = 0.5 * (lo + hi);
+  /* Newton steps in complex arithmetic carry d dp / d input (derivative of g
+     by a real central difference; the steps converge the imaginary part) */
+  const double h = 1e-7 * (creal(dp) > 0.0 ? creal(dp) : 1e-12);
+  const double gp = (creal(pa66_g(P, epsr, thr, zn, trn, dt, creal(dp) + h, ntrr, &tmp)) -
+                     creal(pa66_g(P, epsr, thr, zn, trn, dt, creal(dp) - h, ntrr, &tmp))) / (2.0 * h);
+  for (int it = 0; it < 4; ++it) dp -= pa66_g(P, eps, theta, zn, trn, dt, dp, ntr, o) / gp;
+  pa66_g(P, eps, theta, zn, trn, dt, dp, ntr, o);
+}
+
+static void pa66_leaf(const double *row, const double eps[6], double theta, const double *zn,
+                      double trn, double dt, oleaf *L) {
+  opa66 P;
+  pa66_params(row, &P);
+  const double h = 1e-30;
+  opa66_out o;
+  ocx e[6];
+  for (int c = 0; c < 6; ++c) e[c] = eps[c];
+  int plastic = -1;
+  pa66_eval(&P, e, theta, zn, trn, dt, &plastic, &o);
+  for (int c = 0; c < 6; ++c) L->sig[c] = creal(o.sig[c]);
+  L->D = creal(o.D);
+  L->diss = creal(o.diss);
+  for (int c = 0; c < OR_ZMAX; ++c) L->znew[c] = creal(o.znew[c]);
+  /* complex-step derivatives in the six strain directions and in theta */
+  for (int j = 0; j < 7; ++j) {
+    for (int c = 0; c < 6; ++c) e[c] = eps[c] + (c == j ? I * h : 0.0);
+    const ocx th = theta + (j == 6 ? I * h : 0.0);
+    opa66_out od;
+    pa66_eval(&P, e, th, zn, trn, dt, &plastic, &od);
+    for (int c = 0; c < 6; ++c) {
+      if (j < 6) L->C[c][j] = cimag(od.sig[c]) / h;
+      else L->tau[c] = cimag(od.sig[c]) / h;
+    }
+    if (j < 6) L->d[j] = cimag(od.D) / h;
+    else L->g = cimag(od.D) / h;
+  }
+}
 
 /* eps: Mandel strain at t^{n+1}; trn: trace of the leaf strain at t^n (kinds 0
    and 1; kind 2 takes its strain at t^n from zn); zn: internal variables of
    the leaf at t^n (kinds 1 and 2) */
 void oracle_leaf(const double *matp, const double eps[6], double theta, const double *zn,
                  double trn, double dt, double *outp) {
+  if ((int)matp[0] == 3) {
+    oleaf L3;
+    memset(&L3, 0, sizeof(L3));
+    pa66_leaf(matp, eps, theta, zn, trn, dt, &L3);
+    double *o = outp;
+    memcpy(o, L3.sig, 6 * sizeof(double)); o += 6;
+    memcpy(o, L3.C, 36 * sizeof(double)); o += 36;
+    memcpy(o, L3.tau, 6 * sizeof(double)); o += 6;
+    *o++ = L3.D;
+    memcpy(o, L3.d, 6 * sizeof(double)); o += 6;
+    *o++ = L3.g;
+    *o++ = L3.diss;
+    memcpy(o, L3.znew, OR_ZMAX * sizeof(double));
+    return;
+  }
   omat m;
   m.kind = (int)matp[0];
   m.E = matp[1]; m.nu = matp[2]; m.alpha = matp[3]; m.theta0 = matp[4];
@@ -355,7 +592,7 @@ void oracle_leaf(const double *matp, const double eps[6], double theta, const do
       L.g += ((sf + theta * dsf) * sv + theta * sf * (tv - q * ddp_dth)) / dt;
     }
   }
-  /* pack: sig 6, C 36, tau 6, D, d 6, g, diss, znew 13 = 70 */
+  /* pack: sig 6, C 36, tau 6, D, d 6, g, diss, znew 79 = 136 */
   double *o = outp;
   memcpy(o, L.sig, 6 * sizeof(double)); o += 6;
   memcpy(o, L.C, 36 * sizeof(double)); o += 36;
@@ -369,10 +606,8 @@ void oracle_leaf(const double *matp, const double eps[6], double theta, const do
 
 static void leaf_eval(const omat *m, const double eps[6], double theta, const double *zn,
                       double trn, double dt, oleaf *L) {
-  double mp[OR_MATW] = {(double)m->kind, m->E,  m->nu,     m->alpha,  m->theta0, m->sy0,
-                        m->dsy_dT,       m->H,  m->m_rate, m->t_visc, m->dE_dT,  0.0};
-  double o[70];
-  oracle_leaf(mp, eps, theta, zn, trn, dt, o);
+  double o[57 + OR_ZMAX];
+  oracle_leaf(m->row, eps, theta, zn, trn, dt, o);
   memcpy(L->sig, o, 6 * sizeof(double));
   memcpy(L->C, o + 6, 36 * sizeof(double));
   memcpy(L->tau, o + 42, 6 * sizeof(double));
@@ -881,8 +1116,10 @@ static int load_mats(const double *mats, int n_mats, omat *m) {
     m[i].E = r[1]; m[i].nu = r[2]; m[i].alpha = r[3]; m[i].theta0 = r[4];
     m[i].sy0 = r[5]; m[i].dsy_dT = r[6]; m[i].H = r[7];
     m[i].m_rate = r[8]; m[i].t_visc = r[9]; m[i].dE_dT = r[10];
-    if (m[i].kind < 0 || m[i].kind > 2) return -1;
+    memcpy(m[i].row, r, OR_MATW * sizeof(double));
+    if (m[i].kind < 0 || m[i].kind > 3) return -1;
     if (m[i].kind == 2 && !(m[i].m_rate >= 1.0 && m[i].t_visc > 0.0)) return -1;
+    if (m[i].kind == 3 && !(r[8] >= 1.0 && r[9] > 0.0 && r[5] > 0.0)) return -1;
   }
   return 0;
 }

@@ -51,6 +51,15 @@ FIBER = (KIND_THERMOELASTIC, 72000.0, 0.22, 5e-6, 293.0, 0.0, 0.0, 0.0)
 MATRIX = (KIND_J2_LINEAR, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0)
 MATRIX_PERZYNA = (KIND_J2_PERZYNA, 2500.0, 0.38, 8e-5, 293.0, 50.0, -0.3, 300.0, 5.0, 1e3, -0.002, 0.0)
 THETA_START = 293.0
+KIND_PA66 = 3
+# PA66 matrix (Sec. 4, after Krairi et al.; the paper's material table): E_inf, nu,
+# alpha0, theta0 (the paper's reference temperature of its validation runs), sigma_Y0,
+# hardening k and exponent n, rate exponent m, eta0, beta1, beta2, theta_ref, WLF C1,
+# C2, then the 12 Maxwell moduli E_i (MPa) and relaxation times tau_i (s)
+PA66_E_MAXWELL = (265.0, 262.0, 248.0, 231.0, 211.0, 190.0, 170.0, 92.0, 78.0, 65.0, 54.0, 48.0)
+PA66_LOG10_TAU = (-4.22, -3.42, -2.63, -1.84, -1.05, -0.26, 0.53, 1.32, 2.12, 2.91, 3.70, 4.49)
+MATRIX_PA66 = ((KIND_PA66, 1500.0, 0.42, 70e-6, 293.15, 15.5, 103.0, 0.32, 2.0, 74.0, 0.011, 0.07,
+                298.15, 26.21, 446.31, 0.0) + PA66_E_MAXWELL + tuple(10.0 ** t for t in PA66_LOG10_TAU))
 # volumetric heat capacity c_0 (MPa/K = 1e6 J m^-3 K^-1) of the rows of
 # materials(): E-glass fiber and PA66 matrix (Sec. 4, material tables)
 HEAT_CAPACITY = (2.1, 1.9)
@@ -72,6 +81,13 @@ def materials_viscoplastic():
     fib = np.zeros(12)
     fib[:8] = FIBER
     return np.array([fib, MATRIX_PERZYNA], dtype=np.float64)
+
+
+def materials_pa66():
+    """E-glass fiber and the PA66 matrix as 40-column rows."""
+    fib = np.zeros(40)
+    fib[:8] = FIBER
+    return np.array([fib, MATRIX_PA66], dtype=np.float64)
 
 
 def materials_cyclic():
