@@ -144,6 +144,9 @@ def solve_kernel_name(variant, precision, law=1):
     """Template instance the solve launches for K = 8: thermoelastic / J2
     leaves (law 1, by variant) or with Perzyna leaves (law 2, always the
     compact form; see dmn_solve.cu)."""
+    if law == 3:
+        return ("dmn_solve_compact<double, double, 128, 1, 3>" if precision == "fp64"
+                else "dmn_solve_compact<float, dfl, 128, 2, 3>")
     if law == 2:
         return ("dmn_solve_compact<double, double, 128, 1, 2>" if precision == "fp64"
                 else "dmn_solve_compact<float, dfl, 128, 3, 2>")
@@ -484,7 +487,9 @@ def run_cyclic(args):
     increment is an outer Newton over Algorithm 1 evaluations (mixed
     precision, each one warm-started from the previous one's jumps), started
     from the previous increment's tangent prediction, until the prescribed
-    stresses and the heat balance hold to 1e-10."""
+    stresses and the heat balance hold to 1e-10.  With --matrix pa66 the
+    matrix is the paper's PA66 law (12 Maxwell branches, WLF, power-law
+    hardening, thermal softening), as in its cyclic validation."""
     import torch
 
     from paper_2109_14403_gb300 import DMN, synthetic as syn
@@ -501,7 +506,9 @@ def run_cyclic(args):
     mask_h, tgt_h, dt, amp, direction = syn.cyclic_stress(n, n_cycles, seed=42 + rank)
     w, nrm, ph = syn.tree(K_DEPTH)
     c_heat = syn.effective_heat_capacity(w, ph)
-    d = DMN(K_DEPTH, w, nrm, ph, syn.materials_cyclic(), tol=TOL, precision=args.precision)
+    pa66 = args.matrix == "pa66"
+    mats = syn.materials_pa66() if pa66 else syn.materials_cyclic()
+    d = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision=args.precision)
     mask = torch.tensor(mask_h, device=dev)
     tgt = torch.tensor(tgt_h[:warm + steps], device=dev)
     deps = torch.zeros((n, 6), dtype=torch.float64, device=dev)
@@ -552,16 +559,19 @@ def run_cyclic(args):
             torch.distributed.destroy_process_group()
         return
     flops = alu_flops_per_pass(K_DEPTH) * passes * n / (solve_ms / 1e3) / 1e12
-    bpe = algorithmic_bytes_per_eval(K_DEPTH, 13)
+    bpe = algorithmic_bytes_per_eval(K_DEPTH, 79 if pa66 else 13)
     hbm = bpe * n / (solve_ms / 1e3) / 1e9
     peak, how = measured_peaks()
-    line = {"metric": "stress-controlled adiabatic Gauss-pt increments/s, K=8 (outer Newton over Algorithm 1)",
+    matrix = ("PA66 matrix (12 Maxwell branches, WLF, power-law hardening, thermal softening)" if pa66
+              else "Perzyna matrix (m 2, t_visc 74/15.5 s)")
+    line = {"metric": "stress-controlled adiabatic Gauss-pt increments/s, K=8 (outer Newton over Algorithm 1)"
+                      + (", PA66 matrix" if pa66 else ""),
             "value": whole_job_rate(n, world, steps, t_ms), "unit": "GP-increments/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32 + float-float (2xf32); f64 outer Newton",
             "data": "synthetic",
-            "config": {"workload": f"K=8 DMN, Perzyna matrix (m 2, t_visc 74/15.5 s), {n} points, uniaxial "
+            "config": {"workload": f"K=8 DMN, {matrix}, {n} points, uniaxial "
                                    "sinusoidal stress 20-80 MPa at 10 Hz, 20 increments per cycle, adiabatic; "
                                    f"increments {warm}-{warm + steps - 1}",
                        "precision": args.precision, "tol": TOL, "tol_outer": tol_outer,
@@ -571,7 +581,8 @@ def run_cyclic(args):
             "not_converged": failed,
             "temperature_change_K": {"min": float(dT.min()), "max": float(dT.max())},
             "roofline": {"bound": "alu", "achieved": flops, "peak": 73.2, "unit": "TFLOP/s", "frac": flops / 73.2,
-                         "traffic": None, "kernel": solve_kernel_name(d.solve_variant, args.precision, law=2),
+                         "traffic": None,
+                         "kernel": solve_kernel_name(d.solve_variant, args.precision, law=3 if pa66 else 2),
                          "launch": "one plain evaluation of the last increment from a^n, timed alone",
                          "launch_ms": solve_ms, "flops_per_pass": alu_flops_per_pass(K_DEPTH),
                          "passes_per_eval": passes,
@@ -579,20 +590,20 @@ def run_cyclic(args):
                                  "peak_source": how, "bytes_per_eval": bpe}},
             "clocks": clk.summary(), "gpu_launches": 2 * evals + 2 * steps}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline_cyclic(n_points=256)
+        line["cpu_baseline"] = cpu_baseline_cyclic(n_points=32 if pa66 else 256, pa66=pa66)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline_cyclic(n_points=256, threads=None):
+def cpu_baseline_cyclic(n_points=256, threads=None, pa66=False):
     """FP64 oracle's outer Newton on the host cores: the first increment of the
     cyclic workload on n_points points."""
     import oracle
     from paper_2109_14403_gb300 import synthetic as syn
     threads = threads or os.cpu_count() or 1
     w, nrm, ph = syn.tree(K_DEPTH)
-    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials_cyclic())
+    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials_pa66() if pa66 else syn.materials_cyclic())
     mask, tgt, dt, _, _ = syn.cyclic_stress(n_points, 1, seed=42)
     s = tree.init_state(n_points, syn.THETA_START)
     t0 = time.perf_counter()
@@ -682,6 +693,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="uneven and cyclic workloads only")
+    ap.add_argument("--matrix", default="perzyna", choices=["perzyna", "pa66"],
+                    help="cyclic workload only: the matrix law")
     ap.add_argument("--workload", default="random_walk",
                     choices=["random_walk", "uneven", "mlp", "large", "cyclic"])
     args = ap.parse_args()

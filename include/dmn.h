@@ -78,7 +78,21 @@ enum {
                                 <(q - sigma_Y - H p)/sigma_Y>^m), linear
                                 hardening, moduli E (1 + dE_dT (theta -
                                 theta0)); internal variables eps_p, p and
-                                the leaf strain (13 words)                */
+                                the leaf strain (13 words)                */,
+  DMN_MAT_PA66 = 3           /* the PA66 matrix of Sec. 4 (after Krairi et
+                                al.): long-term branch E (here E_inf) and up
+                                to 12 Maxwell branches E_maxwell[i],
+                                tau_maxwell[i] with a common nu, WLF-shifted
+                                viscosities (wlf_C1, wlf_C2, theta_ref),
+                                J2 viscoplasticity p_dot = (sigma_Y/eta)
+                                <(q - sigma_Y - H)/sigma_Y>^m with sigma_Y =
+                                Gamma(beta1) sy0, H = Gamma(beta1) k_hard
+                                p^n_hard, eta = Gamma(beta2) eta0, Gamma(b) =
+                                exp(-b (theta - theta_ref)); coupling term
+                                and dissipation of the PA66 model; implicit
+                                Euler; internal variables eps_vp (6), p and
+                                the 12 Maxwell strains (79 words); trees
+                                with K <= 8                                */
 };
 
 typedef struct {
@@ -96,6 +110,17 @@ typedef struct {
   double t_visc;  /* Perzyna: viscous time (s), > 0                         */
   double dE_dT;   /* Perzyna: relative modulus slope (1/K); the factor
                      1 + dE_dT (theta - theta0) is floored at 1e-3          */
+  /* PA66 (kind 3; also uses E = E_inf, nu, alpha, theta0, sy0 and m_rate) */
+  double k_hard, n_hard; /* hardening H = Gamma k_hard p^n_hard: k >= 0,
+                            0 < n <= 1                                      */
+  double eta0;           /* reference viscosity (MPa s), > 0                */
+  double beta1, beta2;   /* thermal softening of sigma_Y and H, of eta (1/K) */
+  double theta_ref;      /* reference temperature of Gamma and WLF (K)      */
+  double wlf_C1, wlf_C2; /* WLF constants; C2 + theta - theta_ref must stay
+                            > 0 (else the point reports a non-finite output) */
+  double E_maxwell[12];  /* Maxwell moduli (MPa), >= 0; 0 = unused branch   */
+  double tau_maxwell[12]; /* relaxation times at theta_ref (s), > 0 where
+                             E_maxwell > 0                                  */
 } dmn_material;
 
 enum { DMN_PREC_FP64 = 0, DMN_PREC_MIXED = 1 };
@@ -153,8 +178,10 @@ dmn_status dmn_destroy(dmn_handle h);
  *   [6]      theta^n    (K)
  *   [7]      reserved (0)
  *   [8 .. 8+3(2^K-1))  jump vectors a^n, node order as above, (x, y, z) each
- *   then, for every leaf j in order whose material is DMN_MAT_J2_LINEAR:
- *            plastic strain (6, Mandel) and accumulated plastic strain p (1)
+ *   then, for every leaf j in order whose material has internal variables:
+ *            DMN_MAT_J2_LINEAR: eps_p (6), p; DMN_MAT_J2_PERZYNA: eps_p (6), p,
+ *            the leaf strain (6); DMN_MAT_PA66: eps_vp (6), p, eps_v,1 .. eps_v,12
+ *            (6 each), all Mandel; p is the accumulated plastic strain
  *   padded to an even number of words.
  * A batch is n_points such blocks back to back.
  */

@@ -24,25 +24,66 @@ struct dmn_handle_s {
   double *d_node;        // [N][kNodeWords]
   float *d_node_df;      // [N][kNodeDfl]
   double *d_leafw;       // [nleaf]
-  int zw;                // words of internal variables per state block
+  int zw;                // words of internal variables per state block (law 3: words
+                         // of the leaves' history in the solve's shared memory)
   int law;               // largest material kind (1: kinds 0/1, 2: Perzyna leaves)
   uint8_t *d_phase;      // [nleaf]
   int *d_zoff;           // [nleaf]
+  int *d_hoff;           // [nleaf], law 3 only
   double *d_mat;         // [n_mats][kMatWords]
 };
 
 namespace dmn {
 int material_z_words(int kind) {
-  return kind == DMN_MAT_J2_LINEAR ? 7 : (kind == DMN_MAT_J2_PERZYNA ? 13 : 0);
+  return kind == DMN_MAT_J2_LINEAR ? 7
+                                   : (kind == DMN_MAT_J2_PERZYNA ? 13 : (kind == DMN_MAT_PA66 ? kPaZ : 0));
 }
+int material_hist_words(int kind) { return kind == DMN_MAT_PA66 ? kPaHist : material_z_words(kind); }
 
 // Sec. 4: K = E/(3(1-2nu)), G = E/(2(1+nu)); the device row holds the moduli at
 // theta0 and, for the Perzyna leaf, m, 1/t_visc and dE_dT
 const char *material_row(const dmn_material &m, double r[kMatWords]) {
-  if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR && m.kind != DMN_MAT_J2_PERZYNA)
+  if (m.kind != DMN_MAT_THERMOELASTIC && m.kind != DMN_MAT_J2_LINEAR && m.kind != DMN_MAT_J2_PERZYNA &&
+      m.kind != DMN_MAT_PA66)
     return "unknown kind";
   if (!(m.E > 0.0) || !(m.nu > -1.0 && m.nu < 0.5) || !isfinite(m.alpha) || !(m.theta0 > 0.0))
     return "invalid elastic constants";
+  for (int i = 0; i < kMatWords; ++i) r[i] = 0.0;
+  if (m.kind == DMN_MAT_PA66) {
+    if (!(m.sy0 > 0.0) || !(m.k_hard >= 0.0) || !isfinite(m.k_hard) || !(m.n_hard > 0.0 && m.n_hard <= 1.0))
+      return "invalid PA66 hardening (sy0 > 0, k_hard >= 0, 0 < n_hard <= 1)";
+    if (!(m.m_rate >= 1.0 && m.m_rate <= 8.0) || m.m_rate != floor(m.m_rate) || !(m.eta0 > 0.0) ||
+        !isfinite(m.eta0))
+      return "invalid PA66 rate law (m an integer in 1..8, eta0 > 0)";
+    if (!(m.beta1 >= 0.0) || !isfinite(m.beta1) || !(m.beta2 >= 0.0) || !isfinite(m.beta2) ||
+        !(m.theta_ref > 0.0) || !isfinite(m.wlf_C1) || !(m.wlf_C2 > 0.0) || !isfinite(m.wlf_C2))
+      return "invalid PA66 softening / WLF constants";
+    for (int i = 0; i < kPaBranches; ++i)
+      if (!(m.E_maxwell[i] >= 0.0) || !isfinite(m.E_maxwell[i]) ||
+          (m.E_maxwell[i] > 0.0 && !(m.tau_maxwell[i] > 0.0 && isfinite(m.tau_maxwell[i]))))
+        return "invalid Maxwell branch (E >= 0, tau > 0)";
+    r[0] = m.kind;
+    r[1] = m.E / (3.0 * (1.0 - 2.0 * m.nu));
+    r[2] = m.E / (2.0 * (1.0 + m.nu));
+    r[3] = m.alpha;
+    r[4] = m.theta0;
+    r[5] = m.sy0;
+    r[6] = m.k_hard;
+    r[7] = m.n_hard;
+    r[8] = m.m_rate;
+    r[9] = m.eta0;
+    r[10] = m.beta1;
+    r[11] = m.beta2;
+    r[12] = m.theta_ref;
+    r[13] = m.wlf_C1;
+    r[14] = m.wlf_C2;
+    r[15] = m.nu;
+    for (int i = 0; i < kPaBranches; ++i) {
+      r[16 + i] = m.E_maxwell[i];
+      r[28 + i] = m.E_maxwell[i] > 0.0 ? m.tau_maxwell[i] : 1.0;
+    }
+    return nullptr;
+  }
   const bool j2 = m.kind != DMN_MAT_THERMOELASTIC;
   if (j2 && (!(m.sy0 > 0.0) || !isfinite(m.dsy_dT) || !(m.H >= 0.0) || !isfinite(m.H)))
     return "invalid J2 constants";
@@ -103,6 +144,7 @@ static void free_handle(dmn_handle h) {
   cudaFree(h->d_node_df);
   cudaFree(h->d_phase);
   cudaFree(h->d_zoff);
+  cudaFree(h->d_hoff);
   cudaFree(h->d_mat);
   cudaFree(h->d_queue);
   cudaFree(h->d_open);
@@ -194,23 +236,30 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
     o[16] = (float)r[7];
     o[17] = (float)r[6];
   }
-  // z offsets in a state block
-  std::vector<int> zoff(nleaf);
-  int off = 8 + 3 * N, law = 1;
+  // z offsets in a state block; with PA66 leaves also the offsets of the
+  // leaves' history words in the solve's shared memory
+  std::vector<int> zoff(nleaf), hoff(nleaf);
+  int off = 8 + 3 * N, law = 1, hw = 0;
   for (int j = 0; j < nleaf; ++j) {
     const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
-    if (kind == DMN_MAT_J2_PERZYNA) law = 2;
+    if (kind == DMN_MAT_J2_PERZYNA && law < 2) law = 2;
+    if (kind == DMN_MAT_PA66) law = 3;
     if (zwl > 0) {
       zoff[j] = off;
       off += zwl;
+      hoff[j] = hw;
+      hw += material_hist_words(kind);
     } else {
       zoff[j] = -1;
+      hoff[j] = -1;
     }
   }
   const int zend = off;
-  const int zw = zend - (8 + 3 * N);
+  int zw = zend - (8 + 3 * N);
   if (off & 1) off += 1;
   if (law == 2 && K > 9) return fail(DMN_ERR_ARG, "dmn_create: Perzyna leaves need K <= 9 (K=%d)", K);
+  if (law == 3 && K > 8) return fail(DMN_ERR_ARG, "dmn_create: PA66 leaves need K <= 8 (K=%d)", K);
+  if (law == 3) zw = hw;  // the solve keeps the leaves' history, not z, in shared memory
 
   dmn_handle h = new dmn_handle_s();
   memset(h, 0, sizeof(*h));
@@ -251,6 +300,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (e = cudaMalloc(&h->d_node_df, sizeof(float) * kNodeDfl * N)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_phase, nleaf)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_zoff, sizeof(int) * nleaf)) != cudaSuccess ||
+      (law == 3 && (e = cudaMalloc(&h->d_hoff, sizeof(int) * nleaf)) != cudaSuccess) ||
       (e = cudaMalloc(&h->d_mat, sizeof(double) * kMatWords * n_mats)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess ||
       (e = cudaMalloc(&h->d_open, sizeof(unsigned long long))) != cudaSuccess) {
@@ -262,6 +312,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (e = cudaMemcpy(h->d_node_df, node_df.data(), sizeof(float) * kNodeDfl * N, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_phase, phase_map, nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(h->d_zoff, zoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (law == 3 && (e = cudaMemcpy(h->d_hoff, hoff.data(), sizeof(int) * nleaf, cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemcpy(h->d_mat, mat.data(), sizeof(double) * kMatWords * n_mats, cudaMemcpyHostToDevice)) != cudaSuccess) {
     free_handle(h);
     return cuda_fail(e, "cudaMemcpy");
@@ -346,6 +397,7 @@ static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
   P.law = h->law;
   P.phase = h->d_phase;
   P.zoff = h->d_zoff;
+  P.hoff = h->d_hoff;
   P.mat = h->d_mat;
   P.n_points = n_points;
   P.deps = d_deps;

@@ -17,11 +17,16 @@ using KernelFn = void (*)(const SolveParams);
 size_t compact_smem_bytes(int K, int zw, int n_mats, bool mixed);
 KernelFn compact_kernel(int K, bool mixed, int minb);
 KernelFn compact_kernel_vp(int K, bool mixed);
+// ... and dmn_solve_compact_pa66.cu (also kind 3, K <= 8; hw: history words)
+size_t compact_smem_bytes_pa(int K, int hw, int n_mats, bool mixed);
+KernelFn compact_kernel_pa66(int K, bool mixed);
 // host: validate a material and write its device row (kMatWords doubles);
 // returns nullptr or the reason it is invalid
 const char *material_row(const dmn_material &m, double row[kMatWords]);
-// words of internal variables of a leaf of this kind (0, 7 or 13)
+// words of internal variables of a leaf of this kind (0, 7, 13 or 79), and
+// the words of shared memory the solve keeps for it (kind 3: its history)
 int material_z_words(int kind);
+int material_hist_words(int kind);
 cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
                           int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);

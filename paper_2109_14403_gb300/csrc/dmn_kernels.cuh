@@ -40,17 +40,26 @@ constexpr int kOutWords = 57;
 constexpr int kNodeWords = 12;  // FP64 node table row
 constexpr int kNodeDfl = 20;    // float-float node table row (floats)
 
-constexpr int kMatWords = 12;  // device material row
+constexpr int kPaBranches = 12;  // Maxwell branches of the PA66 leaf
+constexpr int kPaZ = 7 + 6 * kPaBranches;  // its internal variables in the state
+constexpr int kPaHist = 34;  // its history words in the solve's shared memory
+constexpr int kMatWords = 40;  // device material row
+// Kinds 0-2 use the first 12 words.  Kind 3 (PA66): Kb, G of the long-term
+// branch, alpha, theta0, sy0, then dsy = k (hardening), H = n (exponent),
+// mexp = m, itv = eta0, cE = beta1, pad_ = beta2, and pa = theta_ref, C1, C2,
+// nu, E_1..E_12, tau_1..tau_12.
 struct MatDev {
   double kind, Kb, G, alpha, theta0, sy0, dsy, H;  // moduli at theta0
   double mexp, itv, cE, pad_;  // Perzyna: rate exponent, 1 / t_visc, dE_dT / E
+  double pa[28];
 };
 
 struct SolveParams {
   int K, N, G, SW;         // depth, nodes, threads per point, state words
   int n_mats, maxit, maxbt, zend;  // zend: end of the z data in a state block
   int zw;                          // words of internal variables per state block
-  int law;                         // largest material kind of the tree (1 or 2)
+  int law;                         // largest material kind of the tree (1, 2 or 3)
+  const int *hoff;                 // law 3: offset of a leaf's history in shared memory, -1 none
   unsigned long long *queue;       // device counter of points taken (zeroed per launch)
   const float *da0;                // optional warm-start increment [n][3N] (NULL: start at a^n)
   const int *skip;                 // optional [n]: points with skip[i] != 0 are left untouched

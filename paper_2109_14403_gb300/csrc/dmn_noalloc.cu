@@ -148,6 +148,8 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   int off = 8 + 3 * N, law = 1;
   for (int j = 0; j < nleaf; ++j) {
     const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
+    if (kind == DMN_MAT_PA66)
+      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: PA66 leaves (kind 3) need a dmn_handle");
     if (kind == DMN_MAT_J2_PERZYNA) law = 2;
     if (zwl > 0) {
       zoff[j] = off;

@@ -453,7 +453,8 @@ static size_t owner_smem_bytes(int K, int zw, int n_mats, bool mixed) {
 // or 4 CTAs per SM (11 runs as 12), FP64 for one.  Depth K > 8 takes the
 // owner-mapped 512-thread kernel.  A tree with Perzyna leaves (law 2) always
 // takes the compact instances that include that leaf law
-// (dmn_solve_compact_vp.cu, K <= 9), whatever the variant.
+// (dmn_solve_compact_vp.cu, K <= 9), whatever the variant; one with PA66
+// leaves (law 3) the instances of dmn_solve_compact_pa66.cu (K <= 8).
 bool solve_variant_valid(int variant) {
   return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 14);
 }
@@ -462,6 +463,7 @@ static bool is_compact(int K, int variant, int law) {
 }
 
 static KernelFn pick(int K, bool mixed, int variant, int law) {
+  if (law == 3) return compact_kernel_pa66(K, mixed);
   if (law >= 2) return compact_kernel_vp(K, mixed);
   if (is_compact(K, variant, law)) return compact_kernel(K, mixed, variant - 10);
   if (K > 8) return mixed ? dmn_solve_kernel<float, dfl, 512, 1> : dmn_solve_kernel<double, double, 512, 1>;
@@ -474,6 +476,7 @@ static KernelFn pick(int K, bool mixed, int variant, int law) {
 }
 
 size_t solve_smem_bytes(int K, int zw, int n_mats, bool mixed, int variant, int law) {
+  if (law == 3) return compact_smem_bytes_pa(K, zw, n_mats, mixed);
   return is_compact(K, variant, law) ? compact_smem_bytes(K, zw, n_mats, mixed)
                                      : owner_smem_bytes(K, zw, n_mats, mixed);
 }

@@ -23,6 +23,7 @@
 #pragma once
 #include "dmn_internal.h"
 #include "solve_common.cuh"
+#include "pa66.cuh"
 
 namespace dmn {
 
@@ -85,7 +86,9 @@ __host__ __device__ inline Scratch scratch_layout(int G, int tf_bytes) {
 using namespace compact_detail;
 
 // LAW: largest material kind the instance handles (1: thermoelastic and J2;
-// 2: also the Perzyna leaf)
+// 2: also the Perzyna leaf; 3: also the PA66 leaf, whose per-point constants
+// (MatPA) follow the materials' and whose leaves keep their history, not
+// their internal variables, in zn_s at P.hoff)
 template <typename TF, typename HP, int MAXT, int MINB, int LAW>
 __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,8 +104,12 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   HP *misc = sroot + 6;                        // 4: 1/dt, D_bar, X_bar
   HP *scr = misc + 4;                          // scratch region (Scratch)
   MatPt<TF, HP> *mp_s = reinterpret_cast<MatPt<TF, HP> *>(scr + sc_.words);
-  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(
+  MatPA<TF, HP> *mpa_s = reinterpret_cast<MatPA<TF, HP> *>(
       (reinterpret_cast<uintptr_t>(mp_s + P.n_mats) + 15) & ~uintptr_t(15));
+  Ctrl<TF> *ctrl = reinterpret_cast<Ctrl<TF> *>(
+      (reinterpret_cast<uintptr_t>(LAW == 3 ? reinterpret_cast<void *>(mpa_s + P.n_mats)
+                                            : reinterpret_cast<void *>(mp_s + P.n_mats)) + 15) &
+      ~uintptr_t(15));
   TF *red = reinterpret_cast<TF *>(ctrl + 1);  // 32
   TF *orec = red + 32;                         // 40
   TF *da_s = orec + 40;                        // 3N  Newton increment
@@ -153,6 +160,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
   const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
   const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
+  const int hq0 = LAW == 3 ? P.hoff[2 * t] : zq0, hq1 = LAW == 3 ? P.hoff[2 * t + 1] : zq1;
   const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
   // Strains of the bottom laminates by ancestor sums (eq. DMN kinematics):
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       for (int u = 0; u < U; ++u) {
         const int i = t + u * G;
         va[u] = i < 3 * N ? ld_stream(sin + 8 + i) : 0.0;
-        vz[u] = i < ZW ? ld_stream(sin + 8 + 3 * N + i) : 0.0;
+        vz[u] = LAW < 3 && i < ZW ? ld_stream(sin + 8 + 3 * N + i) : 0.0;
         vp[u] = d0 && i < 3 * N ? ld_stream(d0 + i) : 0.0f;
       }
       if (G >= 8 && t < 6) {
@@ -270,9 +278,9 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           a_s[i] = hp_load(va[u], tag);
           if (d0) da_s[i] = TF(vp[u]);
         }
-        if (i < ZW) zn_s[i] = hp_load(vz[u], tag);
+        if (LAW < 3 && i < ZW) zn_s[i] = hp_load(vz[u], tag);
       }
-      if (ZW > U * G) load_hp(zn_s + U * G, sin + 8 + 3 * N + U * G, ZW - U * G);
+      if (LAW < 3 && ZW > U * G) load_hp(zn_s + U * G, sin + 8 + 3 * N + U * G, ZW - U * G);
       if (G >= 8) {
         if (t < 6) {
           ebd[t] = ve + vd;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
@@ -290,6 +298,27 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     }
     __syncthreads();
     for (int i = t; i < P.n_mats; i += G) mat_point<TF, HP, LAW>(mp_s[i], hp_load(theta, tag), misc[0], idt_f);
+    if (LAW == 3) {
+      // PA66 constants at this temperature, then each thread's leaves: the
+      // history of a PA66 leaf, the internal variables of a J2 leaf
+      for (int i = t; i < P.n_mats; i += G)
+        if (mp_s[i].kind == 3)
+          mat_point_pa<TF, HP>(mpa_s[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i), theta,
+                               P.dt);
+      __syncthreads();
+#pragma unroll 1
+      for (int sd = 0; sd < 2; ++sd) {
+        const int j = 2 * t + sd, zo = sd ? zo1 : zo0, ph = sd ? ph1 : ph0, hq = sd ? hq1 : hq0;
+        if (zo < 0) continue;
+        if (mp_s[ph].kind == 3) {
+          pa_history<TF, HP>(mpa_s[ph], sin + zo, zn_s + hq);
+        } else {
+          const int nz = mp_s[ph].kind == 1 ? 7 : 13;
+          for (int c = 0; c < nz; ++c) zn_s[hq + c] = hp_load(sin[zo + c], tag);
+        }
+        (void)j;
+      }
+    }
     if (t == 0) {
       ctrl->first = 1;
       ctrl->it = 0;
@@ -298,8 +327,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       ctrl->res_old = TF(0);
       ctrl->status = 0;
     }
-    const HP *zn0 = zq0 >= 0 ? zn_s + zq0 : nullptr;
-    const HP *zn1 = zq1 >= 0 ? zn_s + zq1 : nullptr;
+    const HP *zn0 = hq0 >= 0 ? zn_s + hq0 : nullptr;
+    const HP *zn1 = hq1 >= 0 ? zn_s + hq1 : nullptr;
     HP *zw0 = zq0 >= 0 ? zw + zq0 : nullptr;
     HP *zw1 = zq1 >= 0 ? zw + zq1 : nullptr;
 
@@ -350,8 +379,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         }
         HP sl[6], sr[6], DL, DR, XL, XR;
         Rec<TF> rr;
-        leaf_eval<TF, HP, LAW>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
-        leaf_eval<TF, HP, LAW>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
+        if (LAW == 3 && mp_s[ph0].kind == 3)
+          leaf_pa66<TF, HP>(mp_s[ph0], mpa_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+        else
+          leaf_eval<TF, HP, LAW>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+        if (LAW == 3 && mp_s[ph1].kind == 3)
+          leaf_pa66<TF, HP>(mp_s[ph1], mpa_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
+        else
+          leaf_eval<TF, HP, LAW>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
         Dsum = wL * DL + wR * DR;
         Xsum = wL * XL + wR * XR;
         HP dsh[6];
@@ -630,13 +665,31 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     }
     for (int c = t; c < 8; c += G) sout[c] = c < 6 ? ebd[c] : (c == 6 ? theta : 0.0);
     for (int i = t; i < 3 * N; i += G) __stcs(sout + 8 + i, hp_to(a_s[i]));
-    for (int i0 = t; i0 < ZW; i0 += 8 * G) {  // parked internal variables -> FP64 in place
-      HP v[8];
+    if (LAW == 3) {  // each thread its own leaves (it parked their values itself)
+#pragma unroll 1
+      for (int sd = 0; sd < 2; ++sd) {
+        const int zo = sd ? zo1 : zo0, ph = sd ? ph1 : ph0;
+        if (zo < 0) continue;
+        if (mp_s[ph].kind == 3) {
+          pa_finish<TF, HP>(mpa_s[ph], sin + zo, sout + zo);
+        } else {
+          const int nz = mp_s[ph].kind == 1 ? 7 : 13;
+          const HP *zp = reinterpret_cast<const HP *>(sout + zo);
+          for (int c = 0; c < nz; ++c) {
+            const HP v = zp[c];
+            sout[zo + c] = hp_to(v);
+          }
+        }
+      }
+    } else {
+      for (int i0 = t; i0 < ZW; i0 += 8 * G) {  // parked internal variables -> FP64 in place
+        HP v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < ZW ? ld_once(zw + i0 + u * G) : hp_zero(tag);
+        for (int u = 0; u < 8; ++u) v[u] = i0 + u * G < ZW ? ld_once(zw + i0 + u * G) : hp_zero(tag);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (i0 + u * G < ZW) __stcs(sout + 8 + 3 * N + i0 + u * G, hp_to(v[u]));
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * G < ZW) __stcs(sout + 8 + 3 * N + i0 + u * G, hp_to(v[u]));
+      }
     }
     for (int i = P.zend + t; i < P.SW; i += G) sout[i] = 0.0;  // padding word
     __syncthreads();

@@ -28,7 +28,11 @@ class dmn_material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("E", ctypes.c_double),
                 ("nu", ctypes.c_double), ("alpha", ctypes.c_double), ("theta0", ctypes.c_double),
                 ("sy0", ctypes.c_double), ("dsy_dT", ctypes.c_double), ("H", ctypes.c_double),
-                ("m_rate", ctypes.c_double), ("t_visc", ctypes.c_double), ("dE_dT", ctypes.c_double)]
+                ("m_rate", ctypes.c_double), ("t_visc", ctypes.c_double), ("dE_dT", ctypes.c_double),
+                ("k_hard", ctypes.c_double), ("n_hard", ctypes.c_double), ("eta0", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("theta_ref", ctypes.c_double),
+                ("wlf_C1", ctypes.c_double), ("wlf_C2", ctypes.c_double),
+                ("E_maxwell", ctypes.c_double * 12), ("tau_maxwell", ctypes.c_double * 12)]
 
 
 class dmn_options(ctypes.Structure):
@@ -123,16 +127,29 @@ def _dev(t, dtype, shape, name):
 
 
 def materials_from_rows(rows):
-    """Material table rows (kind, E, nu, alpha, theta0, sy0, dsy_dT, H[, m_rate,
-    t_visc, dE_dT, 0]) -> ctypes array; rows of 8 leave the Perzyna fields 0."""
+    """Material table rows -> ctypes array.  Kinds 0-2: (kind, E, nu, alpha,
+    theta0, sy0, dsy_dT, H[, m_rate, t_visc, dE_dT, 0]); rows of 8 leave the
+    Perzyna fields 0.  Kind 3 (PA66, 40 columns): (3, E_inf, nu, alpha0, theta0,
+    sy0, k, n, m, eta0, beta1, beta2, theta_ref, C1, C2, 0, E_1..E_12,
+    tau_1..tau_12).  Shorter rows may be padded with zeros to 40 columns."""
     rows = np.atleast_2d(np.asarray(rows, np.float64))
-    if rows.shape[1] not in (8, 11, 12):
-        raise ValueError("material rows have 8 or 12 columns")
+    if rows.shape[1] not in (8, 11, 12, 40):
+        raise ValueError("material rows have 8, 12 or 40 columns")
     arr = (dmn_material * rows.shape[0])()
     for i, r in enumerate(rows):
         arr[i].kind = int(r[0])
         arr[i].E, arr[i].nu, arr[i].alpha, arr[i].theta0 = r[1], r[2], r[3], r[4]
-        arr[i].sy0, arr[i].dsy_dT, arr[i].H = r[5], r[6], r[7]
+        arr[i].sy0 = r[5]
+        if int(r[0]) == 3:
+            if rows.shape[1] != 40:
+                raise ValueError("PA66 rows have 40 columns")
+            arr[i].k_hard, arr[i].n_hard, arr[i].m_rate, arr[i].eta0 = r[6], r[7], r[8], r[9]
+            arr[i].beta1, arr[i].beta2, arr[i].theta_ref = r[10], r[11], r[12]
+            arr[i].wlf_C1, arr[i].wlf_C2 = r[13], r[14]
+            for b in range(12):
+                arr[i].E_maxwell[b], arr[i].tau_maxwell[b] = r[16 + b], r[28 + b]
+            continue
+        arr[i].dsy_dT, arr[i].H = r[6], r[7]
         if rows.shape[1] > 8:
             arr[i].m_rate, arr[i].t_visc, arr[i].dE_dT = r[8], r[9], r[10]
     return arr

@@ -326,3 +326,51 @@ def test_perzyna_k9_full_batch_sampled(prec):
     launch configuration; the oracle checks 48 sampled points."""
     deps, theta = syn.large_path(n_points=1 << 20, n_incr=2, seed=10, dtype=np.float64)
     run_path(9, prec, deps * 30.0, theta, n_check=48, dt=syn.LARGE_DT, mats=syn.materials_viscoplastic())
+
+
+@pytest.mark.parametrize("K", [1, 3, 5, 8])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pa66_depths(K, prec):
+    """The paper's PA66 matrix (12 Maxwell branches, WLF shift, power-law
+    hardening, thermal softening) with E-glass fibers; three increments of
+    dt = 0.01 s with N(0, 2e-3) strain increments, so that the branches carry
+    history and the matrix flows (at twice that a K = 3 point drives one leaf
+    to p ~ 0.3 in one increment and Algorithm 1 stalls in the oracle)."""
+    rng = np.random.default_rng(400 + K)
+    n = 29
+    deps = rng.normal(0, 2e-3, size=(3, n, 6))
+    theta = 293.0 + np.cumsum(rng.uniform(0, 5, size=(3, n)), axis=0)
+    run_path(K, prec, deps, theta, dt=0.01, mats=syn.materials_pa66())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_pa66_homogeneous_tree_is_the_leaf(prec):
+    """All leaves PA66: the DMN returns the leaf law (the oracle's complex-step
+    leaf) with a = 0, on two increments."""
+    dev = _dev()
+    from paper_2109_14403_gb300 import DMN
+    K = 3
+    w, nrm, ph = syn.tree(K)
+    mats = syn.materials_pa66()
+    d = DMN(K, w, nrm, np.ones_like(ph), mats, tol=1e-12, precision=prec)
+    rng = np.random.default_rng(5)
+    n = 8
+    s = d.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+    z = np.zeros((n, 79))
+    eps = np.zeros((n, 6))
+    for k in range(2):
+        deps = rng.normal(0, 5e-3, (n, 6))
+        th = np.full(n, 300.0 + 5 * k)
+        s, out, st, it = d.eval(torch.tensor(deps, device=dev), torch.tensor(th, device=dev), 0.02, s)
+        out = out.cpu().numpy()
+        tr_n = eps[:, :3].sum(axis=1)
+        eps = eps + deps
+        for i in range(n):
+            o = oracle.leaf(mats[1], eps[i], th[i], z[i], tr_n[i], 0.02)
+            tol = 1e-10 if prec == "fp64" else 1e-8
+            assert np.abs(out[i, :6] - o["sig"]).max() <= tol * np.abs(o["sig"]).max()
+            assert abs(out[i, 48] - o["D"]) <= tol * max(abs(o["D"]), 1.0)
+            z[i] = o["znew"]
+        zs = s[:, 8 + 21:8 + 21 + 79].cpu().numpy()
+        assert np.abs(zs - z).max() <= (1e-10 if prec == "fp64" else 1e-7) * np.abs(z).max()
+    d.close()
