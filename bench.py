@@ -127,16 +127,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# the translation unit of the headline solve kernel and everything it includes
+SOLVE_SOURCES = ("dfl.cuh", "dmn_internal.h", "dmn_kernels.cuh", "dmn_solve_compact.cu", "pa66.cuh",
+                 "solve_common.cuh", "solve_compact.cuh")
+
+
 def kernel_source_hash():
-    """SHA-256 over the CUDA sources of the library (file names and bytes)."""
+    """SHA-256 over the sources the headline solve kernel is compiled from
+    (file names and bytes, and the public header they include)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2109_14403_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in SOLVE_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "dmn.h"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()
 
 
