@@ -185,3 +185,41 @@ def cyclic_stress(n_points, n_cycles=1, seed=42, steps_per_cycle=CYCLE_STEPS, pe
     mask = np.full(n_points, MASK_STRESS_ADIABATIC, np.uint8)
     return mask, target, dt, amp, direction
 
+
+
+def iso_mandel(E, nu):
+    """Isotropic stiffness 3K P1 + 2G P2 as 6x6 Mandel matrices (E, nu arrays)."""
+    E, nu = np.asarray(E, np.float64), np.asarray(nu, np.float64)
+    K, G = E / (3 * (1 - 2 * nu)), E / (2 * (1 + nu))
+    P1 = np.zeros((6, 6))
+    P1[:3, :3] = 1.0 / 3.0
+    P2 = np.eye(6) - P1
+    return 3 * K[..., None, None] * P1 + 2 * G[..., None, None] * P2
+
+
+def stiffness_pairs(n_samples, seed=7, log10_contrast=2.0):
+    """Phase stiffness pairs for offline training (stand-in for the paper's
+    sampled 8-D set, Sec. 5.1): C_1 isotropic with E_1 = 1, C_2 isotropic with
+    E_2 = 10^U(-c, c), both nu ~ U(0.1, 0.45); C_2 loses a random rank-one
+    part (a fraction U(0, 0.5) of its smallest-eigenvalue direction is not
+    removed: C_2 - t (m^T C_2 m) m m^T with unit m, t ~ U(0, 0.5)), so it is
+    anisotropic but positive definite.  Returns C1s, C2s [n, 6, 6]."""
+    rng = np.random.default_rng(seed)
+    C1 = iso_mandel(np.ones(n_samples), rng.uniform(0.1, 0.45, n_samples))
+    C2 = iso_mandel(10.0 ** rng.uniform(-log10_contrast, log10_contrast, n_samples),
+                    rng.uniform(0.1, 0.45, n_samples))
+    m = rng.standard_normal((n_samples, 6))
+    m /= np.linalg.norm(m, axis=1, keepdims=True)
+    t = rng.uniform(0.0, 0.5, n_samples)
+    mCm = np.einsum("si,sij,sj->s", m, C2, m)
+    C2 = C2 - (t * mCm)[:, None, None] * np.einsum("si,sj->sij", m, m)
+    return C1, C2
+
+
+def linear_params(K, seed=None):
+    """Random DMN^L parameters: normals [(2^K-1), 3] (not normalised) and
+    unconstrained weights v [2^K] (positive, summing to about 1)."""
+    rng = np.random.default_rng(4321 + K if seed is None else seed)
+    normals = rng.standard_normal(((1 << K) - 1, 3))
+    v = rng.uniform(0.5, 1.5, 1 << K)
+    return normals, v / v.sum()
