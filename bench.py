@@ -603,6 +603,95 @@ def run_cyclic(args):
         torch.distributed.destroy_process_group()
 
 
+def lin_flops_per_sample(K):
+    """Algorithmic FLOPs of one training step per sample: two forward sweeps
+    (loss, then the backward's recomputation) at ~975 per laminate (U = D B,
+    M B, B^T M B, its inverse, U K^-1, the 21 outputs) and one reverse sweep at
+    ~2350 per laminate (the forward intermediates again, A, Q, the three inner
+    products, dJ/dB, B Q and the two child adjoints)."""
+    N = (1 << K) - 1
+    return N * (2 * 975 + 2350)
+
+
+def run_linear(args):
+    """Offline training of DMN^L (Sec. 3.2) on synthetic stiffness triples: a
+    K = 8 network, a batch of 65,536 samples (stiffness pairs with contrast up
+    to 100 and a rank-one anisotropy; targets from another random K = 8
+    network); one step = loss J with its gradient (four launches) and the
+    AMSGrad update (two launches), FP32 laminate arithmetic."""
+    import torch
+
+    from paper_2109_14403_gb300 import synthetic as syn
+    from paper_2109_14403_gb300.linear import DMNLinear
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    K, n = 8, args.points
+    prec = "fp64" if args.precision == "fp64" else "fp32"
+    C1h, C2h = syn.stiffness_pairs(n, seed=7 + rank)
+    C1 = torch.tensor(C1h, device=dev)
+    C2 = torch.tensor(C2h, device=dev)
+    teacher = DMNLinear(K, *syn.linear_params(K, seed=101), device=dev)
+    Ct = teacher.forward(C1, C2, precision="fp64")
+    d = DMNLinear(K, *syn.linear_params(K, seed=102), device=dev)
+    steps, warm = args.steps, args.warmup
+
+    def step():
+        d.loss_grad(C1, C2, Ct, p=1.0, q=10.0, penalty=1e3, precision=prec)
+        d.amsgrad_step(1.5e-2, 1.5e-3)
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    losses = [float(d.loss[0].item())]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    losses.append(float(d.loss[0].item()))
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    fl = lin_flops_per_sample(K) * n * steps / (t_ms / 1e3) / 1e12
+    line = {"metric": "DMN^L training samples/s (loss J + gradient + AMSGrad), K=8", "value":
+            whole_job_rate(n, world, steps, t_ms), "unit": "samples/s", "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": t_ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 laminates, f64 loss and gradient sums" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"K=8 DMN^L, batch {n} stiffness pairs (E2/E1 = 10^U(-2,2), rank-one "
+                                   "anisotropy), targets of another random K=8 network, p=1, q=10, "
+                                   "penalty 1e3", "precision": prec,
+                       "parallelism": f"replicas x{world} (independent batches)"},
+            "loss_before_after": losses,
+            "roofline": {"bound": "alu", "achieved": fl, "peak": 73.2 if prec == "fp32" else 1.25,
+                         "unit": "TFLOP/s", "frac": fl / (73.2 if prec == "fp32" else 1.25), "traffic": None,
+                         "kernel": f"k_lin_backward<{'float' if prec == 'fp32' else 'double'}> + "
+                                   "k_lin_forward (whole step)", "flops_per_sample": lin_flops_per_sample(K)},
+            "clocks": clk.summary(), "gpu_launches": 7 * steps}
+    if not args.no_cpu_baseline and world == 1:
+        import oracle.linear as olin
+        m = 2
+        t0 = time.perf_counter()
+        olin.loss_grad(C1h[:m], C2h[:m], Ct[:m].cpu().numpy(), *syn.linear_params(K, seed=102))
+        dtm = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m / dtm, "unit": "samples/s", "cores": torch.get_num_threads(),
+                                "kind": "oracle", "sample": f"{m} samples of the batch, loss J and gradient by "
+                                                            "automatic differentiation (PyTorch CPU, FP64)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def cpu_baseline_cyclic(n_points=256, threads=None, pa66=False):
     """FP64 oracle's outer Newton on the host cores: the first increment of the
     cyclic workload on n_points points."""
@@ -699,11 +788,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                    help="uneven and cyclic workloads only")
+                    help="uneven, cyclic and linear (fp64 or fp32 laminates) workloads only")
     ap.add_argument("--matrix", default="perzyna", choices=["perzyna", "pa66"],
                     help="cyclic workload only: the matrix law")
     ap.add_argument("--workload", default="random_walk",
-                    choices=["random_walk", "uneven", "mlp", "large", "cyclic"])
+                    choices=["random_walk", "uneven", "mlp", "large", "cyclic", "linear"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -718,6 +807,9 @@ def main():
         return
     if args.workload == "cyclic":
         run_cyclic(args)
+        return
+    if args.workload == "linear":
+        run_linear(args)
         return
     if args.workload == "large":
         run_large(args)

@@ -75,6 +75,10 @@ SIGNATURES = {
     "dmn_eval_warm": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P]),
     "dmn_eval_mixed": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _D, _D, _I32, _D, _P, _P, _P, _P, _P,
                               _P, _P, _I32]),
+    # include/dmn_linear.h
+    "dmn_linear_forward": (_I32, [_P, _I32, _I64, _P, _P, _P, _P, _P, _I32]),
+    "dmn_linear_loss_grad": (_I32, [_P, _I32, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P, _I32]),
+    "dmn_linear_amsgrad": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _D, _D, _D, _D, _I64]),
 }
 
 

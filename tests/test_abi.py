@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every function include/dmn.h
+"""The C-ABI library builds, loads and exports every function include/*.h
 declares (no GPU needed: nothing here launches a kernel)."""
 import ctypes
 import os
@@ -24,7 +24,7 @@ def lib():
 
 
 def test_every_declared_symbol_is_exported(lib):
-    names = declared_functions("dmn.h") + declared_functions("dmn_mlp.h")
+    names = declared_functions("dmn.h") + declared_functions("dmn_mlp.h") + declared_functions("dmn_linear.h")
     assert "dmn_eval" in names and "dmn_create" in names
     for n in names:
         assert hasattr(lib, n), f"{n} declared in dmn.h but not exported"
@@ -32,7 +32,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_covers_the_headers():
     from paper_2109_14403_gb300 import dmn
-    assert set(declared_functions("dmn.h") + declared_functions("dmn_mlp.h")) == set(dmn.SIGNATURES)
+    assert set(declared_functions("dmn.h") + declared_functions("dmn_mlp.h")
+               + declared_functions("dmn_linear.h")) == set(dmn.SIGNATURES)
 
 
 def test_default_options_and_error_string(lib):

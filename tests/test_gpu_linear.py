@@ -1,0 +1,100 @@
+"""The linear homogenization function DMN^L and the gradient of the
+offline-training loss on the GPU (``dmn_linear_*`` through the C ABI) against
+the oracle (Milton's laminate formula, automatic differentiation in FP64).
+
+Tolerances.  FP64 kernels: the condensed laminate and Milton's formula agree to
+rounding, amplified by the conditioning of the 3x3 jump systems (stiffness
+contrast up to 100 here): 1e-10 relative for DMN^L, 1e-8 for J and the
+gradients (which add the 1/|C|_p and max-normalised q-norm steps).  FP32
+kernels: 2^-24 per operation, K levels deep, times the same conditioning:
+2e-4 for DMN^L and J, 5e-3 for the gradients (relative to their largest entry).
+"""
+import numpy as np
+import pytest
+
+import oracle.linear as olin
+from paper_2109_14403_gb300 import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(fwd=1e-10, loss=1e-8, grad=1e-8), "fp32": dict(fwd=2e-4, loss=2e-4, grad=5e-3)}
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=_dev())
+
+
+@pytest.mark.parametrize("K,n", [(1, 33), (3, 17), (5, 9), (8, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_forward_parity(K, n, prec):
+    from paper_2109_14403_gb300.linear import DMNLinear
+    normals, v = syn.linear_params(K, seed=K)
+    C1, C2 = syn.stiffness_pairs(n, seed=10 + K)
+    d = DMNLinear(K, normals, v, device=_dev())
+    out = d.forward(_t(C1), _t(C2), precision=prec).cpu().numpy()
+    ref = olin.forward(C1, C2, normals, v)
+    err = np.linalg.norm((out - ref).reshape(n, -1), axis=1) / np.linalg.norm(ref.reshape(n, -1), axis=1)
+    assert err.max() < TOL[prec]["fwd"], err.max()
+
+
+@pytest.mark.parametrize("K,p,q", [(2, 1.0, 10.0), (3, 1.0, 10.0), (4, 2.0, 2.0)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_loss_and_gradient_parity(K, p, q, prec):
+    from paper_2109_14403_gb300.linear import DMNLinear
+    normals, v = syn.linear_params(K, seed=20 + K)
+    v = v.copy()
+    v[1] = -0.03  # a dead leaf
+    tn, tv = syn.linear_params(K, seed=40 + K)
+    n = 12
+    C1, C2 = syn.stiffness_pairs(n, seed=30 + K)
+    Ct = olin.forward(C1, C2, tn, tv)
+    J, gn, gv = olin.loss_grad(C1, C2, Ct, normals, v, p=p, q=q, penalty=10.0)
+    d = DMNLinear(K, normals, v, device=_dev())
+    loss = d.loss_grad(_t(C1), _t(C2), _t(Ct), p=p, q=q, penalty=10.0, precision=prec).cpu().numpy()
+    g = d.grad.cpu().numpy()
+    t = TOL[prec]
+    assert abs(loss[0] - J) <= t["loss"] * abs(J)
+    gscale = max(np.abs(gn).max(), np.abs(gv).max())
+    assert np.abs(g[:3 * d.N].reshape(-1, 3) - gn).max() <= t["grad"] * gscale
+    assert np.abs(g[3 * d.N:] - gv).max() <= t["grad"] * gscale
+    assert g[3 * d.N + 1] == 0.0
+
+
+def test_training_reduces_the_loss():
+    """A depth-3 DMN^L fitted by AMSGrad to the stiffnesses of another one
+    (targets from the oracle): the loss falls by an order of magnitude."""
+    from paper_2109_14403_gb300.linear import DMNLinear
+    K = 3
+    tn, tv = syn.linear_params(K, seed=77)
+    C1, C2 = syn.stiffness_pairs(256, seed=78, log10_contrast=1.0)
+    Ct = olin.forward(C1, C2, tn, tv)
+    normals, v = syn.linear_params(K, seed=79)
+    d = DMNLinear(K, normals, v, device=_dev())
+    c1, c2, ct = _t(C1), _t(C2), _t(Ct)
+    first = float(d.loss_grad(c1, c2, ct, p=1.0, q=2.0, penalty=10.0)[0].item())
+    for it in range(400):
+        d.loss_grad(c1, c2, ct, p=1.0, q=2.0, penalty=10.0)
+        d.amsgrad_step(2e-2, 2e-3)
+    last = float(d.loss_grad(c1, c2, ct, p=1.0, q=2.0, penalty=10.0)[0].item())
+    assert np.isfinite(last) and last < 0.1 * first, (first, last)
+
+
+def test_argument_errors():
+    from paper_2109_14403_gb300 import dmn
+    from paper_2109_14403_gb300.linear import DMNLinear
+    d = DMNLinear(2, *syn.linear_params(2), device=_dev())
+    C1, C2 = syn.stiffness_pairs(2)
+    with pytest.raises(RuntimeError, match="p, q"):
+        d.loss_grad(_t(C1), _t(C2), _t(C1), p=0.5)
+    L = dmn.load()
+    assert L.dmn_linear_forward(None, 9, 1, 1, 1, 1, 1, 1, 0) == 1 and b"K must be" in L.dmn_last_error()
+    assert L.dmn_linear_forward(None, 2, 0, None, None, None, None, None, 7) == 1
+    assert b"precision" in L.dmn_last_error()
+    assert L.dmn_linear_amsgrad(None, 4, 1, 1, 1, 1, 1, 0.1, 0.9, 0.999, 1e-8, 0) == 1
