@@ -604,21 +604,22 @@ def run_cyclic(args):
 
 
 def lin_flops_per_sample(K):
-    """Algorithmic FLOPs of one training step per sample: two forward sweeps
-    (loss, then the backward's recomputation) at ~975 per laminate (U = D B,
-    M B, B^T M B, its inverse, U K^-1, the 21 outputs) and one reverse sweep at
-    ~2350 per laminate (the forward intermediates again, A, Q, the three inner
-    products, dJ/dB, B Q and the two child adjoints)."""
+    """Algorithmic FLOPs of one training step per sample: one forward sweep at
+    ~975 per laminate (U = D B, M B, B^T M B, its inverse, U K^-1, the 21
+    outputs) and one reverse sweep at ~2350 per laminate (the forward
+    intermediates again, A, Q, the three inner products, dJ/dB, B Q and the
+    two child adjoints)."""
     N = (1 << K) - 1
-    return N * (2 * 975 + 2350)
+    return N * (975 + 2350)
 
 
 def run_linear(args):
     """Offline training of DMN^L (Sec. 3.2) on synthetic stiffness triples: a
     K = 8 network, a batch of 65,536 samples (stiffness pairs with contrast up
     to 100 and a rank-one anisotropy; targets from another random K = 8
-    network); one step = loss J with its gradient (four launches) and the
-    AMSGrad update (two launches), FP32 laminate arithmetic."""
+    network); one step = loss J with its gradient (2K + 6 launches, level-
+    synchronous over the batch) and the AMSGrad update (two launches), FP32
+    laminate arithmetic."""
     import torch
 
     from paper_2109_14403_gb300 import synthetic as syn
@@ -675,9 +676,9 @@ def run_linear(args):
             "loss_before_after": losses,
             "roofline": {"bound": "alu", "achieved": fl, "peak": 73.2 if prec == "fp32" else 1.25,
                          "unit": "TFLOP/s", "frac": fl / (73.2 if prec == "fp32" else 1.25), "traffic": None,
-                         "kernel": f"k_lin_backward<{'float' if prec == 'fp32' else 'double'}> + "
-                                   "k_lin_forward (whole step)", "flops_per_sample": lin_flops_per_sample(K)},
-            "clocks": clk.summary(), "gpu_launches": 7 * steps}
+                         "kernel": f"k_lvl_bwd<{'float' if prec == 'fp32' else 'double'}> + "
+                                   "k_lvl_fwd (whole step)", "flops_per_sample": lin_flops_per_sample(K)},
+            "clocks": clk.summary(), "gpu_launches": (2 * K + 8) * steps}
     if not args.no_cpu_baseline and world == 1:
         import oracle.linear as olin
         m = 2

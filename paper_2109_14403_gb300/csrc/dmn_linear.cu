@@ -3,14 +3,15 @@
 // Sec. 3.2), for a batch of stiffness samples.  Declared in
 // include/dmn_linear.h.
 //
-// One CTA of G = 2^(K-1) threads per sample, persistent over the batch; the
-// laminates of a level run one per thread (node j of the level on thread j),
-// the levels one after another with a barrier.  Every node keeps its
-// stiffness in shared memory (packed symmetric, 21 words), so the backward
-// pass walks the tree top-down from them: per node it turns the adjoint G of
-// its stiffness into the adjoints of its two children and into dJ/dn and
-// dJ/dc1, which each thread sums over the samples its CTA processes (the
-// same thread always owns the same node) and adds to global FP64 sums once.
+// dmn_linear_forward: one CTA of G = 2^(K-1) threads per sample, persistent
+// over the batch; the laminates of a level run one per thread, the levels one
+// after another with a barrier, the node stiffnesses in shared memory.
+// dmn_linear_loss_grad: level-synchronous over the whole batch, one launch
+// per level and direction, every (sample, node) pair a thread, the node
+// stiffnesses and their adjoints in the caller's workspace; the backward pass
+// walks the tree top-down: per node it turns the adjoint G of its stiffness
+// into the adjoints of its two children and into dJ/dn and dJ/dc1, which each
+// block sums over its samples before one FP64 atomic add.
 // A laminate is computed in condensed form: with D = C_L - C_R, M = c2 C_L +
 // c1 C_R, U = D B, K = B^T M B,
 //   C = c1 C_L + c2 C_R - c1 c2 U K^-1 U^T,
@@ -203,21 +204,19 @@ __device__ void lam_backward(const T *CL, const T *CR, const T n[3], T c1, const
     }
 }
 
-// shared-memory carving (T words): normals 3N, c1 N, phases 42, nodes 21N,
-// adjoints 2 x 21G, per-node sums 4N
+// shared-memory carving of dmn_linear_forward (T words): normals 3N, c1 N,
+// phases 42, nodes 21N
 struct LinLayout {
-  int nh, c1, ph, ns, ga, acc, words;
+  int nh, c1, ph, ns, words;
 };
-__host__ __device__ inline LinLayout lin_layout(int K, bool backward) {
-  const int N = (1 << K) - 1, G = 1 << (K - 1);
+__host__ __device__ inline LinLayout lin_layout(int K) {
+  const int N = (1 << K) - 1;
   LinLayout L;
   L.nh = 0;
   L.c1 = L.nh + 3 * N;
   L.ph = L.c1 + N;
   L.ns = L.ph + 42;
-  L.ga = L.ns + 21 * N;
-  L.acc = L.ga + (backward ? 42 * G : 0);
-  L.words = L.acc + (backward ? 4 * N : 0);
+  L.words = L.ns + 21 * N;
   return L;
 }
 
@@ -308,7 +307,7 @@ __global__ void k_lin_forward(int K, int64_t n, const double *C1, const double *
                               double *err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
-  const LinLayout L = lin_layout(K, false);
+  const LinLayout L = lin_layout(K);
   const int N = (1 << K) - 1, root = N - 1;
   lin_constants<T>(K, normals, v, sm + L.nh, sm + L.c1, sm + L.ns);
   for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
@@ -363,76 +362,156 @@ __global__ void k_lin_reduce(int K, int64_t n, const double *err, const double *
   }
 }
 
+// ---- level-synchronous training pass over the whole batch.  Node values
+// live in the caller's workspace as [node][21][sample] (samples fastest, so a
+// warp's loads of one component are contiguous); one launch per level and
+// direction, a 2-D grid of (sample blocks, nodes of the level), so every
+// block serves one node and reduces its gradient terms before one atomic add.
+constexpr int kLvlThreads = 128;
+
 template <typename T>
-__global__ void k_lin_backward(int K, int64_t n, const double *C1, const double *C2, const double *normals,
-                               const double *v, const double *Ctarget, double p, double q,
-                               const double *err, const double *scal, double *gnh, double *gc1) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sm = reinterpret_cast<T *>(smem_raw);
-  const LinLayout L = lin_layout(K, true);
-  const int N = (1 << K) - 1, G = 1 << (K - 1), root = N - 1, t = threadIdx.x;
-  lin_constants<T>(K, normals, v, sm + L.nh, sm + L.c1, sm + L.ns);
-  T *acc = sm + L.acc;
-  for (int i = t; i < 4 * N; i += blockDim.x) acc[i] = T(0);
+__device__ __forceinline__ void lvl_load(const T *X, int p, int64_t n, int64_t s, T out[21]) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) out[q] = X[(int64_t(p) * 21 + q) * n + s];
+}
+template <typename T>
+__device__ __forceinline__ void lvl_store(T *X, int p, int64_t n, int64_t s, const T v[21]) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) X[(int64_t(p) * 21 + q) * n + s] = v[q];
+}
+template <typename T>
+__device__ __forceinline__ void phase_packed(const double *C, T out[21]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i; j < 6; ++j) out[sidx(i, j)] = T(0.5 * (C[6 * i + j] + C[6 * j + i]));
+}
+
+// normalised normals and c1 of every node (one CTA)
+__global__ void k_lvl_const(int K, const double *normals, const double *v, double *nh, double *c1s) {
+  __shared__ double Wt[2 * (1 << kLinMaxK)];
+  const int N = (1 << K) - 1, L = 1 << K, t = threadIdx.x;
+  for (int pp = t; pp < N; pp += blockDim.x) {
+    const double x = normals[3 * pp], y = normals[3 * pp + 1], z = normals[3 * pp + 2];
+    const double il = 1.0 / sqrt(x * x + y * y + z * z);
+    nh[3 * pp] = x * il;
+    nh[3 * pp + 1] = y * il;
+    nh[3 * pp + 2] = z * il;
+  }
+  for (int j = t; j < L; j += blockDim.x) Wt[j] = v[j] > 0.0 ? v[j] : 0.0;
   __syncthreads();
-  const double m = scal[0], cb = scal[1];
-  for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
-    load_phases<T>(C1 + 36 * s, C2 + 36 * s, sm + L.ph);
-    __syncthreads();
-    lin_sweep_up<T>(K, sm + L.nh, sm + L.c1, sm + L.ph, sm + L.ns);
-    // seed: dJ/dD = (1/N) S^(1/q-1) (e_s/m)^(q-1) de_s/dD
-    T *GA0 = sm + L.ga, *GA1 = GA0 + 21 * G;
-    if (t == 0) {
-      const double e = err[s];
-      const double coef = (m > 0.0 && e > 0.0) ? cb * pow(e / m, q - 1.0) : 0.0;
-      const T *D = sm + L.ns + 21 * root;
-      const double *Tg = Ctarget + 36 * s;
-      double num = 0.0, den = 0.0;
-      for (int i = 0; i < 36; ++i) {
-        num += pow(fabs(Tg[i] - double(sget(D, i / 6, i % 6))), p);
-        den += pow(fabs(Tg[i]), p);
-      }
-      const double nx = pow(num, 1.0 / p), nt = pow(den, 1.0 / p);
-      T *Gr = GA1;  // level 1 reads buffer 1
-      for (int i = 0; i < 6; ++i)
-        for (int j = i; j < 6; ++j) {
-          const double x = Tg[6 * i + j] - double(sget(D, i, j));
-          const double sg = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
-          const double de = nx > 0.0 ? -sg * pow(fabs(x), p - 1.0) * pow(nx, 1.0 - p) / nt : 0.0;
-          Gr[sidx(i, j)] = T(coef * de);
-        }
+  for (int k = K; k >= 1; --k) {
+    for (int i = t; i < (1 << (k - 1)); i += blockDim.x) {
+      const int pp = (1 << K) - (1 << k) + i;
+      const int pc = (1 << K) - (1 << (k + 1)) + 2 * i;
+      const double a = k == K ? Wt[2 * i] : Wt[L + pc], b = k == K ? Wt[2 * i + 1] : Wt[L + pc + 1];
+      const double W = a + b;
+      Wt[L + pp] = W;
+      c1s[pp] = W > 0.0 ? a / W : 0.5;
     }
     __syncthreads();
-    for (int k = 1; k <= K; ++k) {
-      const int cnt = 1 << (k - 1);
-      T *Gin = (k & 1) ? GA1 : GA0, *Gout = (k & 1) ? GA0 : GA1;
-      for (int j = t; j < cnt; j += blockDim.x) {
-        const int pp = (1 << K) - (1 << k) + j;
-        const T *CL, *CR;
-        if (k == K) {
-          CL = sm + L.ph;
-          CR = sm + L.ph + 21;
-        } else {
-          const int pc = (1 << K) - (1 << (k + 1)) + 2 * j;
-          CL = sm + L.ns + 21 * pc;
-          CR = sm + L.ns + 21 * (pc + 1);
-        }
-        T gn[3], g1;
-        lam_backward(CL, CR, sm + L.nh + 3 * pp, sm[L.c1 + pp], Gin + 21 * j, k < K ? Gout + 42 * j : nullptr,
-                     k < K ? Gout + 42 * j + 21 : nullptr, gn, g1);
-        acc[4 * pp] += gn[0];
-        acc[4 * pp + 1] += gn[1];
-        acc[4 * pp + 2] += gn[2];
-        acc[4 * pp + 3] += g1;
-      }
-      __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLvlThreads) k_lvl_fwd(int K, int k, int64_t n, const double *C1, const double *C2,
+                                                         const double *nh, const double *c1s, T *NS) {
+  const int64_t s = int64_t(blockIdx.x) * kLvlThreads + threadIdx.x;
+  if (s >= n) return;
+  const int j = blockIdx.y, pp = (1 << K) - (1 << k) + j;
+  T CL[21], CR[21], out[21];
+  if (k == K) {
+    phase_packed(C1 + 36 * s, CL);
+    phase_packed(C2 + 36 * s, CR);
+  } else {
+    const int pc = (1 << K) - (1 << (k + 1)) + 2 * j;
+    lvl_load(NS, pc, n, s, CL);
+    lvl_load(NS, pc + 1, n, s, CR);
+  }
+  const T nn[3] = {T(nh[3 * pp]), T(nh[3 * pp + 1]), T(nh[3 * pp + 2])};
+  lam_forward(CL, CR, nn, T(c1s[pp]), out);
+  lvl_store(NS, pp, n, s, out);
+}
+
+// per-sample error from the root column
+template <typename T>
+__global__ void k_lvl_err(int K, int64_t n, const T *NS, const double *Ct, double p, double *err) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  T D[21];
+  lvl_load(NS, (1 << K) - 2, n, s, D);
+  err[s] = lin_error<T>(Ct + 36 * s, D, p);
+}
+
+// dJ/dD at the root: (1/N) S^(1/q-1) (e_s/m)^(q-1) de_s/dD
+template <typename T>
+__global__ void k_lvl_seed(int K, int64_t n, const T *NS, const double *Ct, double p, double q, const double *err,
+                           const double *scal, T *GA) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int root = (1 << K) - 2;
+  T D[21], G[21];
+  lvl_load(NS, root, n, s, D);
+  const double m = scal[0], e = err[s];
+  const double coef = (m > 0.0 && e > 0.0) ? scal[1] * pow(e / m, q - 1.0) : 0.0;
+  const double *Tg = Ct + 36 * s;
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < 36; ++i) {
+    num += pow(fabs(Tg[i] - double(sget(D, i / 6, i % 6))), p);
+    den += pow(fabs(Tg[i]), p);
+  }
+  const double nx = pow(num, 1.0 / p), nt = pow(den, 1.0 / p);
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j) {
+      const double x = Tg[6 * i + j] - double(sget(D, i, j));
+      const double sg = x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0);
+      const double de = nx > 0.0 ? -sg * pow(fabs(x), p - 1.0) * pow(nx, 1.0 - p) / nt : 0.0;
+      G[sidx(i, j)] = T(coef * de);
+    }
+  lvl_store(GA, root, n, s, G);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLvlThreads) k_lvl_bwd(int K, int k, int64_t n, const double *C1, const double *C2,
+                                                         const double *nh, const double *c1s, const T *NS, T *GA,
+                                                         double *gnh, double *gc1) {
+  __shared__ double red[4][kLvlThreads / 32];
+  const int64_t s = int64_t(blockIdx.x) * kLvlThreads + threadIdx.x;
+  const int j = blockIdx.y, pp = (1 << K) - (1 << k) + j;
+  T gn[3] = {T(0), T(0), T(0)}, g1 = T(0);
+  if (s < n) {
+    T CL[21], CR[21], G[21], GL[21], GR[21];
+    const int pc = (1 << K) - (1 << (k + 1)) + 2 * j;
+    if (k == K) {
+      phase_packed(C1 + 36 * s, CL);
+      phase_packed(C2 + 36 * s, CR);
+    } else {
+      lvl_load(NS, pc, n, s, CL);
+      lvl_load(NS, pc + 1, n, s, CR);
+    }
+    lvl_load(GA, pp, n, s, G);
+    const T nn[3] = {T(nh[3 * pp]), T(nh[3 * pp + 1]), T(nh[3 * pp + 2])};
+    lam_backward(CL, CR, nn, T(c1s[pp]), G, k < K ? GL : nullptr, k < K ? GR : nullptr, gn, g1);
+    if (k < K) {
+      lvl_store(GA, pc, n, s, GL);
+      lvl_store(GA, pc + 1, n, s, GR);
     }
   }
-  for (int pp = t; pp < N; pp += blockDim.x) {
-    atomicAdd(gnh + 3 * pp, double(acc[4 * pp]));
-    atomicAdd(gnh + 3 * pp + 1, double(acc[4 * pp + 1]));
-    atomicAdd(gnh + 3 * pp + 2, double(acc[4 * pp + 2]));
-    atomicAdd(gc1 + pp, double(acc[4 * pp + 3]));
+  // block sums of dJ/dn and dJ/dc1 of this node, one atomic add each
+  double r[4] = {double(gn[0]), double(gn[1]), double(gn[2]), double(g1)};
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_down_sync(0xffffffffu, r[c], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[c][warp] = r[c];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+    for (int w = 0; w < kLvlThreads / 32; ++w) acc += red[threadIdx.x][w];
+    atomicAdd(threadIdx.x < 3 ? gnh + 3 * pp + threadIdx.x : gc1 + pp, acc);
   }
 }
 
@@ -553,7 +632,7 @@ template <typename T>
 dmn_status lin_forward(cudaStream_t st, int K, int64_t n, const double *C1, const double *C2,
                        const double *normals, const double *v, const double *Ct, double p, double *Cbar,
                        double *err) {
-  const size_t smem = sizeof(T) * lin_layout(K, false).words;
+  const size_t smem = sizeof(T) * lin_layout(K).words;
   const int threads = 1 << (K - 1);
   int grid = 0;
   cudaError_t e = lin_grid(k_lin_forward<T>, threads, smem, n, &grid);
@@ -563,17 +642,28 @@ dmn_status lin_forward(cudaStream_t st, int K, int64_t n, const double *C1, cons
   return DMN_OK;
 }
 
+// the training pass: forward by levels, errors, batch reduction, seed,
+// backward by levels; NS and GA in the workspace
 template <typename T>
-dmn_status lin_backward(cudaStream_t st, int K, int64_t n, const double *C1, const double *C2,
-                        const double *normals, const double *v, const double *Ct, double p, double q,
-                        const double *err, const double *scal, double *gnh, double *gc1) {
-  const size_t smem = sizeof(T) * lin_layout(K, true).words;
-  const int threads = 1 << (K - 1);
-  int grid = 0;
-  cudaError_t e = lin_grid(k_lin_backward<T>, threads, smem, n, &grid);
-  if (e != cudaSuccess) return lin_cuda(e, "dmn_linear: launch configuration");
-  k_lin_backward<T><<<grid, threads, smem, st>>>(K, n, C1, C2, normals, v, Ct, p, q, err, scal, gnh, gc1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: backward launch");
+dmn_status lin_train_pass(cudaStream_t st, int K, int64_t n, const double *C1, const double *C2,
+                          const double *Ct, const double *v, double p, double q, double penalty, double *err,
+                          double *scal, double *loss, const double *nh, const double *c1s, T *NS, T *GA,
+                          double *gnh, double *gc1) {
+  const unsigned nb = unsigned((n + kLvlThreads - 1) / kLvlThreads);
+  if (nb > 2147483647u) return lin_fail("dmn_linear_loss_grad: batch too large");
+  cudaError_t e;
+  for (int k = K; k >= 1; --k) {
+    k_lvl_fwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, C1, C2, nh, c1s, NS);
+    if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: forward level launch");
+  }
+  k_lvl_err<T><<<nb, kLvlThreads, 0, st>>>(K, n, NS, Ct, p, err);
+  k_lin_reduce<<<1, 1024, 0, st>>>(K, n, err, v, q, penalty, scal, loss);
+  k_lvl_seed<T><<<nb, kLvlThreads, 0, st>>>(K, n, NS, Ct, p, q, err, scal, GA);
+  if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: loss launch");
+  for (int k = 1; k <= K; ++k) {
+    k_lvl_bwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, C1, C2, nh, c1s, NS, GA, gnh, gc1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: backward level launch");
+  }
   return DMN_OK;
 }
 
@@ -611,18 +701,20 @@ extern "C" dmn_status dmn_linear_loss_grad(dmn_stream stream, int32_t K, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   const int N = (1 << K) - 1;
   double *err = d_work, *gnh = d_work + n_samples, *gc1 = gnh + 3 * N, *scal = gc1 + N;
+  double *nh = scal + 8, *c1s = nh + 3 * N, *nodes = c1s + N;
   k_lin_zero<<<8, 256, 0, st>>>(gnh, 4 * N + 8);
+  k_lvl_const<<<1, 256, 0, st>>>(K, d_normals, d_v, nh, c1s);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return lin_cuda(e, "dmn_linear: zero launch");
-  dmn_status s = precision == DMN_LIN_FP64
-                     ? lin_forward<double>(st, K, n_samples, d_C1, d_C2, d_normals, d_v, d_Ctarget, p, nullptr, err)
-                     : lin_forward<float>(st, K, n_samples, d_C1, d_C2, d_normals, d_v, d_Ctarget, p, nullptr, err);
-  if (s != DMN_OK) return s;
-  k_lin_reduce<<<1, 1024, 0, st>>>(K, n_samples, err, d_v, q, penalty, scal, d_loss);
-  if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: reduce launch");
-  s = precision == DMN_LIN_FP64
-          ? lin_backward<double>(st, K, n_samples, d_C1, d_C2, d_normals, d_v, d_Ctarget, p, q, err, scal, gnh, gc1)
-          : lin_backward<float>(st, K, n_samples, d_C1, d_C2, d_normals, d_v, d_Ctarget, p, q, err, scal, gnh, gc1);
+  if (e != cudaSuccess) return lin_cuda(e, "dmn_linear: set-up launch");
+  const int64_t cells = int64_t(21) * N * n_samples;
+  dmn_status s;
+  if (precision == DMN_LIN_FP64)
+    s = lin_train_pass<double>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_v, p, q, penalty, err, scal, d_loss,
+                               nh, c1s, nodes, nodes + cells, gnh, gc1);
+  else
+    s = lin_train_pass<float>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_v, p, q, penalty, err, scal, d_loss,
+                              nh, c1s, reinterpret_cast<float *>(nodes),
+                              reinterpret_cast<float *>(nodes) + cells, gnh, gc1);
   if (s != DMN_OK) return s;
   k_lin_finish<<<1, 32, 0, st>>>(K, d_normals, d_v, penalty, gnh, gc1, d_grad_n, d_grad_v);
   if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: finish launch");
