@@ -617,7 +617,7 @@ def run_linear(args):
     """Offline training of DMN^L (Sec. 3.2) on synthetic stiffness triples: a
     K = 8 network, a batch of 65,536 samples (stiffness pairs with contrast up
     to 100 and a rank-one anisotropy; targets from another random K = 8
-    network); one step = loss J with its gradient (2K + 6 launches, level-
+    network); one step = loss J with its gradient (2K + 7 launches, level-
     synchronous over the batch) and the AMSGrad update (two launches), FP32
     laminate arithmetic."""
     import torch
@@ -678,7 +678,7 @@ def run_linear(args):
                          "unit": "TFLOP/s", "frac": fl / (73.2 if prec == "fp32" else 1.25), "traffic": None,
                          "kernel": f"k_lvl_bwd<{'float' if prec == 'fp32' else 'double'}> + "
                                    "k_lvl_fwd (whole step)", "flops_per_sample": lin_flops_per_sample(K)},
-            "clocks": clk.summary(), "gpu_launches": (2 * K + 8) * steps}
+            "clocks": clk.summary(), "gpu_launches": (2 * K + 9) * steps}
     if not args.no_cpu_baseline and world == 1:
         import oracle.linear as olin
         m = 2

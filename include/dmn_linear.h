@@ -54,14 +54,15 @@ dmn_status dmn_linear_forward(dmn_stream stream, int32_t K, int64_t n_samples, c
  *   d_loss     3 doubles: J, its data term, its penalty term
  *   d_grad_n   (2^K - 1) x 3 doubles: dJ / d normals (through the normalisation)
  *   d_grad_v   2^K doubles: dJ / dv (zero where v_j < 0)
- *   d_work     scratch of n_samples + 8 (2^K - 1) + 8 doubles, then the node
- *              stiffnesses and their adjoints: 42 (2^K - 1) n_samples words of
- *              the laminate precision (doubles for DMN_LIN_FP64, floats for
- *              DMN_LIN_FP32), 2.8 GB at K = 8, 65,536 samples, FP32
+ *   d_work     scratch of n_samples + 8 (2^K - 1) + 8 doubles, then the packed
+ *              phase stiffnesses, the node stiffnesses and their adjoints:
+ *              42 2^K n_samples words of the laminate precision (doubles for
+ *              DMN_LIN_FP64, floats for DMN_LIN_FP32), 2.8 GB at K = 8,
+ *              65,536 samples, FP32
  * The gradient is exact for the forward computation (reverse mode through
  * every laminate).  Level-synchronous over the batch: K forward launches,
  * errors, batch reduction, seed, K backward launches, the chain through the
- * weights (2K + 6 launches).
+ * weights (2K + 7 launches).
  */
 dmn_status dmn_linear_loss_grad(dmn_stream stream, int32_t K, int64_t n_samples, const double *d_C1,
                                 const double *d_C2, const double *d_Ctarget, const double *d_normals,

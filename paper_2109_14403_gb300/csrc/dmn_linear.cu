@@ -387,16 +387,17 @@ __device__ __forceinline__ void phase_packed(const double *C, T out[21]) {
     for (int j = i; j < 6; ++j) out[sidx(i, j)] = T(0.5 * (C[6 * i + j] + C[6 * j + i]));
 }
 
-// normalised normals and c1 of every node (one CTA)
-__global__ void k_lvl_const(int K, const double *normals, const double *v, double *nh, double *c1s) {
+// normalised normals and c1 of every node in the laminate precision (one CTA)
+template <typename T>
+__global__ void k_lvl_const(int K, const double *normals, const double *v, T *nh, T *c1s) {
   __shared__ double Wt[2 * (1 << kLinMaxK)];
   const int N = (1 << K) - 1, L = 1 << K, t = threadIdx.x;
   for (int pp = t; pp < N; pp += blockDim.x) {
     const double x = normals[3 * pp], y = normals[3 * pp + 1], z = normals[3 * pp + 2];
     const double il = 1.0 / sqrt(x * x + y * y + z * z);
-    nh[3 * pp] = x * il;
-    nh[3 * pp + 1] = y * il;
-    nh[3 * pp + 2] = z * il;
+    nh[3 * pp] = T(x * il);
+    nh[3 * pp + 1] = T(y * il);
+    nh[3 * pp + 2] = T(z * il);
   }
   for (int j = t; j < L; j += blockDim.x) Wt[j] = v[j] > 0.0 ? v[j] : 0.0;
   __syncthreads();
@@ -407,29 +408,42 @@ __global__ void k_lvl_const(int K, const double *normals, const double *v, doubl
       const double a = k == K ? Wt[2 * i] : Wt[L + pc], b = k == K ? Wt[2 * i + 1] : Wt[L + pc + 1];
       const double W = a + b;
       Wt[L + pp] = W;
-      c1s[pp] = W > 0.0 ? a / W : 0.5;
+      c1s[pp] = T(W > 0.0 ? a / W : 0.5);
     }
     __syncthreads();
   }
 }
 
+// the phase stiffnesses of every sample, packed, in the laminate precision:
+// PH[phase][21][sample] (converted once instead of by every bottom laminate)
 template <typename T>
-__global__ void __launch_bounds__(kLvlThreads) k_lvl_fwd(int K, int k, int64_t n, const double *C1, const double *C2,
-                                                         const double *nh, const double *c1s, T *NS) {
+__global__ void k_lvl_phases(int64_t n, const double *C1, const double *C2, T *PH) {
+  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  T a[21], b[21];
+  phase_packed(C1 + 36 * s, a);
+  phase_packed(C2 + 36 * s, b);
+  lvl_store(PH, 0, n, s, a);
+  lvl_store(PH, 1, n, s, b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLvlThreads) k_lvl_fwd(int K, int k, int64_t n, const T *PH, const T *nh,
+                                                         const T *c1s, T *NS) {
   const int64_t s = int64_t(blockIdx.x) * kLvlThreads + threadIdx.x;
   if (s >= n) return;
   const int j = blockIdx.y, pp = (1 << K) - (1 << k) + j;
   T CL[21], CR[21], out[21];
   if (k == K) {
-    phase_packed(C1 + 36 * s, CL);
-    phase_packed(C2 + 36 * s, CR);
+    lvl_load(PH, 0, n, s, CL);
+    lvl_load(PH, 1, n, s, CR);
   } else {
     const int pc = (1 << K) - (1 << (k + 1)) + 2 * j;
     lvl_load(NS, pc, n, s, CL);
     lvl_load(NS, pc + 1, n, s, CR);
   }
-  const T nn[3] = {T(nh[3 * pp]), T(nh[3 * pp + 1]), T(nh[3 * pp + 2])};
-  lam_forward(CL, CR, nn, T(c1s[pp]), out);
+  const T nn[3] = {nh[3 * pp], nh[3 * pp + 1], nh[3 * pp + 2]};
+  lam_forward(CL, CR, nn, c1s[pp], out);
   lvl_store(NS, pp, n, s, out);
 }
 
@@ -472,10 +486,10 @@ __global__ void k_lvl_seed(int K, int64_t n, const T *NS, const double *Ct, doub
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kLvlThreads) k_lvl_bwd(int K, int k, int64_t n, const double *C1, const double *C2,
-                                                         const double *nh, const double *c1s, const T *NS, T *GA,
-                                                         double *gnh, double *gc1) {
-  __shared__ double red[4][kLvlThreads / 32];
+__global__ void __launch_bounds__(kLvlThreads) k_lvl_bwd(int K, int k, int64_t n, const T *PH, const T *nh,
+                                                         const T *c1s, const T *NS, T *GA, double *gnh,
+                                                         double *gc1) {
+  __shared__ T red[4][kLvlThreads / 32];
   const int64_t s = int64_t(blockIdx.x) * kLvlThreads + threadIdx.x;
   const int j = blockIdx.y, pp = (1 << K) - (1 << k) + j;
   T gn[3] = {T(0), T(0), T(0)}, g1 = T(0);
@@ -483,22 +497,23 @@ __global__ void __launch_bounds__(kLvlThreads) k_lvl_bwd(int K, int k, int64_t n
     T CL[21], CR[21], G[21], GL[21], GR[21];
     const int pc = (1 << K) - (1 << (k + 1)) + 2 * j;
     if (k == K) {
-      phase_packed(C1 + 36 * s, CL);
-      phase_packed(C2 + 36 * s, CR);
+      lvl_load(PH, 0, n, s, CL);
+      lvl_load(PH, 1, n, s, CR);
     } else {
       lvl_load(NS, pc, n, s, CL);
       lvl_load(NS, pc + 1, n, s, CR);
     }
     lvl_load(GA, pp, n, s, G);
-    const T nn[3] = {T(nh[3 * pp]), T(nh[3 * pp + 1]), T(nh[3 * pp + 2])};
-    lam_backward(CL, CR, nn, T(c1s[pp]), G, k < K ? GL : nullptr, k < K ? GR : nullptr, gn, g1);
+    const T nn[3] = {nh[3 * pp], nh[3 * pp + 1], nh[3 * pp + 2]};
+    lam_backward(CL, CR, nn, c1s[pp], G, k < K ? GL : nullptr, k < K ? GR : nullptr, gn, g1);
     if (k < K) {
       lvl_store(GA, pc, n, s, GL);
       lvl_store(GA, pc + 1, n, s, GR);
     }
   }
-  // block sums of dJ/dn and dJ/dc1 of this node, one atomic add each
-  double r[4] = {double(gn[0]), double(gn[1]), double(gn[2]), double(g1)};
+  // block sums of dJ/dn and dJ/dc1 of this node (laminate precision), one
+  // FP64 atomic add each
+  T r[4] = {gn[0], gn[1], gn[2], g1};
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -509,9 +524,9 @@ __global__ void __launch_bounds__(kLvlThreads) k_lvl_bwd(int K, int k, int64_t n
     for (int c = 0; c < 4; ++c) red[c][warp] = r[c];
   __syncthreads();
   if (threadIdx.x < 4) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int w = 0; w < kLvlThreads / 32; ++w) acc += red[threadIdx.x][w];
-    atomicAdd(threadIdx.x < 3 ? gnh + 3 * pp + threadIdx.x : gc1 + pp, acc);
+    atomicAdd(threadIdx.x < 3 ? gnh + 3 * pp + threadIdx.x : gc1 + pp, double(acc));
   }
 }
 
@@ -646,14 +661,19 @@ dmn_status lin_forward(cudaStream_t st, int K, int64_t n, const double *C1, cons
 // backward by levels; NS and GA in the workspace
 template <typename T>
 dmn_status lin_train_pass(cudaStream_t st, int K, int64_t n, const double *C1, const double *C2,
-                          const double *Ct, const double *v, double p, double q, double penalty, double *err,
-                          double *scal, double *loss, const double *nh, const double *c1s, T *NS, T *GA,
+                          const double *Ct, const double *normals, const double *v, double p, double q,
+                          double penalty, double *err, double *scal, double *loss, T *consts, T *PH, T *NS, T *GA,
                           double *gnh, double *gc1) {
   const unsigned nb = unsigned((n + kLvlThreads - 1) / kLvlThreads);
   if (nb > 2147483647u) return lin_fail("dmn_linear_loss_grad: batch too large");
-  cudaError_t e;
+  const int N = (1 << K) - 1;
+  T *nh = consts, *c1s = consts + 3 * N;
+  k_lvl_const<T><<<1, 256, 0, st>>>(K, normals, v, nh, c1s);
+  k_lvl_phases<T><<<nb, kLvlThreads, 0, st>>>(n, C1, C2, PH);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return lin_cuda(e, "dmn_linear: set-up launch");
   for (int k = K; k >= 1; --k) {
-    k_lvl_fwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, C1, C2, nh, c1s, NS);
+    k_lvl_fwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, PH, nh, c1s, NS);
     if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: forward level launch");
   }
   k_lvl_err<T><<<nb, kLvlThreads, 0, st>>>(K, n, NS, Ct, p, err);
@@ -661,7 +681,7 @@ dmn_status lin_train_pass(cudaStream_t st, int K, int64_t n, const double *C1, c
   k_lvl_seed<T><<<nb, kLvlThreads, 0, st>>>(K, n, NS, Ct, p, q, err, scal, GA);
   if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: loss launch");
   for (int k = 1; k <= K; ++k) {
-    k_lvl_bwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, C1, C2, nh, c1s, NS, GA, gnh, gc1);
+    k_lvl_bwd<T><<<dim3(nb, 1u << (k - 1)), kLvlThreads, 0, st>>>(K, k, n, PH, nh, c1s, NS, GA, gnh, gc1);
     if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: backward level launch");
   }
   return DMN_OK;
@@ -701,20 +721,20 @@ extern "C" dmn_status dmn_linear_loss_grad(dmn_stream stream, int32_t K, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   const int N = (1 << K) - 1;
   double *err = d_work, *gnh = d_work + n_samples, *gc1 = gnh + 3 * N, *scal = gc1 + N;
-  double *nh = scal + 8, *c1s = nh + 3 * N, *nodes = c1s + N;
+  double *consts = scal + 8, *nodes = consts + 4 * N;
   k_lin_zero<<<8, 256, 0, st>>>(gnh, 4 * N + 8);
-  k_lvl_const<<<1, 256, 0, st>>>(K, d_normals, d_v, nh, c1s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return lin_cuda(e, "dmn_linear: set-up launch");
-  const int64_t cells = int64_t(21) * N * n_samples;
+  const int64_t cells = int64_t(21) * N * n_samples, ph = int64_t(42) * n_samples;
   dmn_status s;
   if (precision == DMN_LIN_FP64)
-    s = lin_train_pass<double>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_v, p, q, penalty, err, scal, d_loss,
-                               nh, c1s, nodes, nodes + cells, gnh, gc1);
-  else
-    s = lin_train_pass<float>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_v, p, q, penalty, err, scal, d_loss,
-                              nh, c1s, reinterpret_cast<float *>(nodes),
-                              reinterpret_cast<float *>(nodes) + cells, gnh, gc1);
+    s = lin_train_pass<double>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_normals, d_v, p, q, penalty, err, scal,
+                               d_loss, consts, nodes, nodes + ph, nodes + ph + cells, gnh, gc1);
+  else {
+    float *f = reinterpret_cast<float *>(nodes);
+    s = lin_train_pass<float>(st, K, n_samples, d_C1, d_C2, d_Ctarget, d_normals, d_v, p, q, penalty, err, scal,
+                              d_loss, reinterpret_cast<float *>(consts), f, f + ph, f + ph + cells, gnh, gc1);
+  }
   if (s != DMN_OK) return s;
   k_lin_finish<<<1, 32, 0, st>>>(K, d_normals, d_v, penalty, gnh, gc1, d_grad_n, d_grad_v);
   if ((e = cudaGetLastError()) != cudaSuccess) return lin_cuda(e, "dmn_linear: finish launch");

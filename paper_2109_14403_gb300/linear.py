@@ -74,7 +74,7 @@ class DMNLinear:
         import torch
         self._check_batch(C1, C2, Ctarget)
         n = C1.shape[0]
-        cells = 42 * self.N * n  # node stiffnesses and adjoints
+        cells = 42 * (self.N + 1) * n  # packed phases, node stiffnesses and adjoints
         need = n + 8 * self.N + 8 + (cells if precision == "fp64" else (cells + 1) // 2)
         if self._work is None or self._work.numel() < need:
             self._work = torch.empty(need, dtype=torch.float64, device=C1.device)
