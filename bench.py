@@ -190,22 +190,27 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(n_points=1024, n_incr=2, threads=None):
+def cpu_baseline(n_points=1024, n_incr=2, threads=None, ramp=False):
     """FP64 oracle on the host cores: the first n_incr increments of the same
-    K=8 random walk on n_points points (its own trajectory)."""
+    K=8 load path (random walk, or the plastic ramp) on n_points points (its
+    own trajectory)."""
     import oracle
     from paper_2109_14403_gb300 import synthetic as syn
     threads = threads or os.cpu_count() or 1
     w, nrm, ph = syn.tree(K_DEPTH)
     tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials())
-    deps, theta = syn.random_walk_k8(n_points=n_points, n_incr=n_incr)
+    if ramp:
+        deps, theta = syn.ramp_k4(n_points=n_points, n_incr=n_incr)
+    else:
+        deps, theta = syn.random_walk_k8(n_points=n_points, n_incr=n_incr)
     s = tree.init_state(n_points, syn.THETA_START)
     t0 = time.perf_counter()
     for k in range(n_incr):
         s, out, st, it = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
     dt = time.perf_counter() - t0
+    path = "plastic ramp" if ramp else "random walk"
     return {"value": n_points * n_incr / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 random walk, tol {TOL}"}
+            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 {path}, tol {TOL}"}
 
 
 def run_reference(args):
@@ -793,7 +798,7 @@ def main():
     ap.add_argument("--matrix", default="perzyna", choices=["perzyna", "pa66"],
                     help="cyclic workload only: the matrix law")
     ap.add_argument("--workload", default="random_walk",
-                    choices=["random_walk", "uneven", "mlp", "large", "cyclic", "linear"])
+                    choices=["random_walk", "plastic", "uneven", "mlp", "large", "cyclic", "linear"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -836,7 +841,11 @@ def main():
     n_gen = 6  # increments of the FP64 solver that produce the training pairs
     first = n_gen + warm  # first timed increment
     n_incr = first + steps
-    deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=n_incr, seed=42 + rank)
+    plastic = args.workload == "plastic"
+    if plastic:  # the K = 4 configuration's ramp on the K = 8 batch: the matrix flows
+        deps_h, theta_h = syn.ramp_k4(n_points=n, n_incr=n_incr, seed=42 + rank)
+    else:
+        deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=n_incr, seed=42 + rank)
     D = torch.tensor(deps_h, device=dev)
     T = torch.tensor(theta_h, device=dev)
 
@@ -1008,13 +1017,15 @@ def main():
             "flops_per_pass": alu_flops_per_pass(K_DEPTH), "passes_per_eval": passes,
             "hbm": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s", "frac": hbm_achieved / peak,
                     "peak_source": how, "bytes_per_eval": bpe}}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+    line = {"metric": METRIC + (", plastic ramp" if plastic else ""), "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": steps,
             "warmup": warm, "ms_per_step": t_max / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 + float-float (2xf32) + bf16 MLP",
             "data": "synthetic",
-            "config": {"workload": f"K={K_DEPTH} DMN, {n} Gauss points per GPU, random-walk increments "
-                                   f"{first}-{first + steps - 1}",
+            "config": {"workload": f"K={K_DEPTH} DMN, {n} Gauss points per GPU, "
+                                   + ("plastic ramp (0.1 % in 11 + N(0, 1e-4), +3 K) increments " if plastic
+                                      else "random-walk increments ") + f"{first}-{first + steps - 1}",
                        "path": "mixed precision + learned warm start (MLP inference in the step)",
                        "tol": TOL, "points_per_gpu": n,
                        "l2": "inputs larger than L2 (device state ~0.9 GB)",
@@ -1026,7 +1037,7 @@ def main():
             "solve_kernel_ms": solve_ms,
             "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 6 * steps}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(ramp=plastic)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
