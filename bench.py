@@ -132,18 +132,29 @@ SOLVE_SOURCES = ("dfl.cuh", "dmn_internal.h", "dmn_kernels.cuh", "dmn_solve_comp
                  "solve_common.cuh", "solve_compact.cuh")
 
 
-def kernel_source_hash():
-    """SHA-256 over the sources the headline solve kernel is compiled from
-    (file names and bytes, and the public header they include)."""
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed: a change of
+    comments leaves the compiled kernel, and so this text, the same."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_hash(read=None):
+    """SHA-256 over the code (comments stripped) of the sources the headline
+    solve kernel is compiled from, and of the public header they include.
+    read(path relative to the repository) -> text; default: the working tree."""
     import hashlib
+    if read is None:
+        def read(rel):
+            with open(os.path.join(ROOT, rel)) as fh:
+                return fh.read()
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2109_14403_gb300", "csrc")
     for f in SOLVE_SOURCES:
         h.update(f.encode())
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
-    with open(os.path.join(ROOT, "include", "dmn.h"), "rb") as fh:
-        h.update(fh.read())
+        h.update(_code_only(read("paper_2109_14403_gb300/csrc/" + f)).encode())
+    h.update(_code_only(read("include/dmn.h")).encode())
     return h.hexdigest()
 
 

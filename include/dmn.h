@@ -231,7 +231,9 @@ dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points, const dou
  * array that is part of the library (64 KiB per GPU, held by every GPU that
  * loads the library until the process exits) and then runs the same solve as
  * dmn_eval; the caller's inputs, outputs and state are as in dmn_eval.
- *   Limit: K <= 8; larger trees are rejected with DMN_ERR_ARG.
+ *   Limit: K <= 8; larger trees, and trees with PA66 leaves (which need the
+ *   per-leaf history offsets a dmn_handle keeps), are rejected with
+ *   DMN_ERR_ARG.
  *   The first call on a device looks up the device address of that array
  *   (with the device current); make that first call before any stream
  *   capture.  The host-to-device copies of the tables are ordinary
