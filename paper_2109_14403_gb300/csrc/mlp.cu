@@ -52,6 +52,7 @@ int g_gemm_configured_dev = -1;
 // C = A . B^T with the fused epilogue ep; A [M x K], B [N x K] bf16
 cudaError_t gemm(cudaStream_t s, const void *A, const void *B, int M, int N, int K, EpiArgs ep) {
   if (M % BM || N % BN || K % BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if (M / BM > 65535 || N / BN > 65535) return cudaErrorInvalidValue;  // grid limits
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
@@ -64,7 +65,7 @@ cudaError_t gemm(cudaStream_t s, const void *A, const void *B, int M, int N, int
   }
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) return cudaErrorInvalidValue;
-  gemm_bf16_tn<<<dim3(M / BM, N / BN), 128, GEMM_SMEM, s>>>(ma, mb, K, ep);
+  gemm_bf16_tn<<<dim3(N / BN, M / BM), 128, GEMM_SMEM, s>>>(ma, mb, K, ep);
   return cudaGetLastError();
 }
 

@@ -2,8 +2,8 @@
 //   C[M x N] = A[M x K] . B[N x K]^T   (A, B bf16 with K contiguous; FP32
 //   accumulation in tensor memory), followed by a fused epilogue.
 //
-// One CTA of 128 threads computes a 128 x 128 tile; two CTAs share an SM, so
-// one's epilogue overlaps the other's MMAs:
+// One CTA of 128 threads computes a 128 x 128 tile (grid: column tiles fastest);
+// two CTAs share an SM, so one's epilogue overlaps the other's MMAs:
 //   warp 0, lane 0  loads A and B tiles (64 wide in K) with TMA bulk tensor
 //                   copies into a 3-stage ring of 128-byte-swizzled shared
 //                   memory, signalled by mbarriers with transaction counts;
@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(128, 2)
   int *fail = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // column tiles fastest: the CTAs that share an A panel run together and
+  // read it from L2 (the A panel of a 65,536-row batch is larger than L2)
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nk = K / BK;
 
   if (threadIdx.x == 0) {
