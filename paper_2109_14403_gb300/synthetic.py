@@ -201,9 +201,10 @@ def stiffness_pairs(n_samples, seed=7, log10_contrast=2.0):
     """Phase stiffness pairs for offline training (stand-in for the paper's
     sampled 8-D set, Sec. 5.1): C_1 isotropic with E_1 = 1, C_2 isotropic with
     E_2 = 10^U(-c, c), both nu ~ U(0.1, 0.45); C_2 loses a random rank-one
-    part (a fraction U(0, 0.5) of its smallest-eigenvalue direction is not
-    removed: C_2 - t (m^T C_2 m) m m^T with unit m, t ~ U(0, 0.5)), so it is
-    anisotropic but positive definite.  Returns C1s, C2s [n, 6, 6]."""
+    part, C_2 - t m m^T / (m^T C_2^-1 m) with unit m and t ~ U(0, 0.5), which
+    keeps it positive definite (the largest rank-one reduction along m that
+    does is t = 1), so it is anisotropic with a smallest eigenvalue at least
+    half the isotropic one along m.  Returns C1s, C2s [n, 6, 6]."""
     rng = np.random.default_rng(seed)
     C1 = iso_mandel(np.ones(n_samples), rng.uniform(0.1, 0.45, n_samples))
     C2 = iso_mandel(10.0 ** rng.uniform(-log10_contrast, log10_contrast, n_samples),
@@ -211,8 +212,8 @@ def stiffness_pairs(n_samples, seed=7, log10_contrast=2.0):
     m = rng.standard_normal((n_samples, 6))
     m /= np.linalg.norm(m, axis=1, keepdims=True)
     t = rng.uniform(0.0, 0.5, n_samples)
-    mCm = np.einsum("si,sij,sj->s", m, C2, m)
-    C2 = C2 - (t * mCm)[:, None, None] * np.einsum("si,sj->sij", m, m)
+    mCim = np.einsum("si,si->s", m, np.linalg.solve(C2, m[:, :, None])[:, :, 0])
+    C2 = C2 - (t / mCim)[:, None, None] * np.einsum("si,sj->sij", m, m)
     return C1, C2
 
 

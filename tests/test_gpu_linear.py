@@ -98,3 +98,38 @@ def test_argument_errors():
     assert L.dmn_linear_forward(None, 2, 0, None, None, None, None, None, 7) == 1
     assert b"precision" in L.dmn_last_error()
     assert L.dmn_linear_amsgrad(None, 4, 1, 1, 1, 1, 1, 0.1, 0.9, 0.999, 1e-8, 0) == 1
+
+
+def test_full_batch_forward_sampled_and_directional_gradient():
+    """The benchmark's size (K = 8, 65,536 samples): DMN^L of four sampled
+    samples against the oracle, and the FP64 gradient against a central
+    difference of the FP64 loss along a random direction of all parameters
+    (a property that holds at any batch size)."""
+    from paper_2109_14403_gb300.linear import DMNLinear
+    K, n = 8, 65536
+    C1h, C2h = syn.stiffness_pairs(n, seed=7)
+    c1, c2 = _t(C1h), _t(C2h)
+    teacher = DMNLinear(K, *syn.linear_params(K, seed=101), device=_dev())
+    ct = teacher.forward(c1, c2, precision="fp64")
+    normals, v = syn.linear_params(K, seed=102)
+    d = DMNLinear(K, normals, v, device=_dev())
+    out = d.forward(c1, c2, precision="fp32").cpu().numpy()
+    idx = [0, 12345, 40000, n - 1]
+    ref = olin.forward(C1h[idx], C2h[idx], normals, v)
+    err = np.linalg.norm((out[idx] - ref).reshape(4, -1), axis=1) / np.linalg.norm(ref.reshape(4, -1), axis=1)
+    assert err.max() < TOL["fp32"]["fwd"]
+    d.loss_grad(c1, c2, ct, p=1.0, q=10.0, penalty=1e3, precision="fp64")
+    g = d.grad.clone()
+    rng = np.random.default_rng(5)
+    direction = torch.tensor(rng.standard_normal(d.params.numel()), device=_dev())
+    direction[3 * d.N:] *= 1e-2  # weights are O(1/2^K)
+    x0 = d.params.clone()
+    h = 1e-6
+    vals = []
+    for sgn in (1.0, -1.0):
+        d.params.copy_(x0 + sgn * h * direction)
+        vals.append(float(d.loss_grad(c1, c2, ct, p=1.0, q=10.0, penalty=1e3, precision="fp64")[0].item()))
+    d.params.copy_(x0)
+    fd = (vals[0] - vals[1]) / (2 * h)
+    an = float((g * direction).sum().item())
+    assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-6), (fd, an)

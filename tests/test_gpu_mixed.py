@@ -210,15 +210,16 @@ def test_cyclic_self_heating_path(prec, matrix, predict):
     d.close()
 
 
-@pytest.mark.parametrize("prec", ["mixed"])
-def test_cyclic_full_batch_sampled(prec):
-    """65,536 points on a K = 8 tree (the benchmark's cyclic workload), three
-    increments; the oracle follows 32 sampled points."""
+@pytest.mark.parametrize("prec,matrix", [("mixed", "perzyna"), ("mixed", "pa66")])
+def test_cyclic_full_batch_sampled(prec, matrix):
+    """65,536 points on a K = 8 tree (the benchmark's cyclic workload, with
+    either matrix), three increments; the oracle follows sampled points."""
     dev = _dev()
-    d, tree, c = make(8, syn.materials_cyclic(), prec)
+    mats = syn.materials_pa66() if matrix == "pa66" else syn.materials_cyclic()
+    d, tree, c = make(8, mats, prec)
     n = 65536
     mask, target, dt, amp, direction = syn.cyclic_stress(n, 1, seed=42)
-    idx = np.linspace(0, n - 1, 32).astype(int)
+    idx = np.linspace(0, n - 1, 8 if matrix == "pa66" else 32).astype(int)
     idx_d = torch.tensor(idx, device=dev)
     s = d.init_state(torch.full((n,), TH0, dtype=torch.float64, device=dev))
     so = tree.init_state(idx.size, TH0)
