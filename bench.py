@@ -219,9 +219,17 @@ def cpu_baseline(n_points=1024, n_incr=2, threads=None, ramp=False):
     for k in range(n_incr):
         s, out, st, it = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
     dt = time.perf_counter() - t0
+    # the same on one core, a smaller sample
+    m1 = max(n_points // 16, 1)
+    s1 = tree.init_state(m1, syn.THETA_START)
+    t1 = time.perf_counter()
+    for k in range(n_incr):
+        s1, _, _, _ = oracle.eval_batch(tree, deps[k][:m1], theta[k][:m1], 1.0, s1, tol=TOL, threads=1)
+    dt1 = time.perf_counter() - t1
     path = "plastic ramp" if ramp else "random walk"
     return {"value": n_points * n_incr / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 {path}, tol {TOL}"}
+            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 {path}, tol {TOL}",
+            "one_core": {"value": m1 * n_incr / dt1, "sample": f"{m1} points, same increments"}}
 
 
 def run_reference(args):
@@ -906,13 +914,19 @@ def main():
     da = torch.empty((n, net.n_out), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    nvtx = torch.cuda.nvtx  # ranges for profilers that filter on them (ncu --nvtx)
+
     def warm_step(k, it_out, ev=None):
         p, c, nx = bufs
+        nvtx.range_push("warm start")
         net.input(D[k], T[k], c, p, out=xin)
         net.predict(xin, out=da)
+        nvtx.range_pop()
         if ev is not None:
             ev[0].record(stream)
+        nvtx.range_push("solve")
         mixed.eval_warm(D[k], T[k], 1.0, c, da, nx, out, st, it_out)
+        nvtx.range_pop()
         if ev is not None:
             ev[1].record(stream)
         bufs[0], bufs[1], bufs[2] = c, nx, p
