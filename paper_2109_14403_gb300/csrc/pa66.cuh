@@ -48,6 +48,10 @@ struct MatPA {
   TF L, Avv, Add, Av_f, Ad_f, Ke_f, G2e_f, G3e_f, Kc_f, KK_f, sy_f, c_f, Hk_f, nh, b1, b2;
   TF alpha_f, theta_f, idt_f, a3th_idt_f;
   int m, nb;
+  // static, per branch: K_i, G_i, K_i / (tau_i E_i), G_i / (tau_i E_i) (HP);
+  // per material: K_inf, G_inf, sum K_i
+  HP Kst[kPaBranches], Gst[kPaBranches], kvs[kPaBranches], gvs[kPaBranches];
+  HP Kinf, Ginf, KKst;
 };
 
 template <typename T>
@@ -62,61 +66,84 @@ __device__ __forceinline__ double pa_hard(double Hk, double p, double n) {
   return p > 0.0 ? Hk * exp(n * log(p)) : 0.0;
 }
 
-// the per-point constants, one thread per material, in FP64
+// static constants of a PA66 material (once per CTA, FP64 then HP)
 template <typename TF, typename HP>
-__device__ void mat_point_pa(MatPA<TF, HP> &o, const MatDev &m, double theta, double dt) {
+__device__ void mat_static_pa(MatPA<TF, HP> &o, const MatDev &m) {
   HP *tag = nullptr;
-  const double Kinf = m.Kb, Ginf = m.G, nu = m.pa[3];
-  const double x = theta - m.pa[0], C1 = m.pa[1], C2 = m.pa[2];
-  const double ln10 = 2.30258509299404568402;
-  const double a = exp(-ln10 * C1 * x / (C2 + x));
-  const double L = -ln10 * C1 * C2 / ((C2 + x) * (C2 + x));  // d ln a / d theta
-  const double g1 = exp(-m.cE * x), g2 = exp(-m.pad_ * x);
-  const double sy = g1 * m.sy0, eta = g2 * m.itv;
-  double Ke = Kinf, Ge = Ginf, KK = Kinf, Kc = 0.0, Av = 0.0, Ad = 0.0, Avv = 0.0, Add = 0.0;
+  const double nu = m.pa[3];
+  double KK = m.Kb;
   int nb = 0;
   for (int i = 0; i < kPaBranches; ++i) {
-    const double Ei = m.pa[4 + i];
-    double kv = 0.0, kd = 0.0, rv = 1.0, rd = 1.0, omv = 0.0, omd = 0.0, Ki = 0.0, Gi = 0.0;
+    const double Ei = m.pa[4 + i], tau = m.pa[16 + i];
+    double Ki = 0.0, Gi = 0.0;
     if (Ei > 0.0) {
       nb = i + 1;
       Ki = Ei / (3.0 * (1.0 - 2.0 * nu));
       Gi = Ei / (2.0 * (1.0 + nu));
-      const double tau = m.pa[16 + i];
-      const double lv = Ki / (a * tau * Ei), ld = Gi / (a * tau * Ei);  // 1 / (a tau_K), 1 / (a tau_G)
-      rv = 1.0 / (1.0 + dt * lv);
-      rd = 1.0 / (1.0 + dt * ld);
-      omv = dt * lv * rv;  // 1 - r without cancellation
-      omd = dt * ld * rd;
-      kv = Ki * rv;
-      kd = Gi * rd;
-      Ke += kv;
-      Ge += kd;
-      KK += Ki;
-      Kc += Ki * omv;
-      Av += Ki * rv * omv;
-      Ad += Gi * rd * omd;
-      Avv += Ki * (1.0 - 2.0 * rv) * rv * omv;
-      Add += Gi * (1.0 - 2.0 * rd) * rd * omd;
     }
-    o.kr_v[i] = hp_from(kv, tag);
-    o.kr_d[i] = hp_from(kd, tag);
-    o.kq_v[i] = hp_from(Ki * rv * omv, tag);
-    o.kq_d[i] = hp_from(Gi * rd * omd, tag);
-    o.om_v[i] = hp_from(omv, tag);
-    o.om_d[i] = hp_from(omd, tag);
-    o.ko_v[i] = hp_from(Ki * omv, tag);
-    o.kf_v[i] = TF(Ki * (1.0 - 2.0 * rv) * rv * omv);
-    o.kf_d[i] = TF(Gi * (1.0 - 2.0 * rd) * rd * omd);
+    o.Kst[i] = hp_from(Ki, tag);
+    o.Gst[i] = hp_from(Gi, tag);
+    o.kvs[i] = hp_from(Ei > 0.0 ? Ki / (tau * Ei) : 0.0, tag);  // lambda_K = kvs / a
+    o.gvs[i] = hp_from(Ei > 0.0 ? Gi / (tau * Ei) : 0.0, tag);  // lambda_G = gvs / a
+    KK += Ki;
   }
   o.nb = nb;
-  o.Ke3 = hp_from(3.0 * Ke, tag);
-  o.G2e = hp_from(2.0 * Ge, tag);
-  o.G3e = hp_from(3.0 * Ge, tag);
-  o.KK = hp_from(KK, tag);
-  o.Kc3 = hp_from(3.0 * Kc, tag);
-  o.Av = hp_from(Av, tag);
-  o.Ad = hp_from(Ad, tag);
+  o.Kinf = hp_from(m.Kb, tag);
+  o.Ginf = hp_from(m.G, tag);
+  o.KKst = hp_from(KK, tag);
+}
+
+// the per-point constants, one thread per material: the WLF shift and the
+// Gamma factors by FP64 exp, the branch factors r = 1 / (1 + dt lambda) and
+// their sums in HP (no FP64 division per branch)
+template <typename TF, typename HP>
+__device__ void mat_point_pa(MatPA<TF, HP> &o, const MatDev &m, double theta, double dt) {
+  HP *tag = nullptr;
+  const double x = theta - m.pa[0], C1 = m.pa[1], C2 = m.pa[2];
+  const double ln10 = 2.30258509299404568402;
+  const double ia = exp(ln10 * C1 * x / (C2 + x));          // 1 / a_theta
+  const double L = -ln10 * C1 * C2 / ((C2 + x) * (C2 + x));  // d ln a / d theta
+  const double g1 = exp(-m.cE * x), g2 = exp(-m.pad_ * x);
+  const double sy = g1 * m.sy0, eta = g2 * m.itv;
+  const HP one = hp_from(1.0, tag), dtia = hp_from(dt * ia, tag);
+  HP Ke = o.Kinf, Ge = o.Ginf, Kc = hp_zero(tag), Av = hp_zero(tag), Ad = hp_zero(tag);
+  TF Avv = TF(0), Add = TF(0);
+  for (int i = 0; i < kPaBranches; ++i) {
+    if (i >= o.nb) {
+      o.kr_v[i] = o.kr_d[i] = o.kq_v[i] = o.kq_d[i] = o.om_v[i] = o.om_d[i] = o.ko_v[i] = hp_zero(tag);
+      o.kf_v[i] = o.kf_d[i] = TF(0);
+      continue;
+    }
+    const HP tv = dtia * o.kvs[i], td = dtia * o.gvs[i];  // dt lambda
+    const HP rv = hp_div(one, one + tv), rd = hp_div(one, one + td);
+    const HP omv = tv * rv, omd = td * rd;                  // 1 - r without cancellation
+    const HP Ki = o.Kst[i], Gi = o.Gst[i];
+    o.kr_v[i] = Ki * rv;
+    o.kr_d[i] = Gi * rd;
+    o.kq_v[i] = o.kr_v[i] * omv;
+    o.kq_d[i] = o.kr_d[i] * omd;
+    o.om_v[i] = omv;
+    o.om_d[i] = omd;
+    o.ko_v[i] = Ki * omv;
+    const TF rvf = tf_of(rv, (TF *)nullptr), rdf = tf_of(rd, (TF *)nullptr);
+    o.kf_v[i] = (TF(1) - TF(2) * rvf) * tf_of(o.kq_v[i], (TF *)nullptr);
+    o.kf_d[i] = (TF(1) - TF(2) * rdf) * tf_of(o.kq_d[i], (TF *)nullptr);
+    Ke = Ke + o.kr_v[i];
+    Ge = Ge + o.kr_d[i];
+    Kc = Kc + o.ko_v[i];
+    Av = Av + o.kq_v[i];
+    Ad = Ad + o.kq_d[i];
+    Avv += o.kf_v[i];
+    Add += o.kf_d[i];
+  }
+  const HP three = hp_from(3.0, tag), two = hp_from(2.0, tag);
+  o.Ke3 = three * Ke;
+  o.G2e = two * Ge;
+  o.G3e = three * Ge;
+  o.KK = o.KKst;
+  o.Kc3 = three * Kc;
+  o.Av = Av;
+  o.Ad = Ad;
   o.sy = hp_from(sy, tag);
   o.c = hp_from(dt * sy / eta, tag);
   o.Hk = hp_from(g1 * m.dsy, tag);
@@ -125,15 +152,15 @@ __device__ void mat_point_pa(MatPA<TF, HP> &o, const MatDev &m, double theta, do
   o.nh_h = hp_from(m.H, tag);
   o.idt = hp_from(1.0 / dt, tag);
   o.L = TF(L);
-  o.Avv = TF(Avv);
-  o.Add = TF(Add);
-  o.Av_f = TF(Av);
-  o.Ad_f = TF(Ad);
-  o.Ke_f = TF(Ke);
-  o.G2e_f = TF(2.0 * Ge);
-  o.G3e_f = TF(3.0 * Ge);
-  o.Kc_f = TF(Kc);
-  o.KK_f = TF(KK);
+  o.Avv = Avv;
+  o.Add = Add;
+  o.Av_f = tf_of(Av, (TF *)nullptr);
+  o.Ad_f = tf_of(Ad, (TF *)nullptr);
+  o.Ke_f = tf_of(Ke, (TF *)nullptr);
+  o.G2e_f = tf_of(o.G2e, (TF *)nullptr);
+  o.G3e_f = tf_of(o.G3e, (TF *)nullptr);
+  o.Kc_f = tf_of(Kc, (TF *)nullptr);
+  o.KK_f = tf_of(o.KK, (TF *)nullptr);
   o.sy_f = TF(sy);
   o.c_f = TF(dt * sy / eta);
   o.Hk_f = TF(g1 * m.dsy);

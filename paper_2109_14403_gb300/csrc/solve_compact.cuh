@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
 
   for (int i = t; i < P.n_mats; i += G)
     mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i), P.dt);
+  if (LAW == 3)
+    for (int i = t; i < P.n_mats; i += G)
+      if (int(P.mat[kMatWords * i] + 0.5) == 3)
+        mat_static_pa<TF, HP>(mpa_s[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i));
   if (t == 0) misc[0] = hp_from(1.0 / P.dt, tag);
   const TF idt_f = TF(1.0 / P.dt);
   const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
