@@ -41,6 +41,12 @@ N_POINTS = 65536
 METRIC = "Gauss-pt DMN evals/s (K=8, to 1e-8 rel) FP64 vs mixed+warm-start; %HBM roof"
 UNIT = "GP-evals/s"
 TOL = 1e-12  # the paper's tolerance: mixed-path stress within 1e-8 of FP64
+# ALU peaks of the roofline, from the GB300's unit counts and its maximum SM
+# clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz (an FMA probe
+# of 8 independent chains per thread measured 73.2 TFLOP/s, 91 % of it), and
+# the nominal FP64 rate of 1.25 TFLOP/s (the probe: 1.20)
+FP32_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK = 1.25
 
 
 def state_words(K, n_j2, z_per_leaf=7):
@@ -497,7 +503,8 @@ def run_large(args):
             "iter_hist": hist, "mean_iters": mean_iters, "nonconverged": nonconv,
             "fallback_rate": fallback_rate, "warm_start_training": train_info, "variants": variants,
             "solve_kernel_ms": solve_ms,
-            "roofline": {"bound": "alu", "achieved": flops, "peak": 73.2, "unit": "TFLOP/s", "frac": flops / 73.2,
+            "roofline": {"bound": "alu", "achieved": flops, "peak": FP32_PEAK, "unit": "TFLOP/s",
+                         "frac": flops / FP32_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                          "traffic": None, "kernel": "dmn_solve_compact<float, dfl, 256, 1, 2>",
                          "flops_per_pass": alu_flops_per_pass(K), "passes_per_eval": passes,
                          "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
@@ -611,7 +618,8 @@ def run_cyclic(args):
             "solve_launches_per_increment": evals / steps, "mean_outer": float(oc.float().mean().item()),
             "not_converged": failed,
             "temperature_change_K": {"min": float(dT.min()), "max": float(dT.max())},
-            "roofline": {"bound": "alu", "achieved": flops, "peak": 73.2, "unit": "TFLOP/s", "frac": flops / 73.2,
+            "roofline": {"bound": "alu", "achieved": flops, "peak": FP32_PEAK, "unit": "TFLOP/s",
+                         "frac": flops / FP32_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
                          "traffic": None,
                          "kernel": solve_kernel_name(d.solve_variant, args.precision, law=3 if pa66 else 2),
                          "launch": "one plain evaluation of the last increment from a^n, timed alone",
@@ -698,8 +706,9 @@ def run_linear(args):
                                    "penalty 1e3", "precision": prec,
                        "parallelism": f"replicas x{world} (independent batches)"},
             "loss_before_after": losses,
-            "roofline": {"bound": "alu", "achieved": fl, "peak": 73.2 if prec == "fp32" else 1.25,
-                         "unit": "TFLOP/s", "frac": fl / (73.2 if prec == "fp32" else 1.25), "traffic": None,
+            "roofline": {"bound": "alu", "achieved": fl, "peak": FP32_PEAK if prec == "fp32" else FP64_PEAK,
+                         "unit": "TFLOP/s", "frac": fl / (FP32_PEAK if prec == "fp32" else FP64_PEAK),
+                         "traffic": None,
                          "kernel": f"k_lvl_bwd<{'float' if prec == 'fp32' else 'double'}> + "
                                    "k_lvl_fwd (whole step)", "flops_per_sample": lin_flops_per_sample(K)},
             "clocks": clk.summary(), "gpu_launches": (2 * K + 9) * steps}
@@ -1036,8 +1045,9 @@ def main():
     peak, how = measured_peaks()
     passes = mean_iters + 1.0
     flops = alu_flops_per_pass(K_DEPTH) * passes * n / (solve_ms / 1e3) / 1e12
-    alu_peak = 73.2  # measured FP32 FMA throughput on this GB300
+    alu_peak = FP32_PEAK
     roof = {"bound": "alu", "achieved": flops, "peak": alu_peak, "unit": "TFLOP/s",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "frac": flops / alu_peak, "traffic": measured_traffic(kname, n), "kernel": kname,
             "flops_per_pass": alu_flops_per_pass(K_DEPTH), "passes_per_eval": passes,
             "hbm": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s", "frac": hbm_achieved / peak,
