@@ -94,3 +94,47 @@ class DMNLinear:
                 s, hi - lo, self._ptr(self.params[lo:]), self._ptr(self.grad[lo:]), self._ptr(self._m[lo:]),
                 self._ptr(self._s[lo:]), self._ptr(self._smax[lo:]), float(lr), float(beta1), float(beta2),
                 float(eps), self.step_count), "dmn_linear_amsgrad")
+
+
+def lr_schedule(m, alpha_min=1.5e-3, alpha_max=1.5e-2, M=50, gamma=0.999):
+    """Learning rate of epoch m: the harmonic modulation with geometric decay
+    of the paper's offline training (Sec. 5.3, eq. learning_rate_modulation),
+    gamma^m (alpha_min + (alpha_max - alpha_min)(1 + cos(pi m / M)) / 2);
+    its defaults are the paper's values."""
+    import math
+    return gamma ** m * (alpha_min + 0.5 * (alpha_max - alpha_min) * (1.0 + math.cos(math.pi * m / M)))
+
+
+def mean_error(net, C1, C2, Ctarget, precision="fp64"):
+    """e_mean of Sec. 5.3: the mean over the samples of |DMN^L - C_target|_1 /
+    |C_target|_1 (36 components), which is the data term of the loss with
+    p = q = 1 (one loss launch sequence; the gradient it also computes is
+    discarded)."""
+    keep = net.grad.clone()
+    loss = net.loss_grad(C1, C2, Ctarget, p=1.0, q=1.0, penalty=0.0, precision=precision)
+    net.grad.copy_(keep)
+    return float(loss[1].item())
+
+
+def train(net, C1, C2, Ctarget, epochs, batch=32, p=1.0, q=10.0, penalty=1e3, precision="fp32",
+          schedule=lr_schedule, seed=0):
+    """Mini-batch offline training (Sec. 3.2 and 5.3): every epoch visits the
+    samples in a random order in batches of `batch` (a smaller last batch is
+    dropped, as in the paper), takes the loss gradient of each batch on the
+    GPU and one AMSGrad step with the epoch's learning rate for the normals and
+    the weights.  Returns the data term of the loss of the last batch of each
+    epoch."""
+    import torch
+    n = C1.shape[0]
+    g = torch.Generator(device=C1.device).manual_seed(seed)
+    history = []
+    for m in range(epochs):
+        lr = schedule(m)
+        perm = torch.randperm(n, device=C1.device, generator=g)
+        for i in range(0, n - batch + 1, batch):
+            idx = perm[i:i + batch]
+            net.loss_grad(C1[idx].contiguous(), C2[idx].contiguous(), Ctarget[idx].contiguous(), p=p, q=q,
+                          penalty=penalty, precision=precision)
+            net.amsgrad_step(lr, lr)
+        history.append(float(net.loss[1].item()))
+    return history

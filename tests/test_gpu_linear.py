@@ -133,3 +133,24 @@ def test_full_batch_forward_sampled_and_directional_gradient():
     fd = (vals[0] - vals[1]) / (2 * h)
     an = float((g * direction).sum().item())
     assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-6), (fd, an)
+
+
+def test_minibatch_training_with_the_paper_schedule():
+    """Mini-batches of 32 with the paper's learning-rate modulation (p = 1,
+    q = 10, penalty 1e3 as in its Sec. 5.3): the mean error e_mean of a depth-3
+    network fitted to another one falls by a factor of ten, and e_mean on the
+    GPU equals the oracle's for the same parameters."""
+    from paper_2109_14403_gb300.linear import DMNLinear, mean_error, train
+    K = 3
+    tn, tv = syn.linear_params(K, seed=77)
+    C1, C2 = syn.stiffness_pairs(512, seed=78, log10_contrast=1.0)
+    Ct = olin.forward(C1, C2, tn, tv)
+    normals, v = syn.linear_params(K, seed=79)
+    d = DMNLinear(K, normals, v, device=_dev())
+    c1, c2, ct = _t(C1), _t(C2), _t(Ct)
+    e0 = mean_error(d, c1, c2, ct)
+    o_err = olin.loss(C1, C2, Ct, normals, v, p=1.0, q=1.0, penalty=0.0)[1]
+    assert abs(e0 - o_err) <= 1e-9 * o_err
+    train(d, c1, c2, ct, epochs=40, batch=32, precision="fp64")
+    e1 = mean_error(d, c1, c2, ct)
+    assert e1 < 0.1 * e0, (e0, e1)
