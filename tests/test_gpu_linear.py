@@ -154,3 +154,30 @@ def test_minibatch_training_with_the_paper_schedule():
     train(d, c1, c2, ct, epochs=40, batch=32, precision="fp64")
     e1 = mean_error(d, c1, c2, ct)
     assert e1 < 0.1 * e0, (e0, e1)
+
+
+@pytest.mark.parametrize("K", [3, 8])
+def test_trained_parameters_drive_the_online_evaluation(K):
+    """Offline to online (the paper's workflow): a DMN^L parameter set used by
+    dmn_create gives, for linear elastic phases, an algorithmic tangent of
+    Algorithm 1 equal to DMN^L of the same phase stiffnesses."""
+    from paper_2109_14403_gb300 import DMN
+    from paper_2109_14403_gb300.linear import DMNLinear
+    dev = _dev()
+    normals, v = syn.linear_params(K, seed=55)
+    w = np.maximum(v, 0.0)
+    w = w / w.sum()
+    mats = syn.materials().copy()
+    mats[1, 5] = 1e12  # the matrix never yields
+    C1 = syn.iso_mandel(mats[0, 1], mats[0, 2])
+    C2 = syn.iso_mandel(mats[1, 1], mats[1, 2])
+    lin = DMNLinear(K, normals, w, device=dev)
+    ref = lin.forward(_t(C1[None]), _t(C2[None]), precision="fp64").cpu().numpy()[0]
+    phase = (np.arange(1 << K) % 2).astype(np.uint8)  # leaf 2i: phase 1, leaf 2i+1: phase 2
+    d = DMN(K, w, normals, phase, mats, tol=1e-12, precision="fp64")
+    s = d.init_state(torch.full((1,), mats[0, 4], dtype=torch.float64, device=dev))
+    _, out, st, _ = d.eval(_t(np.full((1, 6), 1e-5)), _t(np.full(1, mats[0, 4])), 1.0, s)
+    C = out.cpu().numpy()[0, 6:42].reshape(6, 6)
+    assert st.cpu().numpy()[0] == 0
+    assert np.abs(C - ref).max() <= 1e-10 * np.abs(ref).max()
+    d.close()
