@@ -454,6 +454,8 @@ def run_large(args):
     _, oref, _, _ = ref.eval(D[kl, :n_train], T[kl, :n_train], dt, bufs[0][:n_train].contiguous())
     sig, sref = out[:n_train, :6], oref[:, :6]
     acc_err = ((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item()
+    tan_rel = (out[:n_train, 6:42] - oref[:, 6:42]).norm(dim=1) / oref[:, 6:42].norm(dim=1)
+    tan_err = {"max": tan_rel.max().item(), "median": tan_rel.median().item()}
     ref.close()
     variants = {}
     if not args.no_variants:
@@ -498,8 +500,8 @@ def run_large(args):
                                    f"{first}-{first + steps - 1}",
                        "tol": TOL, "state_bytes_per_buffer": int(8 * state_words(K, 256, 13) * n),
                        "parallelism": f"replicas x{world} (independent points)"},
-            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "reference": "FP64 path at tol 1e-13",
-                         "points": n_train},
+            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "rel_tangent_err_vs_fp64": tan_err,
+                         "reference": "FP64 path at tol 1e-13", "points": n_train},
             "iter_hist": hist, "mean_iters": mean_iters, "nonconverged": nonconv,
             "fallback_rate": fallback_rate, "warm_start_training": train_info, "variants": variants,
             "solve_kernel_ms": solve_ms,
@@ -951,6 +953,9 @@ def main():
     warm_step(first, it)
     sig, sref = out[:, :6], oref[:, :6]
     acc_err = ((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item()
+    tan, tref = out[:, 6:42], oref[:, 6:42]
+    tan_rel = (tan - tref).norm(dim=1) / tref.norm(dim=1)
+    tan_err = {"max": tan_rel.max().item(), "median": tan_rel.median().item()}
     ref.close()
     bufs[0], bufs[1] = p0, c0
     snap_prev, snap_cur = p0.clone(), c0.clone()  # the end-to-end run repeats these increments
@@ -1065,8 +1070,8 @@ def main():
                        "tol": TOL, "points_per_gpu": n,
                        "l2": "inputs larger than L2 (device state ~0.9 GB)",
                        "parallelism": f"replicas x{world} (independent points)"},
-            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "reference": "FP64 path at tol 1e-13",
-                         "points": n},
+            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "rel_tangent_err_vs_fp64": tan_err,
+                         "reference": "FP64 path at tol 1e-13", "points": n},
             "iter_hist": hist, "mean_iters": mean_iters, "fallback_rate": fallback_rate,
             "warm_start_training": train_info, "variants": variants,
             "solve_kernel_ms": solve_ms,
