@@ -96,10 +96,12 @@
  *  - sigma_Y(theta) = sy0 + dsy_dT (theta - theta0), floored at 1e-6 MPa;
  *  - zero leaf weights are rejected (the Hessian would be singular).
  *
- * Parity of the full inelastic K=8 trajectory is unpinned beyond the
- * invariants checked by the test suite (closed-form laminate, homogeneous
- * phases, free thermal expansion, Hill-Mandel, finite-difference tangents,
- * dense-versus-sparse agreement); the paper prints no worked example.
+ * The test suite pins this code against closed-form laminates, homogeneous
+ * phases, free thermal expansion, Hill-Mandel, finite-difference tangents and
+ * dense-versus-sparse agreement.  A full inelastic K=8 path is pinned by
+ * composition: leaf strains by the kinematics, leaf responses by the pinned
+ * leaf law, equilibrium of the converged jumps by virtual work.  The paper
+ * prints no worked example to compare values with.
  */
 #include <complex.h>
 #include <math.h>

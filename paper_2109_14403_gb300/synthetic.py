@@ -115,7 +115,7 @@ def tree(K: int, seed: int | None = None):
     w = g / g.sum()
     v = rng.standard_normal(((1 << K) - 1, 3))
     normals = v / np.linalg.norm(v, axis=1, keepdims=True)
-    phase = (np.arange(1 << K) % 2).astype(np.uint8)  # leaf 1 (odd) -> fiber
+    phase = (np.arange(1 << K) % 2).astype(np.uint8)  # odd leaves: row 1 (the matrix)
     return w, normals, phase
 
 
