@@ -240,10 +240,12 @@ __device__ __forceinline__ void mat_point(MatPt<TF, HP> &o, HP theta, HP idt, TF
 // Newton corrections in HP; the tangent is the radial-return one with
 // 1/(3G + H) replaced by c m phi^(m-1) / (sigma_Y + c m phi^(m-1) (3G + H));
 // temperature-dependent moduli add theta (r'/r) sigma : (de - d eps_p) / dt
-// to D, de the leaf's strain increment.
+// to D, de the leaf's strain increment.  With full = false the output-only
+// quantities (D, X and the record's tau, dd, gg) are left at zero.
 template <typename TF, typename HP, int LAW>
 __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6], const HP *zn,
-                                          HP trn, HP sig[6], HP &D, HP &X, Rec<TF> &R, HP *znew) {
+                                          HP trn, HP sig[6], HP &D, HP &X, Rec<TF> &R, HP *znew,
+                                          bool full = true) {
   const bool j2 = m.kind >= 1;
   const bool vp = LAW >= 2 && m.kind == 2;
   HP ee[6];
@@ -258,20 +260,24 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
 #pragma unroll
   for (int c = 0; c < 6; ++c) s[c] = m.G2 * (c < 3 ? ee[c] - tr3 : ee[c]);
   const HP pk = m.Kb * tr;
-  HP dtr;
+  HP dtr = hp_zero((HP *)nullptr);
   HP de[6];
-  if (vp) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) de[c] = eps[c] - zn[7 + c];
-    dtr = de[0] + de[1] + de[2];
-  } else {
-    const HP treps = eps[0] + eps[1] + eps[2];
-    dtr = treps - trn;
-  }
-  D = -(m.a3Kth_idt * dtr);
+  D = hp_zero((HP *)nullptr);
   X = hp_zero((HP *)nullptr);
-  TF gg = -m.a3K_idt_f * tf_of(dtr, (TF *)nullptr);
-  if (vp) gg -= m.gj_f * tf_of(dtr, (TF *)nullptr);
+  TF gg = TF(0);
+  if (full) {
+    if (vp) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) de[c] = eps[c] - zn[7 + c];
+      dtr = de[0] + de[1] + de[2];
+    } else {
+      const HP treps = eps[0] + eps[1] + eps[2];
+      dtr = treps - trn;
+    }
+    D = -(m.a3Kth_idt * dtr);
+    gg = -m.a3K_idt_f * tf_of(dtr, (TF *)nullptr);
+    if (vp) gg -= m.gj_f * tf_of(dtr, (TF *)nullptr);
+  }
   TF th1 = TF(1), thb = TF(0), kd = TF(0), ktau = TF(0);
   TF Nf[6] = {TF(0), TF(0), TF(0), TF(0), TF(0), TF(0)};
   TF qf = TF(0), kkf = TF(0), ddpf = TF(0);  // kind 2: q, d dp / d eps factor, d dp / d theta
@@ -338,16 +344,19 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
       }
       znew[6] = zn[6] + dp;
       kzs = kz;
-      const HP dis = m.syidt * dp;
-      D = D + dis;
-      X = dis;
+      if (full) {
+        const HP dis = m.syidt * dp;
+        D = D + dis;
+        X = dis;
+      }
       const TF kapf = tf_of(kap, (TF *)nullptr), dpf = tf_of(dp, (TF *)nullptr);
       th1 = TF(1) - m.G3_f * kapf;
       thb = m.G3_f * kinv - m.G3_f * kapf;
       const TF isn = TF(1) / sqrt(tf_of(sn2, (TF *)nullptr));
 #pragma unroll
       for (int c = 0; c < 6; ++c) Nf[c] = tf_of(s[c], (TF *)nullptr) * isn;
-      if (vp) {
+      if (!full) {
+      } else if (vp) {
         qf = tf_of(q, (TF *)nullptr) - m.G3_f * dpf;  // updated equivalent stress
         ddpf = (m.sE_f * qf - m.dsy_f * (TF(1) + phif)) * kinv;
         ktau = TF(0.81649658092772603273) * (m.sE_f * qf - m.G3_f * ddpf);  // sqrt(2/3) dq/dtheta
@@ -381,6 +390,14 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
 #pragma unroll
     for (int j = i; j < 6; ++j)
       R.C[sidx(i, j)] = (i < 3 && j < 3 ? cP1 : TF(0)) + (i == j ? cI : TF(0)) - cN * Nf[i] * Nf[j];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    R.ds[c] = TF(0);
+    R.tau[c] = TF(0);
+    R.dd[c] = TF(0);
+  }
+  R.gg = TF(0);
+  if (!full) return;
   TF ta = -m.a3K_f;
   if (vp) ta += m.dKb_f * tf_of(tr, (TF *)nullptr);
   const TF da_ = -tf_of(m.a3Kth_idt, (TF *)nullptr);
@@ -388,7 +405,6 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
   for (int c = 0; c < 6; ++c) {
     R.tau[c] = (c < 3 ? ta : TF(0)) + ktau * Nf[c];
     R.dd[c] = (c < 3 ? da_ : TF(0)) + kd * Nf[c];
-    R.ds[c] = TF(0);
   }
   if (vp) {
     // elastic leaf: the deviatoric stress scales with the moduli
@@ -429,10 +445,11 @@ __device__ __forceinline__ void leaf_eval(const MatPt<TF, HP> &m, const HP eps[6
 // Combine children L (in/out) and R of node p in precision TF.  rbv =
 // B^T (sigma_bar_L - sigma_bar_R), the node's residual divided by w c1 c2
 // (formed in FP64 by the caller).  Writes G_p (3x6) and h_p (3) for the
-// back-substitution.
+// back-substitution.  With full = false the output-only parts of the record
+// (tau, dd, gg) are not formed.
 template <typename TF>
 __device__ __forceinline__ void combine(Rec<TF> &L, const Rec<TF> &R, const TF n[3], TF c1, TF c2,
-                                        const TF rbv[3], TF *gh) {
+                                        const TF rbv[3], TF *gh, bool full = true) {
   const TF cc = c1 * c2;
   // M = c2 C_L + c1 C_R, dC = C_L - C_R (dC in place of L.C)
   TF M[21];
@@ -504,34 +521,39 @@ __device__ __forceinline__ void combine(Rec<TF> &L, const Rec<TF> &R, const TF n
     for (int a = 0; a < 6; ++a) gh[6 * e + a] = Gm[e][a];
 #pragma unroll
   for (int e = 0; e < 3; ++e) gh[18 + e] = hs[e];
-  TF ht[3];
-  {
-    TF dv[6], t3[3];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) dv[c] = L.tau[c] - R.tau[c];
-    btvec(n, dv, t3);
-#pragma unroll
-    for (int e = 0; e < 3; ++e) ht[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
-  }
-  TF hd[3], bd[3];
-  {
-    TF ddiff[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) ddiff[c] = L.dd[c] - R.dd[c];
-    btvec(n, ddiff, bd);
-#pragma unroll
-    for (int e = 0; e < 3; ++e) hd[e] = Ki[e][0] * bd[0] + Ki[e][1] * bd[1] + Ki[e][2] * bd[2];
-  }
-  // g_hat = c1 g_L + c2 g_R - c1 c2 (B^T d_diff) . h_tau
-  L.gg = c1 * L.gg + c2 * R.gg - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     const TF Uhs = U[a][0] * hs[0] + U[a][1] * hs[1] + U[a][2] * hs[2];
-    const TF Uht = U[a][0] * ht[0] + U[a][1] * ht[1] + U[a][2] * ht[2];
-    const TF Uhd = U[a][0] * hd[0] + U[a][1] * hd[1] + U[a][2] * hd[2];
     L.ds[a] = c1 * L.ds[a] + c2 * R.ds[a] - cc * Uhs;
-    L.tau[a] = c1 * L.tau[a] + c2 * R.tau[a] - cc * Uht;
-    L.dd[a] = c1 * L.dd[a] + c2 * R.dd[a] - cc * Uhd;
+  }
+  if (full) {
+    TF ht[3];
+    {
+      TF dv[6], t3[3];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) dv[c] = L.tau[c] - R.tau[c];
+      btvec(n, dv, t3);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) ht[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
+    }
+    TF hd[3], bd[3];
+    {
+      TF ddiff[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) ddiff[c] = L.dd[c] - R.dd[c];
+      btvec(n, ddiff, bd);
+#pragma unroll
+      for (int e = 0; e < 3; ++e) hd[e] = Ki[e][0] * bd[0] + Ki[e][1] * bd[1] + Ki[e][2] * bd[2];
+    }
+    // g_hat = c1 g_L + c2 g_R - c1 c2 (B^T d_diff) . h_tau
+    L.gg = c1 * L.gg + c2 * R.gg - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const TF Uht = U[a][0] * ht[0] + U[a][1] * ht[1] + U[a][2] * ht[2];
+      const TF Uhd = U[a][0] * hd[0] + U[a][1] * hd[1] + U[a][2] * hd[2];
+      L.tau[a] = c1 * L.tau[a] + c2 * R.tau[a] - cc * Uht;
+      L.dd[a] = c1 * L.dd[a] + c2 * R.dd[a] - cc * Uhd;
+    }
   }
   // C_hat = c1 C_L + c2 C_R - c1 c2 U G  with c1 C_L + c2 C_R = M + (c1 - c2) dC
   const TF cm = c1 - c2;

@@ -358,6 +358,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     HP Dsum = hp_zero(tag), Xsum = hp_zero(tag);
     Rec<TF> rec;
     for (;;) {
+      // Algorithm 1 takes at least one Newton step (maxit >= 1), so the
+      // first pass of an iteration never gives the outputs: it skips their
+      // terms (coupling term, dissipation, thermal tangents)
+      const bool full = !ctrl->first;
       // ---- R2: leaves and laminate t ----
       TF r2;
       HP S[6];
@@ -386,13 +390,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         if (LAW == 3 && mp_s[ph0].kind == 3)
           leaf_pa66<TF, HP>(mp_s[ph0], mpa_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
         else
-          leaf_eval<TF, HP, LAW>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0);
+          leaf_eval<TF, HP, LAW>(mp_s[ph0], el, zn0, trn0, sl, DL, XL, rec, zw0, full);
         if (LAW == 3 && mp_s[ph1].kind == 3)
           leaf_pa66<TF, HP>(mp_s[ph1], mpa_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
         else
-          leaf_eval<TF, HP, LAW>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1);
-        Dsum = wL * DL + wR * DR;
-        Xsum = wL * XL + wR * XR;
+          leaf_eval<TF, HP, LAW>(mp_s[ph1], er, zn1, trn1, sr, DR, XR, rr, zw1, full);
+        if (full) {
+          Dsum = wL * DL + wR * DR;
+          Xsum = wL * XL + wR * XR;
+        }
         HP dsh[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         const TF rbv[3] = {tf_of(rbh[0], (TF *)nullptr), tf_of(rbh[1], (TF *)nullptr),
                            tf_of(rbh[2], (TF *)nullptr)};
         r2 = wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
-        combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t);
+        combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t, full);
       }
       // ---- level K-1: neighbouring lanes (2j, 2j+1) ----
       if (K >= 2) {
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
                             tf_of(rh[2], (TF *)nullptr)};
           r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
           const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
-          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
+          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p, full);
           if (K >= 3) {
             rec_put(recX + RS * j, rec);
 #pragma unroll
@@ -479,7 +485,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
                             tf_of(rh[2], (TF *)nullptr)};
           r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
           const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
-          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p);
+          combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p, full);
           if (k > 1) {
             rec_put(recbuf(k) + RS * j, rec);
 #pragma unroll
