@@ -13,7 +13,10 @@
 //                   tcgen05.commit on that stage's "empty" mbarrier;
 //   all 4 warps     wait for the final commit, read the accumulator with
 //                   tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows)
-//                   and run the epilogue.
+//                   and run the epilogue.  The de-normalised FP32 prediction
+//                   (rows of an odd length) goes through the then idle
+//                   operand ring: each warp stages its 32 rows and writes
+//                   them row by row, the lanes on consecutive columns.
 // Every wait is bounded (about two seconds of SM clock): on a timeout the CTA
 // records an error code, stops issuing work, frees its TMEM and returns.
 #pragma once
@@ -28,6 +31,7 @@ namespace mlp {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
 constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;  // bytes per stage
 constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+static_assert(BM * (BN + 1) * 4 <= STAGES * (TILE_A + TILE_B), "staged FP32 tile fits the ring");
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 enum Epi {
@@ -251,14 +255,10 @@ __global__ void __launch_bounds__(128, 2)
           for (int i = 0; i < 16; ++i) ep.t_out[size_t(n + i) * ep.ldt + r] = db[i];
         }
       } else if (ep.mode == EPI_BIAS_F32) {
-        if (ep.scale) {  // de-normalised prediction on valid rows and columns
-          if (r < ep.m_valid) {
+        if (ep.scale) {  // staged: the ring holds no operands once `done` has fired
+          float *srow = reinterpret_cast<float *>(base) + (warp * 32 + lane) * (BN + 1);
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (n + i < ep.n_valid)
-                ep.f_out[size_t(r) * ep.ld_f + n + i] =
-                    (v[i] + ep.bias[n + i]) * ep.scale[n + i] + ep.shift[n + i];
-          }
+          for (int i = 0; i < 16; ++i) srow[c0 + i] = v[i];
         } else {
           float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
 #pragma unroll
@@ -271,6 +271,30 @@ __global__ void __launch_bounds__(128, 2)
         float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
 #pragma unroll
         for (int q = 0; q < 4; ++q) fo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+    if (ep.mode == EPI_BIAS_F32 && ep.scale) {
+      // de-normalised prediction on valid rows and columns: the warp writes
+      // its 32 staged rows, lane l on columns l, l+32, l+64, l+96
+      __syncwarp();
+      const float *tile = reinterpret_cast<const float *>(base);
+      float bb[4], sc[4], sh[4];
+      bool cv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int n = n0 + lane + 32 * q;
+        cv[q] = n < ep.n_valid;
+        bb[q] = cv[q] ? ep.bias[n] : 0.0f;
+        sc[q] = cv[q] ? ep.scale[n] : 0.0f;
+        sh[q] = cv[q] ? ep.shift[n] : 0.0f;
+      }
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = warp * 32 + rr, rg = m0 + row;
+        if (rg >= ep.m_valid) break;
+        float *dst = ep.f_out + size_t(rg) * ep.ld_f + n0 + lane;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (cv[q]) dst[32 * q] = (tile[row * (BN + 1) + lane + 32 * q] + bb[q]) * sc[q] + sh[q];
       }
     }
   }
