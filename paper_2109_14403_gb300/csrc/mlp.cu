@@ -92,25 +92,36 @@ __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const 
   }
 }
 
-// features of k_features, normalised and rounded to bf16 in one pass
+// features of k_features, normalised and rounded to bf16 in one pass: one
+// warp per row, each lane two adjacent columns per step (one bf16x2 store;
+// ld = kin is a multiple of 128, so the pairs stay 4-byte aligned)
 __global__ void k_features_norm(int64_t n, int n3, int sw, int ld, const double *deps,
                                 const double *theta, const double *sin, const double *sprev,
                                 const float *mean, const float *inv, bf16 *x) {
   const int nin = 8 + n3;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * ld;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / ld;
-    const int c = int(i - r * ld);
-    float v = 0.0f;
-    if (c < nin) {
-      double f;
-      if (c < 6) f = deps[r * 6 + c];
-      else if (c == 6) f = theta[r];
-      else if (c == 7) f = theta[r] - sin[r * sw + 6];
-      else f = sprev ? sin[r * sw + 8 + (c - 8)] - sprev[r * sw + 8 + (c - 8)] : 0.0;
-      v = (float(f) - mean[c]) * inv[c];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < n; r += nwarp) {
+    const double *a = sin + r * sw;
+    const double *ap = sprev ? sprev + r * sw : nullptr;
+    __nv_bfloat162 *xr = reinterpret_cast<__nv_bfloat162 *>(x + r * ld);
+    for (int c0 = 2 * lane; c0 < ld; c0 += 64) {
+      float v[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = c0 + u;
+        v[u] = 0.0f;
+        if (c < nin) {
+          double f;
+          if (c < 6) f = deps[r * 6 + c];
+          else if (c == 6) f = theta[r];
+          else if (c == 7) f = theta[r] - a[6];
+          else f = ap ? a[c] - ap[c] : 0.0;
+          v[u] = (float(f) - mean[c]) * inv[c];
+        }
+      }
+      xr[c0 >> 1] = __floats2bfloat162_rn(v[0], v[1]);
     }
-    x[i] = __float2bfloat16(v);
   }
 }
 
@@ -513,7 +524,7 @@ extern "C" dmn_status dmn_mlp_input(dmn_mlp m, dmn_stream stream, int64_t n, con
   if (!m || n < 0 || !d_deps || !d_theta || !d_state_in || !d_x_bf16 || state_words < 8 + m->n3)
     return fail(DMN_ERR_ARG, "dmn_mlp_input: invalid argument");
   if (n == 0) return DMN_OK;
-  k_features_norm<<<blocks_for(n * m->kin), 256, 0, (cudaStream_t)stream>>>(
+  k_features_norm<<<blocks_for(n * 32), 256, 0, (cudaStream_t)stream>>>(
       n, m->n3, int(state_words), m->kin, d_deps, d_theta, d_state_in, d_state_prev, m->fmean,
       m->finv, static_cast<bf16 *>(d_x_bf16));
   cudaError_t e = cudaGetLastError();
