@@ -904,10 +904,10 @@ def main():
     perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
     X, Y = X[perm].contiguous(), Y[perm].contiguous()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    B, epochs = 4096, 12
+    B, epochs = 4096, 36
     for ep in range(epochs):
         for i in range(0, X.shape[0] - B + 1, B):
-            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 24 else 2e-4, loss)
     torch.cuda.synchronize()
     train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
                   "gen_and_train_s": time.perf_counter() - t0,
