@@ -896,6 +896,18 @@ def main():
         feats.append(net.features(D[k], T[k], s, s_prev))
         tgts.append(net.targets(s, s1))
         s_prev, s = s, s1
+    # two more seeded batches of the same load distribution: about 1e6 pairs
+    for extra in range(2):
+        dh, th = syn.random_walk_k8(n_points=n, n_incr=n_gen, seed=1000 + 17 * extra + rank)
+        De, Te = torch.tensor(dh, device=dev), torch.tensor(th, device=dev)
+        xp = None
+        xs = fp64.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+        for k in range(n_gen):
+            x1, _, _, _ = fp64.eval(De[k], Te[k], 1.0, xs)
+            feats.append(net.features(De[k], Te[k], xs, xp))
+            tgts.append(net.targets(xs, x1))
+            xp, xs = xs, x1
+        del De, Te, xp, xs, x1
     F, Tg = torch.cat(feats), torch.cat(tgts)
     del feats, tgts
     net.fit_normalization(F, Tg)
@@ -904,10 +916,10 @@ def main():
     perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
     X, Y = X[perm].contiguous(), Y[perm].contiguous()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    B, epochs = 4096, 36
+    B, epochs = 4096, 12
     for ep in range(epochs):
         for i in range(0, X.shape[0] - B + 1, B):
-            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 24 else 2e-4, loss)
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
     torch.cuda.synchronize()
     train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
                   "gen_and_train_s": time.perf_counter() - t0,
