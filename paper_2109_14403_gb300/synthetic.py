@@ -7,8 +7,9 @@ consume what it returns.
 Workloads (the paper's own trained DMN and FFT data are not available, so these
 stand in for its strain-controlled virtual experiments, Sec. 5.4):
   * tree: leaf weights ~ Dirichlet(1) over 2^K leaves, lamination directions
-    uniform on the unit sphere, phases alternating (odd leaves phase 1 = fiber,
-    even leaves phase 2 = matrix, as in Sec. 3.3), seed 1234 + K;
+    uniform on the unit sphere, phases alternating as in Sec. 3.3 (leaf j,
+    0-based, takes material row j mod 2: even leaves the fiber, odd leaves
+    the matrix), seed 1234 + K;
   * fiber: isotropic linear thermoelastic E = 72 GPa, nu = 0.22, alpha = 5e-6/K;
   * matrix: J2 elastoplastic, linear isotropic hardening 300 MPa,
     E = 2.5 GPa, nu = 0.38, alpha = 8e-5/K, yield 50 MPa at 293 K falling
