@@ -40,7 +40,12 @@ K_DEPTH = 8
 N_POINTS = 65536
 METRIC = "Gauss-pt DMN evals/s (K=8, to 1e-8 rel) FP64 vs mixed+warm-start; %HBM roof"
 UNIT = "GP-evals/s"
-TOL = 1e-12  # the paper's tolerance: mixed-path stress within 1e-8 of FP64
+TOL_PAPER = 1e-12  # the paper's tolerance (uneven, large and cyclic workloads)
+# K = 8 random walk and plastic ramp (the headline metric asks for stress within
+# 1e-8 of FP64): at 1e-12 the mixed path stops just below the tolerance (its FP32
+# Newton correction converges linearly at the end) and the largest stress error over
+# 65,536 points came to 1.2e-8; 5e-13 gives 4.3e-9 for 3 % more Newton iterations
+TOL = 5e-13
 # ALU peaks of the roofline, from the GB300's unit counts and its maximum SM
 # clock: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2070 MHz (an FMA probe
 # of 8 independent chains per thread measured 73.2 TFLOP/s, 91 % of it), and
@@ -292,7 +297,7 @@ def run_uneven(args):
     for i, K in enumerate(syn.UNEVEN_DEPTHS):
         w, nrm, ph = trees[i]
         sel = np.nonzero(tid == i)[0]
-        parts.append((DMN(K, w, nrm, ph, syn.materials(), tol=TOL, precision=args.precision), len(sel)))
+        parts.append((DMN(K, w, nrm, ph, syn.materials(), tol=TOL_PAPER, precision=args.precision), len(sel)))
         sels.append(sel)
     g = IncrementGraph(parts)
     for i, (d, m) in enumerate(parts):
@@ -327,7 +332,7 @@ def run_uneven(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": f"uneven batch, {n} points over DMNs K=6/7/8, lognormal increments, "
-                                       "CUDA-graph increments", "precision": args.precision, "tol": TOL},
+                                       "CUDA-graph increments", "precision": args.precision, "tol": TOL_PAPER},
                 "iter_hist": hist, "clocks": clk.summary(), "gpu_launches": 4 * len(parts) * steps}
         print(json.dumps(line), flush=True)
     for d, _ in parts:
@@ -373,7 +378,7 @@ def run_large(args):
 
     # ---- network: pairs of the plain FP64 solver on the first n_train points
     t0 = time.perf_counter()
-    fp64 = DMN(K, w, nrm, ph, mats, tol=TOL, precision="fp64")
+    fp64 = DMN(K, w, nrm, ph, mats, tol=TOL_PAPER, precision="fp64")
     net = MLP(K=K, hidden=512, n_hidden=3, max_batch=n, seed=0)
     sp, sc = None, fp64.init_state(torch.full((n_train,), syn.THETA_START, dtype=torch.float64, device=dev))
     feats, tgts = [], []
@@ -400,7 +405,7 @@ def run_large(args):
     del X, Y
 
     # ---- the full batch: history by the plain mixed solve, then warm steps
-    mixed = DMN(K, w, nrm, ph, mats, tol=TOL, precision="mixed")
+    mixed = DMN(K, w, nrm, ph, mats, tol=TOL_PAPER, precision="mixed")
     st0 = mixed.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
     bufs = [torch.empty_like(st0), st0, torch.empty_like(st0)]
     out = torch.empty((n, 57), dtype=torch.float64, device=dev)
@@ -498,7 +503,7 @@ def run_large(args):
             "config": {"workload": f"K=9 DMN, Perzyna matrix (m 5, t_visc 1e3 s, moduli -0.2 %/K), {n} points, "
                                    f"dt {dt} s, strain rates N(0,1e-2)/s, +1 K per increment; increments "
                                    f"{first}-{first + steps - 1}",
-                       "tol": TOL, "state_bytes_per_buffer": int(8 * state_words(K, 256, 13) * n),
+                       "tol": TOL_PAPER, "state_bytes_per_buffer": int(8 * state_words(K, 256, 13) * n),
                        "parallelism": f"replicas x{world} (independent points)"},
             "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "rel_tangent_err_vs_fp64": tan_err,
                          "reference": "FP64 path at tol 1e-13", "points": n_train},
@@ -548,7 +553,7 @@ def run_cyclic(args):
     c_heat = syn.effective_heat_capacity(w, ph)
     pa66 = args.matrix == "pa66"
     mats = syn.materials_pa66() if pa66 else syn.materials_cyclic()
-    d = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision=args.precision)
+    d = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL_PAPER, precision=args.precision)
     mask = torch.tensor(mask_h, device=dev)
     tgt = torch.tensor(tgt_h[:warm + steps], device=dev)
     deps = torch.zeros((n, 6), dtype=torch.float64, device=dev)
@@ -614,7 +619,7 @@ def run_cyclic(args):
             "config": {"workload": f"K=8 DMN, {matrix}, {n} points, uniaxial "
                                    "sinusoidal stress 20-80 MPa at 10 Hz, 20 increments per cycle, adiabatic; "
                                    f"increments {warm}-{warm + steps - 1}",
-                       "precision": args.precision, "tol": TOL, "tol_outer": tol_outer,
+                       "precision": args.precision, "tol": TOL_PAPER, "tol_outer": tol_outer,
                        "heat_capacity_MPa_per_K": c_heat,
                        "parallelism": f"replicas x{world} (independent points)"},
             "solve_launches_per_increment": evals / steps, "mean_outer": float(oc.float().mean().item()),
@@ -740,10 +745,10 @@ def cpu_baseline_cyclic(n_points=256, threads=None, pa66=False):
     s = tree.init_state(n_points, syn.THETA_START)
     t0 = time.perf_counter()
     oracle.eval_mixed(tree, mask, tgt[0], np.zeros((n_points, 6)), syn.THETA_START, dt,
-                      syn.effective_heat_capacity(w, ph), s, tol_outer=1e-10, tol=TOL, threads=threads)
+                      syn.effective_heat_capacity(w, ph), s, tol_outer=1e-10, tol=TOL_PAPER, threads=threads)
     dtm = time.perf_counter() - t0
     return {"value": n_points / dtm, "unit": "GP-increments/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n_points} points x the first increment of the cyclic path, tol {TOL}, tol_outer 1e-10"}
+            "sample": f"{n_points} points x the first increment of the cyclic path, tol {TOL_PAPER}, tol_outer 1e-10"}
 
 
 def cpu_baseline_large(n_points=64, threads=None):
@@ -757,10 +762,10 @@ def cpu_baseline_large(n_points=64, threads=None):
     deps, theta = syn.large_path(n_points=n_points, n_incr=1)
     s = tree.init_state(n_points, syn.THETA_START)
     t0 = time.perf_counter()
-    oracle.eval_batch(tree, deps[0], theta[0], syn.LARGE_DT, s, tol=TOL, threads=threads)
+    oracle.eval_batch(tree, deps[0], theta[0], syn.LARGE_DT, s, tol=TOL_PAPER, threads=threads)
     dtm = time.perf_counter() - t0
     return {"value": n_points / dtm, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_points} points x the first increment of the K=9 Perzyna path, tol {TOL}"}
+            "sample": f"{n_points} points x the first increment of the K=9 Perzyna path, tol {TOL_PAPER}"}
 
 
 def run_mlp(args):
