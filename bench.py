@@ -212,35 +212,62 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(n_points=1024, n_incr=2, threads=None, ramp=False):
-    """FP64 oracle on the host cores: the first n_incr increments of the same
-    K=8 load path (random walk, or the plastic ramp) on n_points points (its
-    own trajectory)."""
+N_GEN = 6  # increments of the timed batch that the FP64 solver runs to make training pairs
+
+
+def _load_path(n_incr, plastic=False, n_points=N_POINTS, seed=42):
+    from paper_2109_14403_gb300 import synthetic as syn
+    if plastic:  # the K = 4 configuration's ramp on the K = 8 batch: the matrix flows
+        return syn.ramp_k4(n_points=n_points, n_incr=n_incr, seed=seed)
+    return syn.random_walk_k8(n_points=n_points, n_incr=n_incr, seed=seed)
+
+
+def arm_config(n, first, steps, plastic, world=1):
+    """The workload both arms name (the reference arm times a sample of it)."""
+    return {"workload": f"K={K_DEPTH} DMN, {n} Gauss points per GPU, "
+                        + ("plastic ramp (0.1 % in 11 + N(0, 1e-4), +3 K) increments " if plastic
+                           else "random-walk increments ") + f"{first + 1}-{first + steps}",
+            "path": "mixed precision + learned warm start (MLP inference in the step)",
+            "tol": TOL, "points_per_gpu": n,
+            "l2": "inputs larger than L2 (device state ~0.9 GB)",
+            "parallelism": f"replicas x{world} (independent points)"}
+
+
+def oracle_on_timed_increments(m, first, steps, threads, plastic=False):
+    """FP64 oracle on the first m of the benchmark's Gauss points: increments
+    1..first untimed (its own trajectory from the initial state), then the
+    timed increments first+1..first+steps, the ones the GPU arm times.
+    Returns (evals/s, mean Newton iterations, seconds)."""
     import oracle
     from paper_2109_14403_gb300 import synthetic as syn
-    threads = threads or os.cpu_count() or 1
     w, nrm, ph = syn.tree(K_DEPTH)
     tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials())
-    if ramp:
-        deps, theta = syn.ramp_k4(n_points=n_points, n_incr=n_incr)
-    else:
-        deps, theta = syn.random_walk_k8(n_points=n_points, n_incr=n_incr)
-    s = tree.init_state(n_points, syn.THETA_START)
+    deps, theta = _load_path(first + steps, plastic)
+    deps, theta = deps[:, :m].copy(), theta[:, :m].copy()
+    s = tree.init_state(m, syn.THETA_START)
+    for k in range(first):
+        s, *_ = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
+    its = []
     t0 = time.perf_counter()
-    for k in range(n_incr):
-        s, out, st, it = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
-    dt = time.perf_counter() - t0
-    # the same on one core, a smaller sample
-    m1 = max(n_points // 16, 1)
-    s1 = tree.init_state(m1, syn.THETA_START)
-    t1 = time.perf_counter()
-    for k in range(n_incr):
-        s1, _, _, _ = oracle.eval_batch(tree, deps[k][:m1], theta[k][:m1], 1.0, s1, tol=TOL, threads=1)
-    dt1 = time.perf_counter() - t1
-    path = "plastic ramp" if ramp else "random walk"
-    return {"value": n_points * n_incr / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n_points} points x increments 1-{n_incr} of the K=8 {path}, tol {TOL}",
-            "one_core": {"value": m1 * n_incr / dt1, "sample": f"{m1} points, same increments"}}
+    for k in range(first, first + steps):
+        s, _, _, it = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
+        its.append(np.asarray(it))
+    el = time.perf_counter() - t0
+    return m * steps / el, float(np.concatenate(its).mean()), el
+
+
+def cpu_baseline(first, steps, threads=None, plastic=False, n_points=1024, n_one=64):
+    """The FP64 oracle on the host cores, on the GPU arm's timed increments
+    (a bounded sample of the points), and on one core (a smaller sample)."""
+    threads = threads or os.cpu_count() or 1
+    v, it, _ = oracle_on_timed_increments(n_points, first, steps, threads, plastic)
+    v1, it1, _ = oracle_on_timed_increments(n_one, first, steps, 1, plastic)
+    path = "plastic ramp" if plastic else "random walk"
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"points 1-{n_points} of the K=8 {path} batch, timed increments "
+                      f"{first + 1}-{first + steps} (increments 1-{first} untimed), tol {TOL}",
+            "mean_iters": it,
+            "one_core": {"value": v1, "mean_iters": it1, "sample": f"points 1-{n_one}, same increments"}}
 
 
 def run_reference(args):
@@ -248,29 +275,25 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2109_14403_gb300 import synthetic as syn
     oracle.build()
     threads = os.cpu_count() or 1
-    n = 512
-    w, nrm, ph = syn.tree(K_DEPTH)
-    tree = oracle.Tree(K_DEPTH, w, nrm, ph, syn.materials())
-    deps, theta = syn.random_walk_k8(n_points=n, n_incr=args.warmup + args.steps)
-    s = tree.init_state(n, syn.THETA_START)
-    for k in range(args.warmup):
-        s, *_ = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
-    t0 = time.perf_counter()
-    for k in range(args.warmup, args.warmup + args.steps):
-        s, *_ = oracle.eval_batch(tree, deps[k], theta[k], 1.0, s, tol=TOL, threads=threads)
-    el = time.perf_counter() - t0
-    v = n * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    n = 1024
+    plastic = args.workload == "plastic"
+    first = N_GEN + args.warmup
+    v, mean_it, el = oracle_on_timed_increments(n, first, args.steps, threads, plastic)
+    path = "plastic ramp" if plastic else "random walk"
+    line = {"impl": "reference", "metric": METRIC + (", plastic ramp" if plastic else ""), "value": v,
+            "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"K={K_DEPTH} DMN random walk, {n} of {N_POINTS} points per step (oracle sample)",
-                       "precision": "fp64", "tol": TOL},
+            "config": dict(arm_config(N_POINTS, first, args.steps, plastic, args.gpus),
+                           path="FP64 oracle on the host cores",
+                           oracle_sample=f"points 1-{n} of the {N_POINTS} ({path}), every timed increment"),
+            "mean_iters": mean_it,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{n} points per increment, {args.steps} increments after {args.warmup} warm-up"},
+                             "sample": f"{n} points per increment, increments {first + 1}-{first + args.steps} "
+                                       f"after {first} untimed"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -873,14 +896,11 @@ def main():
     w, nrm, ph = syn.tree(K_DEPTH)
     mats = syn.materials()
     steps, warm = args.steps, args.warmup
-    n_gen = 6  # increments of the FP64 solver that produce the training pairs
-    first = n_gen + warm  # first timed increment
+    n_gen = N_GEN  # increments of the timed batch whose FP64 solutions are training pairs
+    first = n_gen + warm  # increments before the first timed one
     n_incr = first + steps
     plastic = args.workload == "plastic"
-    if plastic:  # the K = 4 configuration's ramp on the K = 8 batch: the matrix flows
-        deps_h, theta_h = syn.ramp_k4(n_points=n, n_incr=n_incr, seed=42 + rank)
-    else:
-        deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=n_incr, seed=42 + rank)
+    deps_h, theta_h = _load_path(n_incr, plastic, n_points=n, seed=42 + rank)
     D = torch.tensor(deps_h, device=dev)
     T = torch.tensor(theta_h, device=dev)
 
@@ -901,16 +921,20 @@ def main():
         feats.append(net.features(D[k], T[k], s, s_prev))
         tgts.append(net.targets(s, s1))
         s_prev, s = s, s1
-    # two more seeded batches of the same load distribution: about 1e6 pairs
+    # two more seeded batches of the same load distribution, solved along the
+    # whole path (as far as the timed increments reach), pairs from every
+    # other increment: the network sees the load states of the timed
+    # increments without seeing the timed batch there
     for extra in range(2):
-        dh, th = syn.random_walk_k8(n_points=n, n_incr=n_gen, seed=1000 + 17 * extra + rank)
+        dh, th = _load_path(n_incr, plastic, n_points=n, seed=1000 + 17 * extra + rank)
         De, Te = torch.tensor(dh, device=dev), torch.tensor(th, device=dev)
         xp = None
         xs = fp64.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
-        for k in range(n_gen):
+        for k in range(n_incr):
             x1, _, _, _ = fp64.eval(De[k], Te[k], 1.0, xs)
-            feats.append(net.features(De[k], Te[k], xs, xp))
-            tgts.append(net.targets(xs, x1))
+            if k % 2 == 1:
+                feats.append(net.features(De[k], Te[k], xs, xp))
+                tgts.append(net.targets(xs, x1))
             xp, xs = xs, x1
         del De, Te, xp, xs, x1
     F, Tg = torch.cat(feats), torch.cat(tgts)
@@ -928,6 +952,8 @@ def main():
     torch.cuda.synchronize()
     train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
                   "gen_and_train_s": time.perf_counter() - t0,
+                  "pairs_from": f"FP64 solves: increments 1-{n_gen} of the timed batch; increments "
+                                f"2, 4, .., {2 * (n_incr // 2)} of two more batches drawn with other seeds",
                   "network": "773 -> 3 x 512 SiLU -> 765, bf16/fp32-accumulate tcgen05, AMSGrad"}
     del X, Y
     start_prev, start_cur = s_prev.clone(), s.clone()
@@ -962,20 +988,7 @@ def main():
     it = torch.empty(n, dtype=torch.int32, device=dev)
     for k in range(n_gen, first):
         warm_step(k, it)
-    # accuracy of the headline path against the FP64 solution at tol 1e-13 on
-    # the first timed increment (untimed)
-    ref = DMN(K_DEPTH, w, nrm, ph, mats, tol=1e-13, precision="fp64")
-    _, oref, _, _ = ref.eval(D[first], T[first], 1.0, bufs[1])
-    p0, c0 = bufs[0].clone(), bufs[1].clone()
-    warm_step(first, it)
-    sig, sref = out[:, :6], oref[:, :6]
-    acc_err = ((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item()
-    tan, tref = out[:, 6:42], oref[:, 6:42]
-    tan_rel = (tan - tref).norm(dim=1) / tref.norm(dim=1)
-    tan_err = {"max": tan_rel.max().item(), "median": tan_rel.median().item()}
-    ref.close()
-    bufs[0], bufs[1] = p0, c0
-    snap_prev, snap_cur = p0.clone(), c0.clone()  # the end-to-end run repeats these increments
+    snap_prev, snap_cur = bufs[0].clone(), bufs[1].clone()  # later runs repeat the timed increments
     barrier()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     kev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(steps)]
@@ -991,9 +1004,9 @@ def main():
     total_ms = ev[0].elapsed_time(ev[steps])
     solve_ms = statistics.mean(kev[j][0].elapsed_time(kev[j][1]) for j in range(steps))
     itc = torch.cat(iters)
-    fallback_rate = float(((st & 4) != 0).float().mean().item())
     hist = torch.bincount(itc.cpu().long()).tolist()
     mean_iters = float(itc.float().mean().item())
+    iters_per_incr = [round(float(x.float().mean().item()), 4) for x in iters]
     t_max = max_over_ranks(total_ms, world, dev)
     value = whole_job_rate(n, world, steps, t_max)
 
@@ -1007,7 +1020,7 @@ def main():
     it_p = torch.empty(n, dtype=torch.int32).pin_memory()
     dd = torch.empty((n, 6), dtype=torch.float64, device=dev)
     th = torch.empty(n, dtype=torch.float64, device=dev)
-    bufs[0], bufs[1] = snap_prev, snap_cur
+    bufs[0], bufs[1] = snap_prev.clone(), snap_cur.clone()
     it = torch.empty(n, dtype=torch.int32, device=dev)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1028,6 +1041,32 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     e2e = {"value": whole_job_rate(n, world, steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": n * 7 * 8, "d2h_bytes_per_step": n * (57 * 8 + 8)}
+
+    # ---- accuracy and fallbacks on every timed increment (untimed): the timed
+    #      increments again from the same states (the solve is deterministic,
+    #      so these are the timed results bit for bit), each against the FP64
+    #      path at tol 1e-13 from the same state
+    ref = DMN(K_DEPTH, w, nrm, ph, mats, tol=1e-13, precision="fp64")
+    bufs[0], bufs[1] = snap_prev.clone(), snap_cur.clone()
+    acc, tan_max, tan_med, fb, same = [], [], [], 0, True
+    it = torch.empty(n, dtype=torch.int32, device=dev)
+    for j in range(steps):
+        _, oref, _, _ = ref.eval(D[first + j], T[first + j], 1.0, bufs[1])
+        warm_step(first + j, it)
+        sig, sref = out[:, :6], oref[:, :6]
+        acc.append(((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item())
+        tan_rel = (out[:, 6:42] - oref[:, 6:42]).norm(dim=1) / oref[:, 6:42].norm(dim=1)
+        tan_max.append(tan_rel.max().item())
+        tan_med.append(tan_rel.median().item())
+        fb += int(((st & 4) != 0).sum().item())
+        same = same and bool(torch.equal(it, iters[j]))
+    ref.close()
+    accuracy = {"max_rel_stress_err_vs_fp64": max(acc), "rel_stress_err_per_increment": acc,
+                "rel_tangent_err_vs_fp64": {"max": max(tan_max), "median": statistics.median(tan_med)},
+                "reference": "FP64 path at tol 1e-13 from the same state", "points": n,
+                "increments": f"every timed increment ({first + 1}-{first + steps})",
+                "replay_matches_timed_iterations": same}
+    fallback_rate = fb / (n * steps)
 
     # ---- the same increments without the network, mixed and FP64
     variants = {}
@@ -1080,21 +1119,15 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 + float-float (2xf32) + bf16 MLP",
             "data": "synthetic",
-            "config": {"workload": f"K={K_DEPTH} DMN, {n} Gauss points per GPU, "
-                                   + ("plastic ramp (0.1 % in 11 + N(0, 1e-4), +3 K) increments " if plastic
-                                      else "random-walk increments ") + f"{first}-{first + steps - 1}",
-                       "path": "mixed precision + learned warm start (MLP inference in the step)",
-                       "tol": TOL, "points_per_gpu": n,
-                       "l2": "inputs larger than L2 (device state ~0.9 GB)",
-                       "parallelism": f"replicas x{world} (independent points)"},
-            "accuracy": {"max_rel_stress_err_vs_fp64": acc_err, "rel_tangent_err_vs_fp64": tan_err,
-                         "reference": "FP64 path at tol 1e-13", "points": n},
-            "iter_hist": hist, "mean_iters": mean_iters, "fallback_rate": fallback_rate,
+            "config": arm_config(n, first, steps, plastic, world),
+            "accuracy": accuracy,
+            "iter_hist": hist, "mean_iters": mean_iters, "mean_iters_per_increment": iters_per_incr,
+            "fallback_rate": fallback_rate,
             "warm_start_training": train_info, "variants": variants,
             "solve_kernel_ms": solve_ms,
             "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 6 * steps}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(ramp=plastic)
+        line["cpu_baseline"] = cpu_baseline(first, steps, plastic=plastic)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -92,6 +92,24 @@ dmn_status dmn_mlp_get_params(dmn_mlp m, float *h_params);
 dmn_status dmn_mlp_set_params(dmn_mlp m, const float *h_params);
 /* Gradients of the last train step, same layout (synchronous). */
 dmn_status dmn_mlp_get_grads(dmn_mlp m, float *h_grads);
+/* Optimiser state of the last train step, same layout (synchronous): the
+   first and second moment estimates and the running maximum of the second
+   (each pointer may be NULL). */
+dmn_status dmn_mlp_get_moments(dmn_mlp m, float *h_m, float *h_v, float *h_vmax);
+
+/* The optimiser step dmn_mlp_train_step ends with, on caller buffers: one
+   AMSGrad step (Reddi, Kale, Kumar 2018, the running maximum of the second
+   moment; the optimiser the paper trains its DMN with, Sec. 5.3) with Adam's
+   bias correction, in FP32, element-wise over n entries of device arrays:
+     m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,  vmax = max(vmax, v),
+     w -= lr (m / (1 - b1^t)) / (sqrt(vmax / (1 - b2^t)) + eps),
+   t = step >= 1; m, v, vmax start at 0.  The bias corrections are formed in
+   FP64 from the FP32 betas and rounded once.  dmn_mlp_train_step uses
+   b1 = 0.9, b2 = 0.999, eps = 1e-8.  Stream-ordered; DMN_ERR_ARG for
+   step < 1, betas outside [0, 1), eps <= 0 or a NULL pointer. */
+dmn_status dmn_mlp_amsgrad(dmn_stream stream, int64_t n, float *d_w, const float *d_g, float *d_m,
+                           float *d_v, float *d_vmax, float lr, float beta1, float beta2, float eps,
+                           int64_t step);
 /* Normalisation statistics (synchronous): feature mean and 1/std [n_in],
    target mean and std [n_out]. */
 dmn_status dmn_mlp_get_normalization(dmn_mlp m, float *h_fmean, float *h_finv, float *h_tmean,

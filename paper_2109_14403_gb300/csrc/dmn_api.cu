@@ -105,6 +105,105 @@ const char *material_row(const dmn_material &m, double r[kMatWords]) {
   r[11] = 0.0;
   return nullptr;
 }
+
+const char *build_tree_tables(int K, const double *leaf_w, const double *normals,
+                              const uint8_t *phase_map, const dmn_material *mats, int n_mats,
+                              double *mat, double *node, float *node_df, int *zoff, int *hoff,
+                              double *wl, TreeLayout *lay, char *why, size_t why_len) {
+  const int nleaf = 1 << K, N = nleaf - 1;
+  lay->Emax = 0.0;
+  for (int i = 0; i < n_mats; ++i) {
+    const char *bad = material_row(mats[i], &mat[kMatWords * i]);
+    if (bad) {
+      snprintf(why, why_len, "material %d (kind %d): %s", i, mats[i].kind, bad);
+      return why;
+    }
+    if (mats[i].E > lay->Emax) lay->Emax = mats[i].E;
+  }
+  // weights (Sec. 3.1): w > 0, sum 1
+  double ws = 0.0;
+  for (int j = 0; j < nleaf; ++j) {
+    if (!(leaf_w[j] > 0.0) || !isfinite(leaf_w[j])) {
+      snprintf(why, why_len, "leaf weight %d is not positive", j);
+      return why;
+    }
+    if (phase_map[j] >= n_mats) {
+      snprintf(why, why_len, "phase_map[%d]=%d >= n_mats", j, phase_map[j]);
+      return why;
+    }
+    ws += leaf_w[j];
+  }
+  if (fabs(ws - 1.0) > 1e-12) {
+    snprintf(why, why_len, "weights sum to %.17g", ws);
+    return why;
+  }
+  // node table: n (normalised), c1, c2, w, w c1 c2, 1/(w c1 c2), n/sqrt2;
+  // weight propagation bottom-up (Sec. 3.1), the subtree weights of a level
+  // replacing those of the level below in place
+  for (int j = 0; j < nleaf; ++j) wl[j] = leaf_w[j];
+  for (int k = K; k >= 1; --k) {
+    const int cnt = 1 << (k - 1);
+    for (int i = 0; i < cnt; ++i) {
+      const double wa = wl[2 * i], wb = wl[2 * i + 1], w = wa + wb;
+      const int p = nleaf - (1 << k) + i;
+      const double *nv = normals + 3 * p;
+      const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      if (!(nn > 0.0) || !isfinite(nn)) {
+        snprintf(why, why_len, "normal %d is zero or not finite", p);
+        return why;
+      }
+      double *r = &node[kNodeWords * p];
+      r[0] = nv[0] / nn;
+      r[1] = nv[1] / nn;
+      r[2] = nv[2] / nn;
+      r[3] = wa / w;
+      r[4] = 1.0 - r[3];
+      r[5] = w;
+      r[6] = w * r[3] * r[4];
+      r[7] = 1.0 / r[6];
+      for (int c = 0; c < 3; ++c) r[8 + c] = r[c] / sqrt(2.0);
+      r[11] = 0.0;
+      wl[i] = w;  // wl[2i], wl[2i+1] are read before slot i is written
+    }
+  }
+  // float-float node table: (hi, lo) of n, n/sqrt2, c1, c2; then 1/(w c1 c2), w c1 c2
+  for (int p = 0; p < N; ++p) {
+    const double *r = &node[kNodeWords * p];
+    const double v[8] = {r[0], r[1], r[2], r[8], r[9], r[10], r[3], r[4]};
+    float *o = &node_df[kNodeDfl * p];
+    for (int i = 0; i < kNodeDfl; ++i) o[i] = 0.0f;
+    for (int i = 0; i < 8; ++i) {
+      const float hi = (float)v[i];
+      o[2 * i] = hi;
+      o[2 * i + 1] = (float)(v[i] - (double)hi);
+    }
+    o[16] = (float)r[7];
+    o[17] = (float)r[6];
+  }
+  // z offsets in a state block; with PA66 leaves also the offsets of the
+  // leaves' history words in the solve's shared memory
+  int off = 8 + 3 * N, law = 1, hw = 0;
+  for (int j = 0; j < nleaf; ++j) {
+    const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
+    if (kind == DMN_MAT_J2_PERZYNA && law < 2) law = 2;
+    if (kind == DMN_MAT_PA66) law = 3;
+    if (zwl > 0) {
+      zoff[j] = off;
+      off += zwl;
+      hoff[j] = hw;
+      hw += material_hist_words(kind);
+    } else {
+      zoff[j] = -1;
+      hoff[j] = -1;
+    }
+  }
+  lay->zend = off;
+  lay->zw = off - (8 + 3 * N);
+  lay->SW = off + (off & 1);
+  lay->law = law;
+  lay->hw = hw;
+  return nullptr;
+}
 }  // namespace dmn
 
 static thread_local char g_err[512] = "";
@@ -172,94 +271,21 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
                 o.solve_variant);
   const int nleaf = 1 << K, N = nleaf - 1;
 
-  // materials: derived bulk and shear moduli (Sec. 4)
-  std::vector<double> mat(kMatWords * n_mats);
-  double Emax = 0.0;
-  for (int i = 0; i < n_mats; ++i) {
-    const char *why = material_row(mats[i], &mat[kMatWords * i]);
-    if (why) return fail(DMN_ERR_ARG, "dmn_create: material %d (kind %d): %s", i, mats[i].kind, why);
-    if (mats[i].E > Emax) Emax = mats[i].E;
-  }
-  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
-
-  // weights (Sec. 3.1): w > 0, sum 1
-  double ws = 0.0;
-  for (int j = 0; j < nleaf; ++j) {
-    if (!(leaf_w[j] > 0.0) || !isfinite(leaf_w[j]))
-      return fail(DMN_ERR_ARG, "dmn_create: leaf weight %d is not positive", j);
-    if (phase_map[j] >= n_mats)
-      return fail(DMN_ERR_ARG, "dmn_create: phase_map[%d]=%d >= n_mats", j, phase_map[j]);
-    ws += leaf_w[j];
-  }
-  if (fabs(ws - 1.0) > 1e-12) return fail(DMN_ERR_ARG, "dmn_create: weights sum to %.17g", ws);
-
-  // node table: n (normalised), c1, c2, w, w c1 c2, 1/(w c1 c2); weight
-  // propagation bottom-up (Sec. 3.1)
-  std::vector<double> node(kNodeWords * N);
-  std::vector<double> wl(leaf_w, leaf_w + nleaf), wn;
-  for (int k = K; k >= 1; --k) {
-    const int cnt = 1 << (k - 1);
-    wn.assign(cnt, 0.0);
-    for (int i = 0; i < cnt; ++i) {
-      const double wa = wl[2 * i], wb = wl[2 * i + 1], w = wa + wb;
-      const int p = nleaf - (1 << k) + i;
-      const double *nv = normals + 3 * p;
-      const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-      if (!(nn > 0.0) || !isfinite(nn))
-        return fail(DMN_ERR_ARG, "dmn_create: normal %d is zero or not finite", p);
-      double *r = &node[kNodeWords * p];
-      r[0] = nv[0] / nn;
-      r[1] = nv[1] / nn;
-      r[2] = nv[2] / nn;
-      r[3] = wa / w;
-      r[4] = 1.0 - r[3];
-      r[5] = w;
-      r[6] = w * r[3] * r[4];
-      r[7] = 1.0 / r[6];
-      for (int c = 0; c < 3; ++c) r[8 + c] = r[c] / sqrt(2.0);
-      r[11] = 0.0;
-      wn[i] = w;
-    }
-    wl.swap(wn);
-  }
-  // float-float node table: (hi, lo) of n, n/sqrt2, c1, c2; then 1/(w c1 c2), w c1 c2
-  std::vector<float> node_df(kNodeDfl * N, 0.0f);
-  for (int p = 0; p < N; ++p) {
-    const double *r = &node[kNodeWords * p];
-    const double v[8] = {r[0], r[1], r[2], r[8], r[9], r[10], r[3], r[4]};
-    float *o = &node_df[kNodeDfl * p];
-    for (int i = 0; i < 8; ++i) {
-      const float hi = (float)v[i];
-      o[2 * i] = hi;
-      o[2 * i + 1] = (float)(v[i] - (double)hi);
-    }
-    o[16] = (float)r[7];
-    o[17] = (float)r[6];
-  }
-  // z offsets in a state block; with PA66 leaves also the offsets of the
-  // leaves' history words in the solve's shared memory
+  // tree setup (Sec. 3.1) and material rows (Sec. 4)
+  std::vector<double> mat(kMatWords * n_mats), node(kNodeWords * N), wscr(nleaf);
+  std::vector<float> node_df(kNodeDfl * N);
   std::vector<int> zoff(nleaf), hoff(nleaf);
-  int off = 8 + 3 * N, law = 1, hw = 0;
-  for (int j = 0; j < nleaf; ++j) {
-    const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
-    if (kind == DMN_MAT_J2_PERZYNA && law < 2) law = 2;
-    if (kind == DMN_MAT_PA66) law = 3;
-    if (zwl > 0) {
-      zoff[j] = off;
-      off += zwl;
-      hoff[j] = hw;
-      hw += material_hist_words(kind);
-    } else {
-      zoff[j] = -1;
-      hoff[j] = -1;
-    }
-  }
-  const int zend = off;
-  int zw = zend - (8 + 3 * N);
-  if (off & 1) off += 1;
+  TreeLayout lay;
+  char why[256];
+  if (build_tree_tables(K, leaf_w, normals, phase_map, mats, n_mats, mat.data(), node.data(),
+                        node_df.data(), zoff.data(), hoff.data(), wscr.data(), &lay, why, sizeof(why)))
+    return fail(DMN_ERR_ARG, "dmn_create: %s", why);
+  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * lay.Emax;
+  const int law = lay.law, zend = lay.zend, off = lay.SW;
+  int zw = lay.zw;
   if (law == 2 && K > 9) return fail(DMN_ERR_ARG, "dmn_create: Perzyna leaves need K <= 9 (K=%d)", K);
   if (law == 3 && K > 8) return fail(DMN_ERR_ARG, "dmn_create: PA66 leaves need K <= 8 (K=%d)", K);
-  if (law == 3) zw = hw;  // the solve keeps the leaves' history, not z, in shared memory
+  if (law == 3) zw = lay.hw;  // the solve keeps the leaves' history, not z, in shared memory
 
   dmn_handle h = new dmn_handle_s();
   memset(h, 0, sizeof(*h));

@@ -27,6 +27,22 @@ const char *material_row(const dmn_material &m, double row[kMatWords]);
 // the words of shared memory the solve keeps for it (kind 3: its history)
 int material_z_words(int kind);
 int material_hist_words(int kind);
+// Tree setup of Sec. 3.1 on the host, into caller-provided arrays (so that a
+// caller without a heap can use it): validates the materials, leaf weights
+// (> 0, sum 1), phase map and normals; writes the material rows
+// mat[n_mats][kMatWords], the node tables node[N][kNodeWords] and
+// node_df[N][kNodeDfl] (weight propagation bottom-up, normalised normals),
+// the state offsets zoff[2^K] of the leaves' internal variables and, with
+// PA66 leaves, the shared-memory offsets hoff[2^K] of their history.
+// wscratch: 2^K doubles.  Returns nullptr, or the reason the input is invalid.
+struct TreeLayout {
+  int SW, zend, zw, law, hw;  // state words, end of z, z words, largest kind, history words
+  double Emax;                // largest Young's modulus (default residual floor)
+};
+const char *build_tree_tables(int K, const double *leaf_w, const double *normals,
+                              const uint8_t *phase_map, const dmn_material *mats, int n_mats,
+                              double *mat, double *node, float *node_df, int *zoff, int *hoff,
+                              double *wscratch, TreeLayout *lay, char *why, size_t why_len);
 cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
                           int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);

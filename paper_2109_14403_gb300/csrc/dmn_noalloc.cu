@@ -21,6 +21,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "../../include/dmn.h"
 #include "dmn_internal.h"
 
@@ -35,8 +37,10 @@ constexpr int kMaxDevices = 64;
 // node tables, leaf tables, material table and the work-queue counter
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-static void *g_scratch_addr[kMaxDevices];       // device address, per device
-static bool g_scratch_ready[kMaxDevices];
+// device address of the array, per device (nullptr until looked up); host
+// threads that make their first call on a device at the same time may both
+// look it up, and both store the same address
+static std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 // errors are reported through dmn_last_error() like every other call
 dmn_status na_fail(dmn_status s, const char *fmt, ...) {
@@ -82,86 +86,29 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
     return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: invalid options");
 
   const int nleaf = 1 << K, N = nleaf - 1;
-  // ---- host tables (fixed-size arrays on the stack: no heap either) ----
-  double mat[kMatWords * kMaxMats];
-  double Emax = 0.0;
-  for (int i = 0; i < n_mats; ++i) {
-    const char *why = material_row(mats[i], &mat[kMatWords * i]);
-    if (why) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: material %d (kind %d): %s", i, mats[i].kind, why);
-    if (mats[i].E > Emax) Emax = mats[i].E;
-  }
-  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * Emax;
-  double ws = 0.0;
-  for (int j = 0; j < nleaf; ++j) {
-    if (!(leaf_w[j] > 0.0) || !isfinite(leaf_w[j]))
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: leaf weight %d is not positive", j);
-    if (phase_map[j] >= n_mats)
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: phase_map[%d]=%d >= n_mats", j, phase_map[j]);
-    ws += leaf_w[j];
-  }
-  if (fabs(ws - 1.0) > 1e-12)
-    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: weights sum to %.17g", ws);
-
+  // ---- host tables: fixed-size arrays on the stack (no heap either).  The
+  //      caller's leaf weights and phase map are copied too, so that every
+  //      upload below reads call-local memory only ----
   constexpr int NMAX = (1 << kNoAllocMaxK) - 1, LMAX = 1 << kNoAllocMaxK;
+  double mat[kMatWords * kMaxMats];
   double node[kNodeWords * NMAX];
   float node_df[kNodeDfl * NMAX];
-  double wl[LMAX], wn[LMAX];
-  for (int j = 0; j < nleaf; ++j) wl[j] = leaf_w[j];
-  for (int k = K; k >= 1; --k) {  // weight propagation, Sec. 3.1
-    const int cnt = 1 << (k - 1);
-    for (int i = 0; i < cnt; ++i) {
-      const double wa = wl[2 * i], wb = wl[2 * i + 1], w = wa + wb;
-      const int p = nleaf - (1 << k) + i;
-      const double *nv = normals + 3 * p;
-      const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
-      if (!(nn > 0.0) || !isfinite(nn))
-        return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: normal %d is zero or not finite", p);
-      double *r = &node[kNodeWords * p];
-      r[0] = nv[0] / nn;
-      r[1] = nv[1] / nn;
-      r[2] = nv[2] / nn;
-      r[3] = wa / w;
-      r[4] = 1.0 - r[3];
-      r[5] = w;
-      r[6] = w * r[3] * r[4];
-      r[7] = 1.0 / r[6];
-      for (int c = 0; c < 3; ++c) r[8 + c] = r[c] / sqrt(2.0);
-      r[11] = 0.0;
-      wn[i] = w;
-    }
-    for (int i = 0; i < cnt; ++i) wl[i] = wn[i];
-  }
-  for (int p = 0; p < N; ++p) {
-    const double *r = &node[kNodeWords * p];
-    const double v[8] = {r[0], r[1], r[2], r[8], r[9], r[10], r[3], r[4]};
-    float *q = &node_df[kNodeDfl * p];
-    for (int i = 0; i < kNodeDfl; ++i) q[i] = 0.0f;
-    for (int i = 0; i < 8; ++i) {
-      const float hi = (float)v[i];
-      q[2 * i] = hi;
-      q[2 * i + 1] = (float)(v[i] - (double)hi);
-    }
-    q[16] = (float)r[7];
-    q[17] = (float)r[6];
-  }
-  int zoff[LMAX];
-  int off = 8 + 3 * N, law = 1;
+  double wscr[LMAX], lw[LMAX];
+  int zoff[LMAX], hoff[LMAX];
+  uint8_t ph[LMAX];
   for (int j = 0; j < nleaf; ++j) {
-    const int kind = mats[phase_map[j]].kind, zwl = material_z_words(kind);
-    if (kind == DMN_MAT_PA66)
-      return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: PA66 leaves (kind 3) need a dmn_handle");
-    if (kind == DMN_MAT_J2_PERZYNA) law = 2;
-    if (zwl > 0) {
-      zoff[j] = off;
-      off += zwl;
-    } else {
-      zoff[j] = -1;
-    }
+    lw[j] = leaf_w[j];
+    ph[j] = phase_map[j];
   }
-  const int zend = off;
-  const int zw = zend - (8 + 3 * N);
-  if (off & 1) off += 1;
-  const int SW = off;
+  TreeLayout lay;
+  char why[256];
+  if (build_tree_tables(K, lw, normals, ph, mats, n_mats, mat, node, node_df, zoff, hoff, wscr, &lay,
+                        why, sizeof(why)))
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: %s", why);
+  if (lay.law == 3)
+    return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: PA66 leaves (kind 3) need a dmn_handle");
+  if (!(o.res_floor > 0.0)) o.res_floor = 1e-8 * lay.Emax;
+  const int law = lay.law, zend = lay.zend, zw = lay.zw, SW = lay.SW;
   const size_t sbytes = sizeof(double) * (size_t)SW * (size_t)n_points;
   const char *sa = (const char *)d_state_in, *sb = (const char *)d_state_out;
   if (sa < sb + sbytes && sb < sa + sbytes)
@@ -186,15 +133,14 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return na_fail(DMN_ERR_INTERNAL, "device %d out of range", dev);
-  if (!g_scratch_ready[dev]) {
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
+    e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
     if (e != cudaSuccess)
       return na_fail(DMN_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_scratch_addr[dev] = ptr;
-    g_scratch_ready[dev] = true;
+    g_scratch_addr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+  unsigned char *base = static_cast<unsigned char *>(addr);
   const bool mixed = o.precision == DMN_PREC_MIXED;
   int num_sms = 0, smem_optin = 0, blocks_per_sm = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -205,8 +151,9 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
   if (e != cudaSuccess) return na_fail(DMN_ERR_CUDA, "prepare_solve: %s", cudaGetErrorString(e));
   if (blocks_per_sm < 1) return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: kernel does not fit one SM");
 
-  // ---- upload the tables (stream-ordered; the host arrays may go out of
-  //      scope on return because pageable copies are staged before it) ----
+  // ---- upload the tables (stream-ordered copies from the call-local
+  //      arrays above, which are pageable memory: the copy is staged before
+  //      cudaMemcpyAsync returns, so they may go out of scope on return) ----
   cudaStream_t s = (cudaStream_t)stream;
   struct {
     size_t off;
@@ -214,8 +161,8 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
     size_t bytes;
   } up[] = {{o_node, node, sizeof(double) * kNodeWords * N},
             {o_ndf, node_df, sizeof(float) * kNodeDfl * N},
-            {o_leafw, leaf_w, sizeof(double) * nleaf},
-            {o_phase, phase_map, (size_t)nleaf},
+            {o_leafw, lw, sizeof(double) * nleaf},
+            {o_phase, ph, (size_t)nleaf},
             {o_zoff, zoff, sizeof(int) * nleaf},
             {o_mat, mat, sizeof(double) * kMatWords * n_mats}};
   for (const auto &u : up) {

@@ -485,8 +485,17 @@ cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, in
                           int *blocks_per_sm) {
   const size_t smem = solve_smem_bytes(K, zw, n_mats, mixed, variant, law);
   KernelFn f = pick(K, mixed, variant, law);
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  // One kernel instance serves every tree of a depth range (the compact
+  // instances do not depend on K), and its attributes are global to the
+  // process: raise them, never lower them, so that a handle prepared for a
+  // larger tree (more shared memory, a larger carveout) stays launchable
+  // after a smaller tree has been prepared.
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
   if (e != cudaSuccess) return e;
+  if (int(smem) > fa.maxDynamicSharedSizeBytes &&
+      (e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+    return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem)) != cudaSuccess)
     return e;
   // shared memory carveout: the smallest configuration that holds the
@@ -507,7 +516,8 @@ cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, in
         break;
       }
     int pct = pick_b >= size_t(per_sm) ? 100 : int(pick_b * 100 / size_t(per_sm));
-    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess)
+    if (pct > fa.preferredShmemCarveout &&
+        (e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess)
       return e;
   }
   return cudaSuccess;

@@ -263,6 +263,20 @@ __global__ void k_amsgrad(int64_t count, float *w, const float *g, float *m, flo
   }
 }
 
+// optimiser constants of the training step (AMSGrad defaults)
+constexpr float kBeta1 = 0.9f, kBeta2 = 0.999f, kEps = 1e-8f;
+
+// One AMSGrad step at iteration step >= 1.  The bias corrections 1 - b^t are
+// formed in FP64 from the FP32 betas and rounded once: in FP32, 1 - powf(b2, t)
+// for b2 near 1 would lose about 5 of its 24 bits to cancellation.
+cudaError_t amsgrad(cudaStream_t s, int64_t n, float *w, const float *g, float *m, float *v, float *vmax,
+                    float lr, float b1, float b2, float eps, int64_t step) {
+  const float bc1 = float(1.0 - pow(double(b1), double(step)));
+  const float bc2 = float(1.0 - pow(double(b2), double(step)));
+  k_amsgrad<<<blocks_for(n), 256, 0, s>>>(n, w, g, m, v, vmax, lr, b1, b2, eps, bc1, bc2);
+  return cudaGetLastError();
+}
+
 // bf16 weights and their transpose from the fp32 master copy
 __global__ void k_pack(int rows, int cols, const float *w32, bf16 *w, bf16 *wt) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(rows) * cols;
@@ -631,12 +645,35 @@ extern "C" dmn_status dmn_mlp_train_step(dmn_mlp m, dmn_stream stream, int64_t n
     }
   }
   m->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float bc1 = 1.0f - powf(b1, float(m->step)), bc2 = 1.0f - powf(b2, float(m->step));
-  k_amsgrad<<<blocks_for(m->nparam), 256, 0, s>>>(m->nparam, m->params, m->grads, m->m, m->v,
-                                                   m->vmax, lr, b1, b2, 1e-8f, bc1, bc2);
+  if ((e = amsgrad(s, m->nparam, m->params, m->grads, m->m, m->v, m->vmax, lr, kBeta1, kBeta2, kEps,
+                   m->step)) != cudaSuccess)
+    return cuda_fail(e, "amsgrad");
   if ((e = pack_all(m, s)) != cudaSuccess) return cuda_fail(e, "pack");
   return DMN_OK;
+}
+
+extern "C" dmn_status dmn_mlp_amsgrad(dmn_stream stream, int64_t n, float *d_w, const float *d_g,
+                                      float *d_m, float *d_v, float *d_vmax, float lr, float beta1,
+                                      float beta2, float eps, int64_t step) {
+  set_error_message("");
+  if (n < 0 || step < 1) return fail(DMN_ERR_ARG, "dmn_mlp_amsgrad: n >= 0 and step >= 1 required");
+  if (n == 0) return DMN_OK;
+  if (!d_w || !d_g || !d_m || !d_v || !d_vmax) return fail(DMN_ERR_ARG, "dmn_mlp_amsgrad: NULL pointer");
+  if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) ||
+      !isfinite(lr))
+    return fail(DMN_ERR_ARG, "dmn_mlp_amsgrad: 0 <= beta < 1, eps > 0 required");
+  cudaError_t e = amsgrad((cudaStream_t)stream, n, d_w, d_g, d_m, d_v, d_vmax, lr, beta1, beta2, eps, step);
+  return e == cudaSuccess ? DMN_OK : cuda_fail(e, "dmn_mlp_amsgrad");
+}
+
+extern "C" dmn_status dmn_mlp_get_moments(dmn_mlp m, float *h_m, float *h_v, float *h_vmax) {
+  if (!m) return fail(DMN_ERR_ARG, "dmn_mlp_get_moments: NULL");
+  cudaError_t e = cudaSuccess;
+  if (h_m && e == cudaSuccess) e = cudaMemcpy(h_m, m->m, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost);
+  if (h_v && e == cudaSuccess) e = cudaMemcpy(h_v, m->v, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost);
+  if (h_vmax && e == cudaSuccess)
+    e = cudaMemcpy(h_vmax, m->vmax, sizeof(float) * m->nparam, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? DMN_OK : cuda_fail(e, "dmn_mlp_get_moments");
 }
 
 extern "C" dmn_status dmn_mlp_predict(dmn_mlp m, dmn_stream stream, int64_t n, const void *d_x_bf16,

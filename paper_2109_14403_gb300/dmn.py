@@ -70,6 +70,9 @@ SIGNATURES = {
     "dmn_mlp_get_params": (_I32, [_P, _P]),
     "dmn_mlp_set_params": (_I32, [_P, _P]),
     "dmn_mlp_get_grads": (_I32, [_P, _P]),
+    "dmn_mlp_get_moments": (_I32, [_P, _P, _P, _P]),
+    "dmn_mlp_amsgrad": (_I32, [_P, _I64, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_float, _I64]),
     "dmn_mlp_get_normalization": (_I32, [_P, _P, _P, _P, _P]),
     "dmn_gemm_bf16_tn": (_I32, [_P, _I32, _I32, _I32, _P, _P, _P]),
     "dmn_eval_warm": (_I32, [_P, _P, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P]),

@@ -145,6 +145,13 @@ class MLP:
         _check(load().dmn_mlp_get_grads(self._h, h.ctypes.data_as(_P)), "dmn_mlp_get_grads")
         return h
 
+    def moments(self):
+        """(m, v, vmax) of the optimiser after the last train step."""
+        m, v, vm = (np.empty(self.n_params, np.float32) for _ in range(3))
+        _check(load().dmn_mlp_get_moments(self._h, m.ctypes.data_as(_P), v.ctypes.data_as(_P),
+                                          vm.ctypes.data_as(_P)), "dmn_mlp_get_moments")
+        return m, v, vm
+
     def normalization(self):
         fm, fi = np.empty(self.n_in, np.float32), np.empty(self.n_in, np.float32)
         tm, ts = np.empty(self.n_out, np.float32), np.empty(self.n_out, np.float32)
@@ -152,6 +159,16 @@ class MLP:
                                                 tm.ctypes.data_as(_P), ts.ctypes.data_as(_P)),
                "dmn_mlp_get_normalization")
         return fm, fi, tm, ts
+
+
+def amsgrad(w, g, m, v, vmax, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One FP32 AMSGrad step on CUDA tensors, in place (``dmn_mlp_amsgrad``)."""
+    import torch
+    n = w.numel()
+    ptrs = [_dev(t, torch.float32, (n,), name) for t, name in
+            ((w, "w"), (g, "g"), (m, "m"), (v, "v"), (vmax, "vmax"))]
+    _check(load().dmn_mlp_amsgrad(_stream_ptr(stream), n, *ptrs, float(lr), float(beta1), float(beta2),
+                                  float(eps), int(step)), "dmn_mlp_amsgrad")
 
 
 def gemm_bf16_tn(a, b, out=None, stream=None):

@@ -181,3 +181,36 @@ def test_trained_parameters_drive_the_online_evaluation(K):
     assert st.cpu().numpy()[0] == 0
     assert np.abs(C - ref).max() <= 1e-10 * np.abs(ref).max()
     d.close()
+
+
+def test_linear_amsgrad_matches_oracle_over_three_steps():
+    """dmn_linear_amsgrad (FP64) against the FP64 AMSGrad step, element by
+    element, over three steps on seeded parameters and gradients; the third
+    step's gradients are small, so most entries keep the running maximum."""
+    import ctypes
+    from oracle import optim
+    from paper_2109_14403_gb300 import dmn
+    dev = _dev()
+    lib = dmn.load()
+    rng = np.random.default_rng(8)
+    n = 5_001
+    mag = 10.0 ** rng.uniform(-6, 1, n)
+    G = [rng.normal(size=n) * mag, rng.normal(size=n) * mag, rng.normal(size=n) * mag * 1e-3]
+    w0 = rng.normal(size=n)
+    X, Gd = torch.tensor(w0, device=dev), torch.empty(n, dtype=torch.float64, device=dev)
+    M, S, SM = (torch.zeros(n, dtype=torch.float64, device=dev) for _ in range(3))
+    wr, mr, sr, smr = w0.copy(), np.zeros(n), np.zeros(n), np.zeros(n)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for t, g in enumerate(G, start=1):
+        Gd.copy_(torch.tensor(g))
+        rc = lib.dmn_linear_amsgrad(stream, n, P(X), P(Gd), P(M), P(S), P(SM), 2e-3, 0.9, 0.999, 1e-8, t)
+        assert rc == dmn.DMN_OK, lib.dmn_last_error().decode()
+        wr, mr, sr, smr = optim.amsgrad_step(wr, g, mr, sr, smr, t, 2e-3, 0.9, 0.999, 1e-8)
+        torch.cuda.synchronize()
+        # FP64 on both sides; the kernel may fuse a multiply-add that numpy
+        # rounds twice, so a few ulp per step (w: of its O(1) scale)
+        np.testing.assert_allclose(X.cpu().numpy(), wr, rtol=1e-14, atol=1e-15)
+        for got, ref in ((M, mr), (S, sr), (SM, smr)):
+            np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
+    assert np.mean(smr > sr) > 0.5

@@ -117,3 +117,46 @@ def test_noalloc_rejects_a_tree_beyond_its_fixed_array():
                               _ptr(it))
     assert rc == dmn.DMN_ERR_ARG
     assert b"outside 1..8" in lib.dmn_last_error()
+
+
+def test_a_smaller_tree_leaves_a_live_larger_handle_launchable():
+    """The compact solve kernel is one instance for every depth up to 8, and
+    its shared-memory limit is a process-wide attribute.  Preparing a K = 4
+    tree (through this entry point, or through a second handle) must not
+    lower the limit below what a live K = 8 handle launches with: the K = 8
+    handle's next dmn_eval still runs and gives the same bits."""
+    from paper_2109_14403_gb300 import DMN, dmn
+    dev = _dev()
+    lib = dmn.load()
+    K8, n = 8, 64
+    w8, nrm8, ph8 = syn.tree(K8)
+    rows = syn.materials()
+    big = DMN(K8, w8, nrm8, ph8, rows, tol=1e-12, precision="mixed", solve_variant=13)
+    deps_h, theta_h = syn.random_walk_k8(n_points=n, n_incr=1)
+    deps = torch.tensor(deps_h[0] * 8.0, device=dev)
+    theta = torch.tensor(theta_h[0], device=dev)
+    s0 = big.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+    _, out0, st0, _ = big.eval(deps, theta, 1.0, s0)
+    torch.cuda.synchronize()
+    assert (st0.cpu().numpy() == 0).all()
+
+    # a K = 4 tree on the same kernel instance, through the allocation-free call
+    K4 = 4
+    w4, nrm4, ph4 = syn.tree(K4)
+    opt = dmn.dmn_options()
+    lib.dmn_default_options(ctypes.byref(opt))
+    opt.tol, opt.precision, opt.solve_variant = 1e-12, dmn.PREC_MIXED, 13
+    small = DMN(K4, w4, nrm4, ph4, rows, tol=1e-12, precision="mixed", solve_variant=13)
+    s4 = small.init_state(torch.full((n,), syn.THETA_START, dtype=torch.float64, device=dev))
+    mats = dmn.materials_from_rows(rows)
+    _noalloc(lib, K4, w4, nrm4, ph4, mats, opt, deps, theta, 1.0, s4)
+    _, out1, st1, _ = big.eval(deps, theta, 1.0, s0)
+    # ... and through a second handle's own launch
+    small.eval(deps, theta, 1.0, s4)
+    _, out2, st2, _ = big.eval(deps, theta, 1.0, s0)
+    torch.cuda.synchronize()
+    for o, s in ((out1, st1), (out2, st2)):
+        assert (s.cpu().numpy() == 0).all()
+        np.testing.assert_array_equal(o.cpu().numpy(), out0.cpu().numpy())
+    small.close()
+    big.close()
