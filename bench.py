@@ -140,7 +140,7 @@ class ClockSampler:
 
 # the translation unit of the headline solve kernel and everything it includes
 SOLVE_SOURCES = ("dfl.cuh", "dmn_internal.h", "dmn_kernels.cuh", "dmn_solve_compact.cu", "pa66.cuh",
-                 "solve_common.cuh", "solve_compact.cuh")
+                 "solve_common.cuh", "solve_compact.cuh", "solve_warp.cuh", "dmn_solve_warp8.cu")
 
 
 def _code_only(text):
@@ -179,6 +179,8 @@ def solve_kernel_name(variant, precision, law=1):
     if law == 2:
         return ("dmn_solve_compact<double, double, 128, 1, 2>" if precision == "fp64"
                 else "dmn_solve_compact<float, dfl, 128, 3, 2>")
+    if 22 <= variant <= 24 and precision == "mixed":
+        return f"dmn_solve_warp<8, 4, {variant - 20}, 1>"
     if variant >= 11:
         if precision == "fp64":
             return "dmn_solve_compact<double, double, 128, 1, 1>"
@@ -855,6 +857,8 @@ def main():
                     help="uneven, cyclic and linear (fp64 or fp32 laminates) workloads only")
     ap.add_argument("--matrix", default="perzyna", choices=["perzyna", "pa66"],
                     help="cyclic workload only: the matrix law")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="solve variant of the timed mixed path (default: the tuning table's)")
     ap.add_argument("--workload", default="random_walk",
                     choices=["random_walk", "plastic", "uneven", "mlp", "large", "cyclic", "linear"])
     args = ap.parse_args()
@@ -959,7 +963,7 @@ def main():
     start_prev, start_cur = s_prev.clone(), s.clone()
 
     # ---- the timed path: mixed precision + learned warm start
-    mixed = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision="mixed")
+    mixed = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision="mixed", solve_variant=args.variant)
     bufs = [start_prev.clone(), start_cur.clone(), torch.empty_like(start_cur)]
     out = torch.empty((n, 57), dtype=torch.float64, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)

@@ -146,8 +146,19 @@ typedef struct {
                            (upper tree levels on one warp, strains updated by
                            the Newton step), FP64 (mixed: as 12); 12, 13, 14
                            = compact mixed kernel for 2, 3 or 4 CTAs per SM.  The
-                           2..4 choice has no effect in FP64.  Any other value
-                           is DMN_ERR_ARG.  Chosen by the autotuner          */
+                           2..4 choice has no effect in FP64.  22, 23, 24 =
+                           one warp per Gauss point (lane l condenses the
+                           subtree under level-6 node l in registers, levels
+                           5..1 by shuffles; four points per CTA, register
+                           budget for 2, 3 or 4 CTAs per SM): mixed
+                           precision, 6 <= K <= 8, thermoelastic and J2
+                           leaves only, else dmn_create returns DMN_ERR_ARG;
+                           the handle then also owns a scratch buffer of
+                           (2^(K-5) - 1) x 21 floats per lane of every
+                           resident warp (about 22 MB at K = 8 on 152 SMs)
+                           and dmn_eval_noalloc rejects these variants.  Any
+                           other value is DMN_ERR_ARG.  Chosen by the
+                           autotuner                                          */
 } dmn_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libdmn.so")
-SOURCES = ["dmn_api.cu", "dmn_solve.cu", "dmn_solve_compact.cu", "dmn_solve_compact_vp.cu", "dmn_solve_compact_pa66.cu", "dmn_noalloc.cu", "dmn_drive.cu", "dmn_linear.cu", "mlp.cu"]
+SOURCES = ["dmn_api.cu", "dmn_solve.cu", "dmn_solve_compact.cu", "dmn_solve_compact_vp.cu", "dmn_solve_compact_pa66.cu", "dmn_solve_warp.cu", "dmn_solve_warp8.cu", "dmn_noalloc.cu", "dmn_drive.cu", "dmn_linear.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

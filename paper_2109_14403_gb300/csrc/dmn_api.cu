@@ -31,6 +31,7 @@ struct dmn_handle_s {
   int *d_zoff;           // [nleaf]
   int *d_hoff;           // [nleaf], law 3 only
   double *d_mat;         // [n_mats][kMatWords]
+  float *d_gh;           // warp form: G_p, h_p slots of the resident warps (scratch)
 };
 
 namespace dmn {
@@ -247,6 +248,7 @@ static void free_handle(dmn_handle h) {
   cudaFree(h->d_mat);
   cudaFree(h->d_queue);
   cudaFree(h->d_open);
+  cudaFree(h->d_gh);
   delete h;
 }
 
@@ -267,7 +269,7 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED))
     return fail(DMN_ERR_ARG, "dmn_create: invalid options");
   if (!solve_variant_valid(o.solve_variant))
-    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4, 11, 12, 13, 14}",
+    return fail(DMN_ERR_ARG, "dmn_create: solve_variant %d not in {0, 2, 3, 4, 11, 12, 13, 14, 22, 23, 24}",
                 o.solve_variant);
   const int nleaf = 1 << K, N = nleaf - 1;
 
@@ -286,6 +288,10 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
   if (law == 2 && K > 9) return fail(DMN_ERR_ARG, "dmn_create: Perzyna leaves need K <= 9 (K=%d)", K);
   if (law == 3 && K > 8) return fail(DMN_ERR_ARG, "dmn_create: PA66 leaves need K <= 8 (K=%d)", K);
   if (law == 3) zw = lay.hw;  // the solve keeps the leaves' history, not z, in shared memory
+  if (is_warp_variant(o.solve_variant) && !warp_form_supports(K, o.precision == DMN_PREC_MIXED, law))
+    return fail(DMN_ERR_ARG,
+                "dmn_create: solve_variant %d (one warp per point) needs mixed precision, 6 <= K <= 8 "
+                "and thermoelastic / J2 leaves only", o.solve_variant);
 
   dmn_handle h = new dmn_handle_s();
   memset(h, 0, sizeof(*h));
@@ -329,7 +335,10 @@ extern "C" dmn_status dmn_create(dmn_handle *out, int32_t K, const double *leaf_
       (law == 3 && (e = cudaMalloc(&h->d_hoff, sizeof(int) * nleaf)) != cudaSuccess) ||
       (e = cudaMalloc(&h->d_mat, sizeof(double) * kMatWords * n_mats)) != cudaSuccess ||
       (e = cudaMalloc(&h->d_queue, sizeof(unsigned long long))) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_open, sizeof(unsigned long long))) != cudaSuccess) {
+      (e = cudaMalloc(&h->d_open, sizeof(unsigned long long))) != cudaSuccess ||
+      (is_warp_variant(o.solve_variant) &&
+       (e = cudaMalloc(&h->d_gh, warp_scratch_bytes_per_cta(K) * size_t(h->num_sms) *
+                                     size_t(h->blocks_per_sm))) != cudaSuccess)) {
     free_handle(h);
     return cuda_fail(e, "cudaMalloc");
   }
@@ -436,8 +445,10 @@ static dmn_status eval_impl(dmn_handle h, dmn_stream stream, int64_t n_points,
   P.queue = h->d_queue;
   P.da0 = d_da;
   P.skip = d_skip;
-  int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm;
-  if (grid > n_points) grid = n_points;
+  P.gh = h->d_gh;
+  int64_t grid = (int64_t)h->num_sms * h->blocks_per_sm;  // the scratch holds this many CTAs
+  const int64_t per_cta = is_warp_variant(h->opt.solve_variant) ? warp_form_warps() : 1;
+  if (grid > (n_points + per_cta - 1) / per_cta) grid = (n_points + per_cta - 1) / per_cta;
   cudaError_t e = launch_solve(P, mixed, h->opt.solve_variant, (int)grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "dmn_eval launch");
   return DMN_OK;

@@ -43,6 +43,19 @@ const char *build_tree_tables(int K, const double *leaf_w, const double *normals
                               const uint8_t *phase_map, const dmn_material *mats, int n_mats,
                               double *mat, double *node, float *node_df, int *zoff, int *hoff,
                               double *wscratch, TreeLayout *lay, char *why, size_t why_len);
+// the warp-per-point form (dmn_solve_warp.cu, dmn_solve_warp8.cu): variants
+// 22..24 (CTAs per SM the register budget is sized for: variant - 20), depth
+// 6..8, kinds 0 and 1, mixed precision; it needs a scratch slot per resident
+// warp
+bool is_warp_variant(int variant);
+bool warp_form_supports(int K, bool mixed, int law);
+int warp_form_warps();
+size_t warp_smem_bytes(int K, int n_mats);
+size_t warp_scratch_bytes_per_cta(int K);
+KernelFn warp_kernel(int K, int minb);
+KernelFn warp_kernel8(int minb);
+// threads per CTA of the kernel a variant selects
+int solve_block_threads(int K, int variant, int law);
 cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, int law,
                           int *blocks_per_sm);
 cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid, cudaStream_t s);

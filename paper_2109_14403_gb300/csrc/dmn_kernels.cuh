@@ -76,6 +76,7 @@ struct SolveParams {
   const double *deps, *theta, *sin;
   double *sout, *out;
   int *status, *iters;
+  float *gh;               // warp form: per-warp slots of the lanes' G_p, h_p (scratch)
 };
 
 // ------------------------------------------------------------------ helpers

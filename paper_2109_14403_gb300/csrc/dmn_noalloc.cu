@@ -84,6 +84,10 @@ extern "C" dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const do
       (o.precision != DMN_PREC_FP64 && o.precision != DMN_PREC_MIXED) ||
       !solve_variant_valid(o.solve_variant))
     return na_fail(DMN_ERR_ARG, "dmn_eval_noalloc: invalid options");
+  if (is_warp_variant(o.solve_variant))
+    return na_fail(DMN_ERR_ARG,
+                   "dmn_eval_noalloc: solve_variant %d (one warp per point) needs the scratch of a dmn_handle",
+                   o.solve_variant);
 
   const int nleaf = 1 << K, N = nleaf - 1;
   // ---- host tables: fixed-size arrays on the stack (no heap either).  The

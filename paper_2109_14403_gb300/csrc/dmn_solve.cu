@@ -455,14 +455,24 @@ static size_t owner_smem_bytes(int K, int zw, int n_mats, bool mixed) {
 // takes the compact instances that include that leaf law
 // (dmn_solve_compact_vp.cu, K <= 9), whatever the variant; one with PA66
 // leaves (law 3) the instances of dmn_solve_compact_pa66.cu (K <= 8).
+bool is_warp_variant(int variant) { return variant >= 22 && variant <= 24; }
 bool solve_variant_valid(int variant) {
-  return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 14);
+  return variant == 0 || (variant >= 2 && variant <= 4) || (variant >= 11 && variant <= 14) ||
+         is_warp_variant(variant);
+}
+static bool uses_warp_form(int K, bool mixed, int variant, int law) {
+  return is_warp_variant(variant) && warp_form_supports(K, mixed, law);
+}
+int solve_block_threads(int K, int variant, int law) {
+  (void)law;
+  return is_warp_variant(variant) ? 32 * warp_form_warps() : (1 << (K - 1));
 }
 static bool is_compact(int K, int variant, int law) {
   return law >= 2 ? K <= 9 : (K <= 8 && variant >= 11);
 }
 
 static KernelFn pick(int K, bool mixed, int variant, int law) {
+  if (uses_warp_form(K, mixed, variant, law)) return warp_kernel(K, variant - 20);
   if (law == 3) return compact_kernel_pa66(K, mixed);
   if (law >= 2) return compact_kernel_vp(K, mixed);
   if (is_compact(K, variant, law)) return compact_kernel(K, mixed, variant - 10);
@@ -476,6 +486,7 @@ static KernelFn pick(int K, bool mixed, int variant, int law) {
 }
 
 size_t solve_smem_bytes(int K, int zw, int n_mats, bool mixed, int variant, int law) {
+  if (uses_warp_form(K, mixed, variant, law)) return warp_smem_bytes(K, n_mats);
   if (law == 3) return compact_smem_bytes_pa(K, zw, n_mats, mixed);
   return is_compact(K, variant, law) ? compact_smem_bytes(K, zw, n_mats, mixed)
                                      : owner_smem_bytes(K, zw, n_mats, mixed);
@@ -496,7 +507,8 @@ cudaError_t prepare_solve(int K, int zw, int n_mats, bool mixed, int variant, in
   if (int(smem) > fa.maxDynamicSharedSizeBytes &&
       (e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, 1 << (K - 1), smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, solve_block_threads(K, variant, law),
+                                                          smem)) != cudaSuccess)
     return e;
   // shared memory carveout: the smallest configuration that holds the
   // resident CTAs (plus 1 KB per CTA for the system); the rest of the SM's
@@ -527,7 +539,7 @@ cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid
   const size_t smem = solve_smem_bytes(P.K, P.zw, P.n_mats, mixed, variant, P.law);
   cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  pick(P.K, mixed, variant, P.law)<<<grid, P.G, smem, s>>>(P);
+  pick(P.K, mixed, variant, P.law)<<<grid, solve_block_threads(P.K, variant, P.law), smem, s>>>(P);
   return cudaGetLastError();
 }
 

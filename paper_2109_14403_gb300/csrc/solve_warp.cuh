@@ -1,0 +1,614 @@
+// solve_warp.cuh -- third form of the Algorithm 1 solve (arXiv 2109.14403,
+// Sec. 3.3): one warp per Gauss point, for trees of depth 6 <= K <= 8.
+//
+// Mapping.  Level 6 of the tree has 32 nodes: lane l owns the subtree under
+// level-6 node l, i.e. M = 2^(K-6) bottom laminates (2M leaves) and the
+// 2M - 1 laminates of levels 6..K above them.  A Newton pass condenses that
+// subtree in the lane's registers (a recursion over the levels, fully
+// unrolled), then the five levels 5..1 by shuffles (level k node j on lane
+// j 2^(6-k)).  Nothing waits for another warp: a CTA holds W independent
+// points, one per warp, and its warps meet only once, when the CTA starts.
+//
+// Strains.  Lane l keeps the strain of its level-6 node (float-float) in
+// shared memory; the strains below it are formed in every pass from the
+// jumps a of the lane's own nodes (eq. DMN kinematics: child 1 gets
+// +c2 B a_p, child 2 -c1 B a_p).  After a Newton step the level-6 strain
+// takes the float-float sum of the B da terms of its five upper ancestors,
+// which the back-substitution forms on the way down anyway.
+//
+// Back-substitution.  da_p = -(G_p de_p + h_p) with G_p, h_p of the pass's
+// condensation: for the five upper levels in shared memory, for the lane's
+// own 2M - 1 nodes in a per-warp slot of global scratch memory laid out
+// [node of the lane][21][lane] (a warp's stores and loads of one component
+// are one 128-byte line; the slot is reused point after point, so it stays
+// in L2).
+//
+// The condensation, the residual and the leaf laws are those of
+// dmn_kernels.cuh (leaf_eval, combine), as in the other two forms.
+#pragma once
+#include "dmn_internal.h"
+#include "solve_common.cuh"
+
+namespace dmn {
+
+namespace warp_detail {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUpNodes = 31;  // levels 5..1
+
+// per-warp shared memory, in bytes (8-byte HP, 4-byte TF), for depth K
+__host__ __device__ constexpr int wlay_a(int) { return 0; }                                   // HP[3N]
+__host__ __device__ constexpr int wlay_e6(int K) { return 8 * 3 * ((1 << K) - 1); }           // HP[32][6]
+__host__ __device__ constexpr int wlay_trn(int K) { return wlay_e6(K) + 8 * 32 * 6; }          // HP[2^K]
+__host__ __device__ constexpr int wlay_eb(int K) { return wlay_trn(K) + 8 * (1 << K); }        // HP[12], double[6]
+__host__ __device__ constexpr int wlay_out(int K) { return wlay_eb(K) + 8 * 18; }              // HP[8] (sigma, D, X), TF[40]
+__host__ __device__ constexpr int wlay_da(int K) { return wlay_out(K) + 8 * 8 + 4 * 40; }      // TF[3N]
+__host__ __device__ constexpr int wlay_ghu(int K) { return wlay_da(K) + 4 * 3 * ((1 << K) - 1); }  // TF[31][21]
+__host__ __device__ constexpr int wlay_mat(int K) {
+  return (wlay_ghu(K) + 4 * kUpNodes * 21 + 15) & ~15;  // MatPt[n_mats] of the warp's point
+}
+// bytes of one warp's region (MatPt rows included)
+__host__ __device__ inline int wlay_bytes(int K, int n_mats, int matpt_bytes) {
+  return (wlay_mat(K) + n_mats * matpt_bytes + 15) & ~15;
+}
+// global scratch floats per warp: the lane's own 2M - 1 nodes x 21 x 32 lanes
+__host__ __device__ constexpr int wscratch_floats(int K) { return (2 * (1 << (K - 6)) - 1) * 21 * 32; }
+
+// Per-warp context of one pass
+template <typename TF, typename HP>
+struct WCtx {
+  const SolveParams *P;
+  HP *a_s;            // jumps (HP), paper node order
+  TF *da_s;           // Newton increment
+  const HP *trn_s;    // traces of the leaf strains at t^n
+  const MatPt<TF, HP> *mp;
+  float *ghw;         // the warp's global scratch slot
+  const double *sin;  // the point's state block (z^n)
+  double *sout;       // the point's output state block (z of the pass parked here)
+  int lane;
+  bool full;
+  TF r2;
+  HP Dsum, Xsum;
+};
+
+// node p's TF constants and HP constants
+template <typename TF, typename HP>
+__device__ __forceinline__ void node_all(const SolveParams &P, int p, NodeHP<HP> &nd, TF n[3], TF &c1,
+                                         TF &c2, TF &iwcc, TF &wcc) {
+  load_node(P, p, nd);
+  load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+}
+
+// children's strains of node p with strain e: e + c2 B a_p, e - c1 B a_p
+template <typename HP>
+__device__ __forceinline__ void child_strains(const NodeHP<HP> &nd, const HP *a, const HP e[6], HP el[6],
+                                              HP er[6]) {
+  const HP av[3] = {a[0], a[1], a[2]};
+  HP J[6];
+  bvec_hp(nd, av, J);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    el[c] = e[c] + nd.c2 * J[c];
+    er[c] = e[c] - nd.c1 * J[c];
+  }
+}
+
+// one leaf: its z^n from the input state (FP64 -> HP), the leaf law, its z
+// of this pass parked in the output state
+template <typename TF, typename HP, int LAW>
+__device__ __forceinline__ void leaf_at(WCtx<TF, HP> &c, int j, const HP e[6], HP sig[6], HP &D, HP &X,
+                                        Rec<TF> &rec) {
+  const SolveParams &P = *c.P;
+  const int ph = __ldg(P.phase + j), zo = __ldg(P.zoff + j);
+  const MatPt<TF, HP> &m = c.mp[ph];
+  HP zn[LAW >= 2 ? 13 : 7];
+  HP *znew = nullptr;
+  HP *tag = nullptr;
+  if (zo >= 0) {
+    const int nz = (LAW >= 2 && m.kind == 2) ? 13 : 7;
+#pragma unroll
+    for (int q = 0; q < (LAW >= 2 ? 13 : 7); ++q)
+      zn[q] = q < nz ? hp_load(ld_stream(c.sin + zo + q), tag) : hp_zero(tag);
+    znew = reinterpret_cast<HP *>(c.sout + zo);
+  } else {
+#pragma unroll
+    for (int q = 0; q < (LAW >= 2 ? 13 : 7); ++q) zn[q] = hp_zero(tag);
+  }
+  HP zdummy[13];
+  leaf_eval<TF, HP, LAW>(m, e, zn, c.trn_s[j], sig, D, X, rec, znew ? znew : zdummy, c.full);
+}
+
+// Condensed record of the subtree under node i of level LEV (strain e),
+// with its plain weighted stress sum S; G/h of the node into the lane's
+// scratch slot; |r|^2, D and X accumulated in the context.
+template <int K, int LEV, typename TF, typename HP, int LAW>
+__device__ __forceinline__ void subtree(WCtx<TF, HP> &c, int i, const HP e[6], Rec<TF> &rec, HP S[6]) {
+  const SolveParams &P = *c.P;
+  const int p = (1 << K) - (1 << LEV) + i;
+  const int slot = ((1 << (LEV - 6)) - 1) + (i - (c.lane << (LEV - 6)));
+  NodeHP<HP> nd;
+  load_node(P, p, nd);
+  HP el[6], er[6];
+  child_strains(nd, c.a_s + 3 * p, e, el, er);
+  TF rbv[3];
+  TF n[3], c1, c2, iwcc, wcc;
+  load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+  Rec<TF> rr;
+  if constexpr (LEV == K) {
+    // bottom laminate i: leaves 2i, 2i+1
+    HP sl[6], sr[6], DL, DR, XL, XR;
+    leaf_at<TF, HP, LAW>(c, 2 * i, el, sl, DL, XL, rec);
+    leaf_at<TF, HP, LAW>(c, 2 * i + 1, er, sr, DR, XR, rr);
+    HP *tag = nullptr;
+    const HP wL = hp_from(__ldg(P.leafw + 2 * i), tag), wR = hp_from(__ldg(P.leafw + 2 * i + 1), tag);
+    if (c.full) {
+      c.Dsum = c.Dsum + (wL * DL + wR * DR);
+      c.Xsum = c.Xsum + (wL * XL + wR * XR);
+    }
+    HP dsh[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      S[q] = wL * sl[q] + wR * sr[q];
+      dsh[q] = sl[q] - sr[q];
+    }
+    HP rbh[3];
+    btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_p / (w c1 c2)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) rbv[r] = tf_of(rbh[r], (TF *)nullptr);
+    c.r2 += wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
+  } else {
+    HP SR[6];
+    subtree<K, LEV + 1, TF, HP, LAW>(c, 2 * i, el, rec, S);
+    subtree<K, LEV + 1, TF, HP, LAW>(c, 2 * i + 1, er, rr, SR);
+    HP dh[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      dh[q] = nd.c2 * S[q] - nd.c1 * SR[q];
+      S[q] = S[q] + SR[q];
+    }
+    HP rh[3];
+    btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
+    TF rv[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) rv[r] = tf_of(rh[r], (TF *)nullptr);
+    c.r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) rbv[r] = rv[r] * iwcc;
+  }
+  TF gh[21];
+  combine<TF>(rec, rr, n, c1, c2, rbv, gh, c.full);
+  float *g = c.ghw + slot * 21 * 32 + c.lane;
+#pragma unroll
+  for (int q = 0; q < 21; ++q) g[q * 32] = gh[q];
+}
+
+// Back-substitution in the lane's subtree: node i of level LEV with the
+// strain perturbation de from its ancestors.
+template <int K, int LEV, typename TF, typename HP>
+__device__ __forceinline__ void subtree_back(WCtx<TF, HP> &c, int i, const TF de[6]) {
+  const SolveParams &P = *c.P;
+  const int p = (1 << K) - (1 << LEV) + i;
+  const int slot = ((1 << (LEV - 6)) - 1) + (i - (c.lane << (LEV - 6)));
+  const float *g = c.ghw + slot * 21 * 32 + c.lane;
+  TF gh[21];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) gh[q] = g[q * 32];
+  TF da[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    TF s = gh[18 + r];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s += gh[6 * r + q] * de[q];
+    da[r] = -s;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    c.da_s[3 * p + r] = da[r];
+    c.a_s[3 * p + r] = hp_add_tf(c.a_s[3 * p + r], da[r]);
+  }
+  if constexpr (LEV < K) {
+    TF n[3], c1, c2, iwcc, wcc;
+    load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+    TF J[6], dl[6], dr[6];
+    bvec(n, da, J);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      dl[q] = de[q] + c2 * J[q];
+      dr[q] = de[q] - c1 * J[q];
+    }
+    subtree_back<K, LEV + 1, TF, HP>(c, 2 * i, dl);
+    subtree_back<K, LEV + 1, TF, HP>(c, 2 * i + 1, dr);
+  }
+}
+
+// traces of the leaf strains at t^n under node i of level LEV (trace tr):
+// tr(B a) = a . n
+template <int K, int LEV, typename HP>
+__device__ __forceinline__ void subtree_traces(const SolveParams &P, const HP *a_s, HP *trn_s, int i, HP tr) {
+  const int p = (1 << K) - (1 << LEV) + i;
+  NodeHP<HP> nd;
+  load_node(P, p, nd);
+  const HP *a = a_s + 3 * p;
+  const HP t = a[0] * nd.n[0] + a[1] * nd.n[1] + a[2] * nd.n[2];
+  const HP tl = tr + nd.c2 * t, trr = tr - nd.c1 * t;
+  if constexpr (LEV == K) {
+    trn_s[2 * i] = tl;
+    trn_s[2 * i + 1] = trr;
+  } else {
+    subtree_traces<K, LEV + 1, HP>(P, a_s, trn_s, 2 * i, tl);
+    subtree_traces<K, LEV + 1, HP>(P, a_s, trn_s, 2 * i + 1, trr);
+  }
+}
+
+// strain (or trace) of lane l's level-6 node from the root value: the five
+// upper ancestors' terms, root first (+c2 B a on the way to child 1, -c1 B a
+// to child 2)
+template <int K, typename HP>
+__device__ __forceinline__ void level6_strain(const SolveParams &P, const HP *a_s, int l, const HP root[6],
+                                              HP e[6]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) e[q] = root[q];
+#pragma unroll
+  for (int k = 1; k <= 5; ++k) {
+    const int i = l >> (6 - k), p = (1 << K) - (1 << k) + i;
+    const bool right = (l >> (5 - k)) & 1;
+    NodeHP<HP> nd;
+    load_node(P, p, nd);
+    const HP av[3] = {a_s[3 * p], a_s[3 * p + 1], a_s[3 * p + 2]};
+    HP J[6];
+    bvec_hp(nd, av, J);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) e[q] = right ? e[q] - nd.c1 * J[q] : e[q] + nd.c2 * J[q];
+  }
+}
+template <int K, typename HP>
+__device__ __forceinline__ HP level6_trace(const SolveParams &P, const HP *a_s, int l, HP tr) {
+#pragma unroll
+  for (int k = 1; k <= 5; ++k) {
+    const int i = l >> (6 - k), p = (1 << K) - (1 << k) + i;
+    const bool right = (l >> (5 - k)) & 1;
+    NodeHP<HP> nd;
+    load_node(P, p, nd);
+    const HP t = a_s[3 * p] * nd.n[0] + a_s[3 * p + 1] * nd.n[1] + a_s[3 * p + 2] * nd.n[2];
+    tr = right ? tr - nd.c1 * t : tr + nd.c2 * t;
+  }
+  return tr;
+}
+
+template <typename TF>
+__device__ __forceinline__ void rec_shfl(Rec<TF> &dst, const Rec<TF> &src, int off) {
+  rec_shfl_down(dst, src, off, kFull, 32);
+}
+
+}  // namespace warp_detail
+
+// K: depth (6..8); W: warps (points) per CTA; MINB: CTAs per SM the
+// register budget is sized for; LAW as in the compact form (1: thermoelastic
+// and J2 leaves; 2: also Perzyna leaves).  Mixed precision only (TF = float,
+// HP = float-float).
+template <int K, int W, int MINB, int LAW>
+__global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams P) {
+  using namespace warp_detail;
+  using TF = float;
+  using HP = dfl;
+  constexpr int N = (1 << K) - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  HP *tag = nullptr;
+  // CTA-wide: the point-independent part of the material constants
+  MatPt<TF, HP> *mp_static = reinterpret_cast<MatPt<TF, HP> *>(smem_raw);
+  const int wbytes = wlay_bytes(K, P.n_mats, int(sizeof(MatPt<TF, HP>)));
+  unsigned char *wbase = smem_raw + ((P.n_mats * int(sizeof(MatPt<TF, HP>)) + 15) & ~15) + warp * wbytes;
+  HP *a_s = reinterpret_cast<HP *>(wbase + wlay_a(K));
+  HP *e6_s = reinterpret_cast<HP *>(wbase + wlay_e6(K));
+  HP *trn_s = reinterpret_cast<HP *>(wbase + wlay_trn(K));
+  HP *eb = reinterpret_cast<HP *>(wbase + wlay_eb(K));  // eps_bar^{n+1} (HP), deps (HP)
+  double *ebd = reinterpret_cast<double *>(wbase + wlay_eb(K) + 8 * 12);  // eps_bar^{n+1} (FP64)
+  HP *ohp = reinterpret_cast<HP *>(wbase + wlay_out(K));                  // sigma_bar, D_bar, X_bar
+  TF *orec = reinterpret_cast<TF *>(wbase + wlay_out(K) + 8 * 8);         // root record
+  TF *da_s = reinterpret_cast<TF *>(wbase + wlay_da(K));
+  TF *ghu = reinterpret_cast<TF *>(wbase + wlay_ghu(K));
+  MatPt<TF, HP> *mp = reinterpret_cast<MatPt<TF, HP> *>(wbase + wlay_mat(K));
+  float *ghw = P.gh + size_t(blockIdx.x * W + warp) * wscratch_floats(K);
+
+  for (int i = threadIdx.x; i < P.n_mats; i += 32 * W)
+    mat_static<TF, HP>(mp_static[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i), P.dt);
+  __syncthreads();
+  const HP idt = hp_from(1.0 / P.dt, tag);
+  const TF idt_f = TF(1.0 / P.dt);
+  const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
+  constexpr int pu0 = (1 << K) - 32;  // first node of level 5
+
+  for (;;) {
+    unsigned long long q = 0;
+    if (lane == 0) {
+      q = atomicAdd(P.queue, 1ull);
+      while (P.skip && q < (unsigned long long)P.n_points && P.skip[q] != 0) q = atomicAdd(P.queue, 1ull);
+    }
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= (unsigned long long)P.n_points) break;
+    const int64_t pt = int64_t(q);
+    const double *sin = P.sin + pt * P.SW;
+    double *sout = P.sout + pt * P.SW;
+    const double theta = P.theta[pt];
+    // ---- point start: eps_bar, jumps a^n, material constants at theta
+    if (lane < 6) {
+      const double e0 = ld_stream(sin + lane), d = ld_stream(P.deps + pt * 6 + lane);
+      ebd[lane] = e0 + d;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
+      eb[lane] = hp_load(e0 + d, tag);
+      eb[6 + lane] = hp_load(d, tag);
+    }
+    for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
+    if (lane < P.n_mats) {
+      mp[lane] = mp_static[lane];
+      mat_point<TF, HP, LAW>(mp[lane], hp_load(theta, tag), idt, idt_f);
+    }
+    __syncwarp();
+    {
+      // traces of the leaf strains at t^n (the coupling term needs tr eps^n)
+      const HP tr0 = hp_load(ld_stream(sin), tag) + hp_load(ld_stream(sin + 1), tag) +
+                     hp_load(ld_stream(sin + 2), tag);
+      subtree_traces<K, 6, HP>(P, a_s, trn_s, lane, level6_trace<K, HP>(P, a_s, lane, tr0));
+    }
+    __syncwarp();
+    if (P.da0) {  // warm start a^n + da0
+      const float *d0 = P.da0 + pt * (3 * N);
+      for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_add_tf(a_s[i], ld_stream(d0 + i));
+      __syncwarp();
+    }
+    {
+      HP e[6];
+      level6_strain<K, HP>(P, a_s, lane, eb, e);
+#pragma unroll
+      for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+    }
+    bool first = true;
+    int it = 0, bt = 0, status = 0, attempt = 0, it_total = 0;
+    TF gi = TF(1), res_old = TF(0);
+    WCtx<TF, HP> c;
+    c.P = &P;
+    c.a_s = a_s;
+    c.da_s = da_s;
+    c.trn_s = trn_s;
+    c.mp = mp;
+    c.ghw = ghw;
+    c.sin = sin;
+    c.sout = sout;
+    c.lane = lane;
+    Rec<TF> rec;
+    HP S[6];
+    for (;;) {
+      // Algorithm 1 takes at least one Newton step, so the first pass of an
+      // iteration never gives the outputs: it skips their terms
+      c.full = !first;
+      c.r2 = TF(0);
+      c.Dsum = hp_zero(tag);
+      c.Xsum = hp_zero(tag);
+      {
+        HP e[6];
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) e[q2] = e6_s[6 * lane + q2];
+        subtree<K, 6, TF, HP, LAW>(c, lane, e, rec, S);
+      }
+      // ---- levels 5..1 by shuffles: level k node j on lane j 2^(6-k)
+#pragma unroll
+      for (int k = 5; k >= 1; --k) {
+        const int off = 1 << (5 - k);
+        Rec<TF> other;
+        rec_shfl(other, rec, off);
+        HP So[6];
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) So[q2] = hp_shfl_down(kFull, S[q2], off, 32);
+        if ((lane & (2 * off - 1)) == 0) {
+          const int j = lane >> (6 - k), p = (1 << K) - (1 << k) + j;
+          NodeHP<HP> nd;
+          load_node(P, p, nd);
+          HP dh[6];
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) {
+            dh[q2] = nd.c2 * S[q2] - nd.c1 * So[q2];
+            S[q2] = S[q2] + So[q2];
+          }
+          HP rh[3];
+          btvec_hp(nd, dh, rh);
+          TF n[3], c1, c2, iwcc, wcc;
+          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+          const TF rv[3] = {rh[0].hi, rh[1].hi, rh[2].hi};
+          c.r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
+          combine<TF>(rec, other, n, c1, c2, rbv, ghu + 21 * (p - pu0), c.full);
+        }
+      }
+      // ---- residual norm and decision (Algorithm 1), identical on every lane
+      TF r2 = c.r2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(kFull, r2, o);
+      TF sn = TF(0);
+#pragma unroll
+      for (int q2 = 0; q2 < 6; ++q2) sn += S[q2].hi * S[q2].hi;
+      sn = __shfl_sync(kFull, sn, 0);
+      TF den = sqrt(sn);
+      if (den < res_floor) den = res_floor;
+      const TF res = __shfl_sync(kFull, sqrt(r2) / (TF(N) * den), 0);
+      const bool accept = first || (res < res_old) || (bt >= P.maxbt);
+      int action;
+      if (accept) {
+        if (!isfinite(res)) {
+          status = 2;
+          action = ACT_DONE;
+        } else if (!first && res < tol) {
+          status = 0;
+          action = ACT_DONE;
+        } else if (it >= P.maxit) {
+          status = 1;
+          action = ACT_DONE;
+        } else {
+          res_old = res;
+          it += 1;
+          bt = 0;
+          gi = TF(1);
+          action = ACT_STEP;
+        }
+        first = false;
+      } else {
+        action = ACT_BACK;
+      }
+      if (action == ACT_DONE) {
+        if (P.da0 && attempt == 0 && status != 0) {
+          // the warm-started iteration failed: Algorithm 1 again from a^n
+          attempt = 1;
+          it_total = it;
+          __syncwarp();
+          for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
+          __syncwarp();
+          HP e[6];
+          level6_strain<K, HP>(P, a_s, lane, eb, e);
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+          first = true;
+          it = bt = status = 0;
+          gi = TF(1);
+          res_old = TF(0);
+          continue;
+        }
+        break;
+      }
+      __syncwarp();
+      if (action == ACT_STEP) {
+        // ---- back-substitution: levels 1..5 by shuffles, the node's strain
+        //      perturbation de in TF for the Newton chain and the float-float
+        //      sum he of its ancestors' B da terms for the level-6 strain
+        TF de[6] = {TF(0), TF(0), TF(0), TF(0), TF(0), TF(0)};
+        HP he[6];
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) he[q2] = hp_zero(tag);
+#pragma unroll
+        for (int k = 1; k <= 5; ++k) {
+          const int stride = 1 << (6 - k), half = stride >> 1;
+          TF dr[6];
+          HP hr[6];
+          if ((lane & (stride - 1)) == 0) {
+            const int j = lane >> (6 - k), p = (1 << K) - (1 << k) + j;
+            const TF *g = ghu + 21 * (p - pu0);
+            TF da[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              TF s = g[18 + r];
+#pragma unroll
+              for (int q2 = 0; q2 < 6; ++q2) s += g[6 * r + q2] * de[q2];
+              da[r] = -s;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              da_s[3 * p + r] = da[r];
+              a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
+            }
+            NodeHP<HP> nd;
+            TF n[3], c1, c2, iwcc, wcc;
+            node_all(P, p, nd, n, c1, c2, iwcc, wcc);
+            TF J[6];
+            bvec(n, da, J);
+            const HP dah[3] = {hp_add_tf(hp_zero(tag), da[0]), hp_add_tf(hp_zero(tag), da[1]),
+                               hp_add_tf(hp_zero(tag), da[2])};
+            HP Jh[6];
+            bvec_hp(nd, dah, Jh);
+#pragma unroll
+            for (int q2 = 0; q2 < 6; ++q2) {
+              dr[q2] = de[q2] - c1 * J[q2];
+              de[q2] = de[q2] + c2 * J[q2];
+              hr[q2] = he[q2] - nd.c1 * Jh[q2];
+              he[q2] = he[q2] + nd.c2 * Jh[q2];
+            }
+          }
+          const bool recv = (lane & (stride - 1)) == half;
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) {
+            const TF v = __shfl_up_sync(kFull, dr[q2], half);
+            const float vh = __shfl_up_sync(kFull, hr[q2].hi, half);
+            const float vl = __shfl_up_sync(kFull, hr[q2].lo, half);
+            if (recv) {
+              de[q2] = v;
+              he[q2] = {vh, vl};
+            }
+          }
+        }
+        // the level-6 node's strain moves by its ancestors' terms; its own
+        // subtree's jumps take the rest of the increment
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e6_s[6 * lane + q2] + he[q2];
+        subtree_back<K, 6, TF, HP>(c, lane, de);
+      } else {
+        // ---- backtracking (rare): a -= f da, strains again from a
+        const TF f = gi * (TF(1) - gamma);
+        for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
+        __syncwarp();
+        HP e[6];
+        level6_strain<K, HP>(P, a_s, lane, eb, e);
+#pragma unroll
+        for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+        gi *= gamma;
+        bt += 1;
+      }
+      __syncwarp();
+    }
+
+    // ---- outputs and state (the last pass is at the final a)
+    HP Db = c.Dsum, Xb = c.Xsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      Db = Db + hp_shfl_down(kFull, Db, o, 32);
+      Xb = Xb + hp_shfl_down(kFull, Xb, o, 32);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q2 = 0; q2 < 6; ++q2) ohp[q2] = S[q2];
+      ohp[6] = Db;
+      ohp[7] = Xb;
+#pragma unroll
+      for (int q2 = 0; q2 < 21; ++q2) orec[q2] = rec.C[q2];
+#pragma unroll
+      for (int q2 = 0; q2 < 6; ++q2) {
+        orec[21 + q2] = rec.tau[q2];
+        orec[27 + q2] = rec.dd[q2];
+      }
+      orec[33] = rec.gg;
+    }
+    __syncwarp();
+    int bad = 0;
+    for (int cc = lane; cc < kOutWords; cc += 32) {
+      double v;
+      if (cc < 6) v = hp_to(ohp[cc]);
+      else if (cc < 42) v = double(sget(orec, (cc - 6) / 6, (cc - 6) % 6));
+      else if (cc < 48) v = double(orec[21 + cc - 42]);
+      else if (cc == 48) v = hp_to(ohp[6]);
+      else if (cc < 55) v = double(orec[27 + cc - 49]);
+      else if (cc == 55) v = double(orec[33]);
+      else v = hp_to(ohp[7]);
+      if (!isfinite(v)) bad = 1;
+      __stcs(P.out + pt * kOutWords + cc, v);
+    }
+    bad = __any_sync(kFull, bad);
+    if (lane == 0) {
+      P.status[pt] = (bad ? 2 : status) | (attempt ? 4 : 0);
+      P.iters[pt] = it + it_total;
+    }
+    if (lane < 8) sout[lane] = lane < 6 ? ebd[lane] : (lane == 6 ? theta : 0.0);
+    for (int i = lane; i < 3 * N; i += 32) __stcs(sout + 8 + i, hp_to(a_s[i]));
+    // the lane's own leaves: parked float-float z of the last pass -> FP64
+#pragma unroll 1
+    for (int j = lane << (K - 5); j < (lane + 1) << (K - 5); ++j) {
+      const int zo = __ldg(P.zoff + j);
+      if (zo < 0) continue;
+      const int nz = (LAW >= 2 && mp[__ldg(P.phase + j)].kind == 2) ? 13 : 7;
+      const HP *zp = reinterpret_cast<const HP *>(sout + zo);
+      for (int q2 = 0; q2 < nz; ++q2) {
+        const HP v = ld_once(zp + q2);
+        sout[zo + q2] = hp_to(v);
+      }
+    }
+    for (int i = P.zend + lane; i < P.SW; i += 32) sout[i] = 0.0;  // padding word
+    __syncwarp();
+  }
+}
+
+}  // namespace dmn

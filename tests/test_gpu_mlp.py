@@ -134,19 +134,29 @@ def test_amsgrad_kernel_matches_oracle_over_three_steps():
     M, V, VM = (torch.zeros(n, dtype=torch.float32, device=dev) for _ in range(3))
     wr, mr, vr, vmr = w.astype(np.float64), np.zeros(n), np.zeros(n), np.zeros(n)
     ulp = 2.0 ** -23
+    b1d, b2d = float(b1), float(b2)
     for t, g in enumerate(G, start=1):
         Gd.copy_(torch.tensor(g))
         amsgrad(W, Gd, M, V, VM, t, lr, b1, b2, eps)
-        w_prev = wr.copy()
-        wr, mr, vr, vmr = optim.amsgrad_step(wr, g, mr, vr, vmr, t, float(lr), float(b1), float(b2),
-                                             float(eps))
+        w_prev, m_prev, v_prev, vm_prev = wr.copy(), mr.copy(), vr.copy(), vmr.copy()
+        wr, mr, vr, vmr = optim.amsgrad_step(wr, g, mr, vr, vmr, t, float(lr), b1d, b2d, float(eps))
         torch.cuda.synchronize()
-        for dev_t, ref in ((M, mr), (V, vr), (VM, vmr)):
-            got = dev_t.cpu().numpy().astype(np.float64)
-            assert (np.abs(got - ref) <= 4 * ulp * np.abs(ref) + 1e-38).all()
+        gd = g.astype(np.float64)
+        # bounds relative to the operands: b1 m + (1-b1) g can cancel
+        em = 4 * ulp * (b1d * np.abs(m_prev) + (1 - b1d) * np.abs(gd))
+        ev = 4 * ulp * (b2d * v_prev + (1 - b2d) * gd * gd)
+        got_m, got_v, got_vm = (x.cpu().numpy().astype(np.float64) for x in (M, V, VM))
+        assert (np.abs(got_m - mr) <= em + 1e-38).all()
+        assert (np.abs(got_v - vr) <= ev + 1e-38).all()
+        assert (np.abs(got_vm - vmr) <= np.maximum(ev, 4 * ulp * vm_prev) + 1e-38).all()
         got_w = W.cpu().numpy().astype(np.float64)
         step = np.abs(wr - w_prev)
-        assert (np.abs(got_w - wr) <= 4 * ulp * np.abs(wr) + 8 * ulp * step + 1e-38).all()
+        bc1, bc2 = 1 - b1d ** t, 1 - b2d ** t
+        den = np.sqrt(vmr / bc2) + float(eps)
+        # the step carries m's error (through m / bc1), a few roundings of its
+        # own and of the square root; w one rounding of the subtraction
+        e_step = float(lr) * (em / bc1) / den + 8 * ulp * step
+        assert (np.abs(got_w - wr) <= 2 * ulp * np.abs(w_prev) + e_step + 1e-38).all()
         # the comparison follows the GPU's own trajectory from here: both sides
         # continue from the same FP32 values
         wr = got_w
