@@ -1,8 +1,8 @@
 // dmn_solve_warp.cu -- instances of the warp-per-point solve (solve_warp.cuh)
 // for depths 6 and 7, and its host-side sizes; depth 8 is in
 // dmn_solve_warp8.cu (the translation units compile in parallel).
-// Thermoelastic and J2 leaves, mixed precision; four warps (four independent
-// points) per CTA, register budget for 2, 3 or 4 CTAs per SM (variants 22,
+// Thermoelastic and J2 leaves, mixed precision; four warps (four points, in
+// lockstep) per CTA, register budget for 2, 3 or 4 CTAs per SM (variants 22,
 // 23, 24).
 #include "solve_warp.cuh"
 
@@ -26,7 +26,8 @@ bool warp_form_supports(int K, bool mixed, int law) { return mixed && K >= 6 && 
 size_t warp_smem_bytes(int K, int n_mats) {
   const size_t mp = sizeof(MatPt<float, dfl>);
   const size_t head = (n_mats * mp + 15) & ~size_t(15);
-  return head + size_t(kWarpsPerCta) * size_t(warp_detail::wlay_bytes(K, n_mats, int(mp)));
+  return head + size_t(kWarpsPerCta) * size_t(warp_detail::wlay_bytes(K, n_mats, int(mp))) +
+         size_t(warp_detail::up_bytes(kWarpsPerCta));
 }
 
 size_t warp_scratch_bytes_per_cta(int K) {

@@ -4,9 +4,10 @@
 // Mapping.  Level 6 of the tree has 32 nodes: lane l owns the subtree under
 // level-6 node l, i.e. M = 2^(K-6) bottom laminates (2M leaves) and the
 // 2M - 1 laminates of levels 6..K above them.  A Newton pass condenses that
-// subtree in the lane's registers (a recursion over the levels, fully
-// unrolled), then the five levels 5..1 by shuffles (level k node j on lane
-// j 2^(6-k)).  Nothing waits for another warp: a CTA holds W independent
+// subtree in the lane's registers (a postorder loop over the lane's bottom
+// laminates), then the five levels 5..1 by shuffles (level k node j on lane
+// j 2^(6-k)).  The loops keep one copy of the leaf, laminate and combine
+// code, small enough for the instruction cache.  Nothing waits for another warp: a CTA holds W independent
 // points, one per warp, and its warps meet only once, when the CTA starts.
 //
 // Strains.  Lane l keeps the strain of its level-6 node (float-float) in
@@ -118,68 +119,152 @@ __device__ __forceinline__ void leaf_at(WCtx<TF, HP> &c, int j, const HP e[6], H
   leaf_eval<TF, HP, LAW>(m, e, zn, c.trn_s[j], sig, D, X, rec, znew ? znew : zdummy, c.full);
 }
 
-// Condensed record of the subtree under node i of level LEV (strain e),
-// with its plain weighted stress sum S; G/h of the node into the lane's
-// scratch slot; |r|^2, D and X accumulated in the context.
-template <int K, int LEV, typename TF, typename HP, int LAW>
-__device__ __forceinline__ void subtree(WCtx<TF, HP> &c, int i, const HP e[6], Rec<TF> &rec, HP S[6]) {
-  const SolveParams &P = *c.P;
-  const int p = (1 << K) - (1 << LEV) + i;
-  const int slot = ((1 << (LEV - 6)) - 1) + (i - (c.lane << (LEV - 6)));
+// Combine the condensed records of two sibling subtrees (L: child 1, in/out;
+// R: child 2) into node p's record, with the residual of p from the
+// children's plain stress sums (S_L in/out becomes S_L + S_R); G/h of p into
+// gh.  The same code serves the lane's own levels and the shuffle levels.
+template <typename TF, typename HP>
+__device__ __forceinline__ void combine_node(const SolveParams &P, int p, Rec<TF> &L, const Rec<TF> &R, HP SL[6],
+                                             const HP SR[6], TF &r2, bool full, TF *gh) {
   NodeHP<HP> nd;
   load_node(P, p, nd);
-  HP el[6], er[6];
-  child_strains(nd, c.a_s + 3 * p, e, el, er);
-  TF rbv[3];
+  HP dh[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    dh[q] = nd.c2 * SL[q] - nd.c1 * SR[q];
+    SL[q] = SL[q] + SR[q];
+  }
+  HP rh[3];
+  btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
   TF n[3], c1, c2, iwcc, wcc;
   load_node_tf(P, p, n, c1, c2, iwcc, wcc);
-  Rec<TF> rr;
-  if constexpr (LEV == K) {
-    // bottom laminate i: leaves 2i, 2i+1
-    HP sl[6], sr[6], DL, DR, XL, XR;
-    leaf_at<TF, HP, LAW>(c, 2 * i, el, sl, DL, XL, rec);
-    leaf_at<TF, HP, LAW>(c, 2 * i + 1, er, sr, DR, XR, rr);
-    HP *tag = nullptr;
-    const HP wL = hp_from(__ldg(P.leafw + 2 * i), tag), wR = hp_from(__ldg(P.leafw + 2 * i + 1), tag);
-    if (c.full) {
-      c.Dsum = c.Dsum + (wL * DL + wR * DR);
-      c.Xsum = c.Xsum + (wL * XL + wR * XR);
-    }
-    HP dsh[6];
+  TF rv[3];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      S[q] = wL * sl[q] + wR * sr[q];
-      dsh[q] = sl[q] - sr[q];
-    }
-    HP rbh[3];
-    btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_p / (w c1 c2)
-#pragma unroll
-    for (int r = 0; r < 3; ++r) rbv[r] = tf_of(rbh[r], (TF *)nullptr);
-    c.r2 += wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
-  } else {
-    HP SR[6];
-    subtree<K, LEV + 1, TF, HP, LAW>(c, 2 * i, el, rec, S);
-    subtree<K, LEV + 1, TF, HP, LAW>(c, 2 * i + 1, er, rr, SR);
-    HP dh[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      dh[q] = nd.c2 * S[q] - nd.c1 * SR[q];
-      S[q] = S[q] + SR[q];
-    }
-    HP rh[3];
-    btvec_hp(nd, dh, rh);  // r_p = B^T (c2 S_L - c1 S_R)
-    TF rv[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) rv[r] = tf_of(rh[r], (TF *)nullptr);
-    c.r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) rbv[r] = rv[r] * iwcc;
-  }
-  TF gh[21];
-  combine<TF>(rec, rr, n, c1, c2, rbv, gh, c.full);
-  float *g = c.ghw + slot * 21 * 32 + c.lane;
+  for (int r = 0; r < 3; ++r) rv[r] = tf_of(rh[r], (TF *)nullptr);
+  r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+  const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
+  combine<TF>(L, R, n, c1, c2, rbv, gh, full);
+}
+
+template <typename TF>
+__device__ __forceinline__ void store_gh(float *slot_base, int lane, const TF gh[21]) {
+  float *g = slot_base + lane;
 #pragma unroll
   for (int q = 0; q < 21; ++q) g[q * 32] = gh[q];
+}
+
+// Bottom laminate i (leaves 2i, 2i+1) with strain e: leaf laws, its
+// condensed record and plain stress sum; |r|^2, D and X accumulated.
+template <typename TF, typename HP, int LAW>
+__device__ __forceinline__ void laminate(WCtx<TF, HP> &c, int i, const HP e[6], Rec<TF> &rec, HP S[6],
+                                         TF *gh) {
+  const SolveParams &P = *c.P;
+  NodeHP<HP> nd;
+  load_node(P, i, nd);  // bottom laminate i is node i
+  HP el[6], er[6];
+  child_strains(nd, c.a_s + 3 * i, e, el, er);
+  HP sl[6], sr[6], DL, DR, XL, XR;
+  Rec<TF> rr;
+  leaf_at<TF, HP, LAW>(c, 2 * i, el, sl, DL, XL, rec);
+  leaf_at<TF, HP, LAW>(c, 2 * i + 1, er, sr, DR, XR, rr);
+  HP *tag = nullptr;
+  const HP wL = hp_from(__ldg(P.leafw + 2 * i), tag), wR = hp_from(__ldg(P.leafw + 2 * i + 1), tag);
+  if (c.full) {
+    c.Dsum = c.Dsum + (wL * DL + wR * DR);
+    c.Xsum = c.Xsum + (wL * XL + wR * XR);
+  }
+  HP dsh[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    S[q] = wL * sl[q] + wR * sr[q];
+    dsh[q] = sl[q] - sr[q];
+  }
+  HP rbh[3];
+  btvec_hp(nd, dsh, rbh);  // B^T (sigma_L - sigma_R) = r_i / (w c1 c2)
+  TF n[3], c1, c2, iwcc, wcc;
+  load_node_tf(P, i, n, c1, c2, iwcc, wcc);
+  TF rbv[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rbv[r] = tf_of(rbh[r], (TF *)nullptr);
+  c.r2 += wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
+  combine<TF>(rec, rr, n, c1, c2, rbv, gh, c.full);
+}
+
+template <typename TF, typename HP>
+__device__ __forceinline__ void rec_copy(Rec<TF> &d, const Rec<TF> &s) { d = s; }
+
+// Condensed record (and plain stress sum) of lane l's subtree, the one under
+// level-6 node l with strain e6.  Postorder over the lane's M bottom
+// laminates: one copy of the laminate code and one of the code combining two
+// subtrees (the instruction cache holds the loop); a record waiting for its
+// sibling stays in the register slot of its level (at most two, K = 8), which
+// the loop addresses by selects, never by an index.
+template <int K, typename TF, typename HP, int LAW>
+__device__ __forceinline__ void lane_condense(WCtx<TF, HP> &c, const HP e6[6], Rec<TF> &rec, HP S[6]) {
+  constexpr int M = 1 << (K - 6);
+  const SolveParams &P = *c.P;
+  const int lane = c.lane;
+  Rec<TF> pend0, pend1;  // waiting records of levels K and K - 1
+  HP pS0[6], pS1[6];
+#pragma unroll 1
+  for (int q = 0; q < M; ++q) {
+    // strain of bottom laminate lane M + q: down from level 6 along q's bits
+    HP e[6];
+#pragma unroll
+    for (int c6 = 0; c6 < 6; ++c6) e[c6] = e6[c6];
+#pragma unroll
+    for (int lev = 6; lev < K; ++lev) {
+      const int pos = (lane << (lev - 6)) + (q >> (K - lev));
+      const int p = (1 << K) - (1 << lev) + pos;
+      NodeHP<HP> nd;
+      load_node(P, p, nd);
+      const HP *a = c.a_s + 3 * p;
+      const HP av[3] = {a[0], a[1], a[2]};
+      HP J[6];
+      bvec_hp(nd, av, J);
+      const bool right = (q >> (K - lev - 1)) & 1;
+#pragma unroll
+      for (int c6 = 0; c6 < 6; ++c6) e[c6] = right ? e[c6] - nd.c1 * J[c6] : e[c6] + nd.c2 * J[c6];
+    }
+    TF gh[21];
+    laminate<TF, HP, LAW>(c, lane * M + q, e, rec, S, gh);
+    store_gh(c.ghw + ((M - 1) + q) * 21 * 32, lane, gh);
+    // merge with waiting left siblings while this record is a right child
+    int lev = K, idx = q;
+#pragma unroll 1
+    while (idx & 1) {
+      Rec<TF> L;
+      HP SL[6];
+      if (lev == K) {
+        L = pend0;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; ++c6) SL[c6] = pS0[c6];
+      } else {
+        L = pend1;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; ++c6) SL[c6] = pS1[c6];
+      }
+      idx >>= 1;
+      lev -= 1;
+      const int p = (1 << K) - (1 << lev) + (lane << (lev - 6)) + idx;
+      combine_node<TF, HP>(P, p, L, rec, SL, S, c.r2, c.full, gh);
+      store_gh(c.ghw + (((1 << (lev - 6)) - 1) + idx) * 21 * 32, lane, gh);
+      rec = L;
+#pragma unroll
+      for (int c6 = 0; c6 < 6; ++c6) S[c6] = SL[c6];
+    }
+    if (lev > 6) {  // a left child: wait for the sibling
+      if (lev == K) {
+        pend0 = rec;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; ++c6) pS0[c6] = S[c6];
+      } else {
+        pend1 = rec;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; ++c6) pS1[c6] = S[c6];
+      }
+    }
+  }
 }
 
 // Back-substitution in the lane's subtree: node i of level LEV with the
@@ -282,33 +367,98 @@ __device__ __forceinline__ void rec_shfl(Rec<TF> &dst, const Rec<TF> &src, int o
 
 }  // namespace warp_detail
 
-// K: depth (6..8); W: warps (points) per CTA; MINB: CTAs per SM the
-// register budget is sized for; LAW as in the compact form (1: thermoelastic
-// and J2 leaves; 2: also Perzyna leaves).  Mixed precision only (TF = float,
-// HP = float-float).
+// Shared buffers of the batched upper levels, after the W per-warp regions:
+// level-5 records and plain stress sums of every point (slot pw 16 + j; level
+// 3 reuses them), level 4 (slot pw 8 + j; level 2 reuses them), the roots,
+// per-node |r|^2 of levels 4..1 (pw 16 + 16 - 2^k + j), per-warp |r|^2 of
+// the lane levels and level 5, per-point flags (1: active, 2: full pass).
+namespace warp_detail {
+constexpr int RSW = 41;  // record stride in floats (40 values, odd)
+__host__ __device__ constexpr int up_rec5(int) { return 0; }                             // TF[W 16 RSW]
+__host__ __device__ constexpr int up_s5(int W) { return 4 * W * 16 * RSW + 4 * (W & 1); }  // HP[W 16 6]
+__host__ __device__ constexpr int up_rec4(int W) { return up_s5(W) + 8 * W * 16 * 6; }    // TF[W 8 RSW]
+__host__ __device__ constexpr int up_s4(int W) { return up_rec4(W) + 4 * W * 8 * RSW + 4 * (W & 1); }  // HP
+__host__ __device__ constexpr int up_root(int W) { return up_s4(W) + 8 * W * 8 * 6; }     // TF[W RSW]
+__host__ __device__ constexpr int up_sroot(int W) { return (up_root(W) + 4 * W * RSW + 7) & ~7; }  // HP[W 6]
+__host__ __device__ constexpr int up_r2(int W) { return up_sroot(W) + 8 * W * 6; }        // TF[W 16]
+__host__ __device__ constexpr int up_r2w(int W) { return up_r2(W) + 4 * W * 16; }         // TF[W]
+__host__ __device__ constexpr int up_flag(int W) { return up_r2w(W) + 4 * W; }            // int[W]
+__host__ __device__ constexpr int up_bytes(int W) { return (up_flag(W) + 4 * W + 15) & ~15; }
+
+template <typename TF>
+__device__ __forceinline__ void rec_to_smem(TF *d, const Rec<TF> &r) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) d[q] = r.C[q];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    d[21 + c] = r.ds[c];
+    d[27 + c] = r.tau[c];
+    d[33 + c] = r.dd[c];
+  }
+  d[39] = r.gg;
+}
+template <typename TF>
+__device__ __forceinline__ void rec_from_smem(Rec<TF> &r, const TF *d) {
+#pragma unroll
+  for (int q = 0; q < 21; ++q) r.C[q] = d[q];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    r.ds[c] = d[21 + c];
+    r.tau[c] = d[27 + c];
+    r.dd[c] = d[33 + c];
+  }
+  r.gg = d[39];
+}
+}  // namespace warp_detail
+
+// K: depth (6..8); W: warps (points) per CTA (4: levels 4..1 of all points fit
+// one warp); MINB: CTAs per SM the register budget is sized for; LAW as in the
+// compact form (1: thermoelastic and J2 leaves).  Mixed precision only
+// (TF = float, HP = float-float).
+//
+// The W warps of a CTA run their passes in lockstep, one pass per slot:
+//   [A] a warp without a point takes one from the queue and loads it;
+//   [C] every warp condenses its point's level-6 subtrees (a lane each) and
+//       level 5 (lane pairs, shuffles);
+//   [E] warp 0 condenses levels 4..1 of all W points, one node per lane;
+//   [G] every warp takes Algorithm 1's decision for its point and makes the
+//       Newton step, the line-search step, or writes the outputs.
+// Barriers between [C], [E] and [G] keep the warps of a CTA in the same code,
+// which the instruction cache needs; the batched phase [E] condenses the
+// upper levels of W points for the price of one.
 template <int K, int W, int MINB, int LAW>
 __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams P) {
   using namespace warp_detail;
   using TF = float;
   using HP = dfl;
   constexpr int N = (1 << K) - 1;
+  static_assert(W * 8 <= 32, "levels 4..1 of all points on one warp");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   HP *tag = nullptr;
-  // CTA-wide: the point-independent part of the material constants
   MatPt<TF, HP> *mp_static = reinterpret_cast<MatPt<TF, HP> *>(smem_raw);
   const int wbytes = wlay_bytes(K, P.n_mats, int(sizeof(MatPt<TF, HP>)));
-  unsigned char *wbase = smem_raw + ((P.n_mats * int(sizeof(MatPt<TF, HP>)) + 15) & ~15) + warp * wbytes;
+  unsigned char *wbase0 = smem_raw + ((P.n_mats * int(sizeof(MatPt<TF, HP>)) + 15) & ~15);
+  unsigned char *wbase = wbase0 + warp * wbytes;
+  unsigned char *ubase = wbase0 + W * wbytes;
   HP *a_s = reinterpret_cast<HP *>(wbase + wlay_a(K));
   HP *e6_s = reinterpret_cast<HP *>(wbase + wlay_e6(K));
   HP *trn_s = reinterpret_cast<HP *>(wbase + wlay_trn(K));
   HP *eb = reinterpret_cast<HP *>(wbase + wlay_eb(K));  // eps_bar^{n+1} (HP), deps (HP)
   double *ebd = reinterpret_cast<double *>(wbase + wlay_eb(K) + 8 * 12);  // eps_bar^{n+1} (FP64)
-  HP *ohp = reinterpret_cast<HP *>(wbase + wlay_out(K));                  // sigma_bar, D_bar, X_bar
-  TF *orec = reinterpret_cast<TF *>(wbase + wlay_out(K) + 8 * 8);         // root record
+  HP *ohp = reinterpret_cast<HP *>(wbase + wlay_out(K));                  // D_bar, X_bar
   TF *da_s = reinterpret_cast<TF *>(wbase + wlay_da(K));
   TF *ghu = reinterpret_cast<TF *>(wbase + wlay_ghu(K));
   MatPt<TF, HP> *mp = reinterpret_cast<MatPt<TF, HP> *>(wbase + wlay_mat(K));
+  TF *rec5 = reinterpret_cast<TF *>(ubase + up_rec5(W));
+  HP *s5 = reinterpret_cast<HP *>(ubase + up_s5(W));
+  TF *rec4 = reinterpret_cast<TF *>(ubase + up_rec4(W));
+  HP *s4 = reinterpret_cast<HP *>(ubase + up_s4(W));
+  TF *rootr = reinterpret_cast<TF *>(ubase + up_root(W));
+  HP *sroot = reinterpret_cast<HP *>(ubase + up_sroot(W));
+  TF *r2up = reinterpret_cast<TF *>(ubase + up_r2(W));
+  TF *r2w = reinterpret_cast<TF *>(ubase + up_r2w(W));
+  int *pflag = reinterpret_cast<int *>(ubase + up_flag(W));
   float *ghw = P.gh + size_t(blockIdx.x * W + warp) * wscratch_floats(K);
 
   for (int i = threadIdx.x; i < P.n_mats; i += 32 * W)
@@ -319,65 +469,80 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
   const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
   constexpr int pu0 = (1 << K) - 32;  // first node of level 5
 
+  WCtx<TF, HP> c;
+  c.P = &P;
+  c.a_s = a_s;
+  c.da_s = da_s;
+  c.trn_s = trn_s;
+  c.mp = mp;
+  c.ghw = ghw;
+  c.lane = lane;
+  // the warp's point and its Algorithm 1 state (identical on every lane)
+  bool active = false, exhausted = false, first = true;
+  int64_t pt = 0;
+  double theta = 0.0;
+  int it = 0, bt = 0, status = 0, attempt = 0, it_total = 0;
+  TF gi = TF(1), res_old = TF(0);
+  Rec<TF> rec;
+  HP S[6];
+
   for (;;) {
-    unsigned long long q = 0;
-    if (lane == 0) {
-      q = atomicAdd(P.queue, 1ull);
-      while (P.skip && q < (unsigned long long)P.n_points && P.skip[q] != 0) q = atomicAdd(P.queue, 1ull);
-    }
-    q = __shfl_sync(kFull, q, 0);
-    if (q >= (unsigned long long)P.n_points) break;
-    const int64_t pt = int64_t(q);
-    const double *sin = P.sin + pt * P.SW;
-    double *sout = P.sout + pt * P.SW;
-    const double theta = P.theta[pt];
-    // ---- point start: eps_bar, jumps a^n, material constants at theta
-    if (lane < 6) {
-      const double e0 = ld_stream(sin + lane), d = ld_stream(P.deps + pt * 6 + lane);
-      ebd[lane] = e0 + d;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
-      eb[lane] = hp_load(e0 + d, tag);
-      eb[6 + lane] = hp_load(d, tag);
-    }
-    for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
-    if (lane < P.n_mats) {
-      mp[lane] = mp_static[lane];
-      mat_point<TF, HP, LAW>(mp[lane], hp_load(theta, tag), idt, idt_f);
-    }
-    __syncwarp();
-    {
-      // traces of the leaf strains at t^n (the coupling term needs tr eps^n)
-      const HP tr0 = hp_load(ld_stream(sin), tag) + hp_load(ld_stream(sin + 1), tag) +
-                     hp_load(ld_stream(sin + 2), tag);
-      subtree_traces<K, 6, HP>(P, a_s, trn_s, lane, level6_trace<K, HP>(P, a_s, lane, tr0));
-    }
-    __syncwarp();
-    if (P.da0) {  // warm start a^n + da0
-      const float *d0 = P.da0 + pt * (3 * N);
-      for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_add_tf(a_s[i], ld_stream(d0 + i));
-      __syncwarp();
-    }
-    {
-      HP e[6];
-      level6_strain<K, HP>(P, a_s, lane, eb, e);
+    // ---- [A] a warp without a point takes the next one and loads it
+    if (!active && !exhausted) {
+      unsigned long long q = 0;
+      if (lane == 0) {
+        q = atomicAdd(P.queue, 1ull);
+        while (P.skip && q < (unsigned long long)P.n_points && P.skip[q] != 0) q = atomicAdd(P.queue, 1ull);
+      }
+      q = __shfl_sync(kFull, q, 0);
+      if (q >= (unsigned long long)P.n_points) {
+        exhausted = true;
+      } else {
+        active = true;
+        pt = int64_t(q);
+        const double *sin = P.sin + pt * P.SW;
+        c.sin = sin;
+        c.sout = P.sout + pt * P.SW;
+        theta = P.theta[pt];
+        if (lane < 6) {
+          const double e0 = ld_stream(sin + lane), d = ld_stream(P.deps + pt * 6 + lane);
+          ebd[lane] = e0 + d;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
+          eb[lane] = hp_load(e0 + d, tag);
+          eb[6 + lane] = hp_load(d, tag);
+        }
+        for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
+        if (lane < P.n_mats) {
+          mp[lane] = mp_static[lane];
+          mat_point<TF, HP, LAW>(mp[lane], hp_load(theta, tag), idt, idt_f);
+        }
+        __syncwarp();
+        {
+          // traces of the leaf strains at t^n (the coupling term needs tr eps^n)
+          const HP tr0 = hp_load(ld_stream(sin), tag) + hp_load(ld_stream(sin + 1), tag) +
+                         hp_load(ld_stream(sin + 2), tag);
+          subtree_traces<K, 6, HP>(P, a_s, trn_s, lane, level6_trace<K, HP>(P, a_s, lane, tr0));
+        }
+        __syncwarp();
+        if (P.da0) {  // warm start a^n + da0
+          const float *d0 = P.da0 + pt * (3 * N);
+          for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_add_tf(a_s[i], ld_stream(d0 + i));
+          __syncwarp();
+        }
+        HP e[6];
+        level6_strain<K, HP>(P, a_s, lane, eb, e);
 #pragma unroll
-      for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+        for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+        first = true;
+        it = bt = status = attempt = it_total = 0;
+        gi = TF(1);
+        res_old = TF(0);
+      }
     }
-    bool first = true;
-    int it = 0, bt = 0, status = 0, attempt = 0, it_total = 0;
-    TF gi = TF(1), res_old = TF(0);
-    WCtx<TF, HP> c;
-    c.P = &P;
-    c.a_s = a_s;
-    c.da_s = da_s;
-    c.trn_s = trn_s;
-    c.mp = mp;
-    c.ghw = ghw;
-    c.sin = sin;
-    c.sout = sout;
-    c.lane = lane;
-    Rec<TF> rec;
-    HP S[6];
-    for (;;) {
+    if (lane == 0) pflag[warp] = (active ? 1 : 0) | (first ? 0 : 2);
+    if (!__syncthreads_or(active)) break;
+
+    // ---- [C] the lanes' subtrees and level 5
+    if (active) {
       // Algorithm 1 takes at least one Newton step, so the first pass of an
       // iteration never gives the outputs: it skips their terms
       c.full = !first;
@@ -388,48 +553,86 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
         HP e[6];
 #pragma unroll
         for (int q2 = 0; q2 < 6; ++q2) e[q2] = e6_s[6 * lane + q2];
-        subtree<K, 6, TF, HP, LAW>(c, lane, e, rec, S);
+        lane_condense<K, TF, HP, LAW>(c, e, rec, S);
       }
-      // ---- levels 5..1 by shuffles: level k node j on lane j 2^(6-k)
+      Rec<TF> other;
+      rec_shfl(other, rec, 1);
+      HP So[6];
 #pragma unroll
-      for (int k = 5; k >= 1; --k) {
-        const int off = 1 << (5 - k);
-        Rec<TF> other;
-        rec_shfl(other, rec, off);
-        HP So[6];
+      for (int q2 = 0; q2 < 6; ++q2) So[q2] = hp_shfl_down(kFull, S[q2], 1, 32);
+      if ((lane & 1) == 0) {
+        const int j = lane >> 1, p = pu0 + j;
+        combine_node<TF, HP>(P, p, rec, other, S, So, c.r2, c.full, ghu + 21 * (p - pu0));
+        rec_to_smem(rec5 + RSW * (warp * 16 + j), rec);
 #pragma unroll
-        for (int q2 = 0; q2 < 6; ++q2) So[q2] = hp_shfl_down(kFull, S[q2], off, 32);
-        if ((lane & (2 * off - 1)) == 0) {
-          const int j = lane >> (6 - k), p = (1 << K) - (1 << k) + j;
-          NodeHP<HP> nd;
-          load_node(P, p, nd);
-          HP dh[6];
-#pragma unroll
-          for (int q2 = 0; q2 < 6; ++q2) {
-            dh[q2] = nd.c2 * S[q2] - nd.c1 * So[q2];
-            S[q2] = S[q2] + So[q2];
-          }
-          HP rh[3];
-          btvec_hp(nd, dh, rh);
-          TF n[3], c1, c2, iwcc, wcc;
-          load_node_tf(P, p, n, c1, c2, iwcc, wcc);
-          const TF rv[3] = {rh[0].hi, rh[1].hi, rh[2].hi};
-          c.r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-          const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
-          combine<TF>(rec, other, n, c1, c2, rbv, ghu + 21 * (p - pu0), c.full);
-        }
+        for (int q2 = 0; q2 < 6; ++q2) s5[6 * (warp * 16 + j) + q2] = S[q2];
       }
-      // ---- residual norm and decision (Algorithm 1), identical on every lane
       TF r2 = c.r2;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(kFull, r2, o);
+      if (lane == 0) r2w[warp] = r2;
+    }
+    __syncthreads();
+
+    // ---- [E] levels 4..1 of every point on warp 0: level k node j of point
+    //      pw on lane pw 2^(k-1) + j; children from the level below
+    if (warp == 0) {
+#pragma unroll 1
+      for (int k = 4; k >= 1; --k) {
+        const int cnt = 1 << (k - 1);
+        const int pw = lane >> (k - 1), j = lane & (cnt - 1);
+        if (pw < W && (pflag[pw] & 1)) {
+          // level k + 1 lives in the level-5 slots (k + 1 odd) or the level-4 slots
+          const bool from5 = ((k + 1) & 1) != 0;
+          const TF *rb = from5 ? rec5 + RSW * (pw * 16) : rec4 + RSW * (pw * 8);
+          const HP *sb = from5 ? s5 + 6 * (pw * 16) : s4 + 6 * (pw * 8);
+          Rec<TF> L, R;
+          rec_from_smem(L, rb + RSW * (2 * j));
+          rec_from_smem(R, rb + RSW * (2 * j + 1));
+          HP SL[6], SR[6];
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) {
+            SL[q2] = sb[6 * (2 * j) + q2];
+            SR[q2] = sb[6 * (2 * j + 1) + q2];
+          }
+          const int p = (1 << K) - (1 << k) + j;
+          TF *ghu_pw = reinterpret_cast<TF *>(wbase0 + pw * wbytes + wlay_ghu(K));
+          TF r2n = TF(0);
+          combine_node<TF, HP>(P, p, L, R, SL, SR, r2n, (pflag[pw] & 2) != 0, ghu_pw + 21 * (p - pu0));
+          r2up[pw * 16 + 16 - (1 << k) + j] = r2n;
+          TF *rd;
+          HP *sd;
+          if (k == 1) {
+            rd = rootr + RSW * pw;
+            sd = sroot + 6 * pw;
+          } else if (k & 1) {  // levels 3: the level-5 slots are free again
+            rd = rec5 + RSW * (pw * 16 + j);
+            sd = s5 + 6 * (pw * 16 + j);
+          } else {
+            rd = rec4 + RSW * (pw * 8 + j);
+            sd = s4 + 6 * (pw * 8 + j);
+          }
+          rec_to_smem(rd, L);
+#pragma unroll
+          for (int q2 = 0; q2 < 6; ++q2) sd[q2] = SL[q2];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+
+    // ---- [G] decision (Algorithm 1), then the Newton step, the line-search
+    //      step, or the outputs
+    if (active) {
+      TF r2 = r2w[warp];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) r2 += r2up[warp * 16 + i];
       TF sn = TF(0);
 #pragma unroll
-      for (int q2 = 0; q2 < 6; ++q2) sn += S[q2].hi * S[q2].hi;
-      sn = __shfl_sync(kFull, sn, 0);
+      for (int q2 = 0; q2 < 6; ++q2) sn += sroot[6 * warp + q2].hi * sroot[6 * warp + q2].hi;
       TF den = sqrt(sn);
       if (den < res_floor) den = res_floor;
-      const TF res = __shfl_sync(kFull, sqrt(r2) / (TF(N) * den), 0);
+      const TF res = sqrt(r2) / (TF(N) * den);
       const bool accept = first || (res < res_old) || (bt >= P.maxbt);
       int action;
       if (accept) {
@@ -453,36 +656,32 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
       } else {
         action = ACT_BACK;
       }
-      if (action == ACT_DONE) {
-        if (P.da0 && attempt == 0 && status != 0) {
-          // the warm-started iteration failed: Algorithm 1 again from a^n
-          attempt = 1;
-          it_total = it;
-          __syncwarp();
-          for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
-          __syncwarp();
-          HP e[6];
-          level6_strain<K, HP>(P, a_s, lane, eb, e);
+      const double *sin = c.sin;
+      double *sout = c.sout;
+      if (action == ACT_DONE && P.da0 && attempt == 0 && status != 0) {
+        // the warm-started iteration failed: Algorithm 1 again from a^n
+        attempt = 1;
+        it_total = it;
+        for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
+        __syncwarp();
+        HP e[6];
+        level6_strain<K, HP>(P, a_s, lane, eb, e);
 #pragma unroll
-          for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
-          first = true;
-          it = bt = status = 0;
-          gi = TF(1);
-          res_old = TF(0);
-          continue;
-        }
-        break;
-      }
-      __syncwarp();
-      if (action == ACT_STEP) {
-        // ---- back-substitution: levels 1..5 by shuffles, the node's strain
-        //      perturbation de in TF for the Newton chain and the float-float
-        //      sum he of its ancestors' B da terms for the level-6 strain
+        for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
+        first = true;
+        it = bt = status = 0;
+        gi = TF(1);
+        res_old = TF(0);
+      } else if (action == ACT_STEP) {
+        // back-substitution: levels 1..5 by shuffles (the node's strain
+        // perturbation de in TF for the Newton chain and the float-float sum
+        // he of its ancestors' B da terms for the level-6 strain), then the
+        // lane's own subtree
         TF de[6] = {TF(0), TF(0), TF(0), TF(0), TF(0), TF(0)};
         HP he[6];
 #pragma unroll
         for (int q2 = 0; q2 < 6; ++q2) he[q2] = hp_zero(tag);
-#pragma unroll
+#pragma unroll 1
         for (int k = 1; k <= 5; ++k) {
           const int stride = 1 << (6 - k), half = stride >> 1;
           TF dr[6];
@@ -493,10 +692,10 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
             TF da[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-              TF s = g[18 + r];
+              TF s2 = g[18 + r];
 #pragma unroll
-              for (int q2 = 0; q2 < 6; ++q2) s += g[6 * r + q2] * de[q2];
-              da[r] = -s;
+              for (int q2 = 0; q2 < 6; ++q2) s2 += g[6 * r + q2] * de[q2];
+              da[r] = -s2;
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -532,13 +731,11 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
             }
           }
         }
-        // the level-6 node's strain moves by its ancestors' terms; its own
-        // subtree's jumps take the rest of the increment
 #pragma unroll
         for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e6_s[6 * lane + q2] + he[q2];
         subtree_back<K, 6, TF, HP>(c, lane, de);
-      } else {
-        // ---- backtracking (rare): a -= f da, strains again from a
+      } else if (action == ACT_BACK) {
+        // backtracking (rare): a -= f da, strains again from a
         const TF f = gi * (TF(1) - gamma);
         for (int i = lane; i < 3 * N; i += 32) a_s[i] = hp_add_tf(a_s[i], -f * da_s[i]);
         __syncwarp();
@@ -548,66 +745,58 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
         for (int q2 = 0; q2 < 6; ++q2) e6_s[6 * lane + q2] = e[q2];
         gi *= gamma;
         bt += 1;
+      } else {
+        // ---- outputs and state (the last pass is at the final a)
+        HP Db = c.Dsum, Xb = c.Xsum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          Db = Db + hp_shfl_down(kFull, Db, o, 32);
+          Xb = Xb + hp_shfl_down(kFull, Xb, o, 32);
+        }
+        if (lane == 0) {
+          ohp[0] = Db;
+          ohp[1] = Xb;
+        }
+        __syncwarp();
+        const TF *orr = rootr + RSW * warp;
+        const HP *osg = sroot + 6 * warp;
+        int bad = 0;
+        for (int cc = lane; cc < kOutWords; cc += 32) {
+          double v;
+          if (cc < 6) v = hp_to(osg[cc]);
+          else if (cc < 42) v = double(sget(orr, (cc - 6) / 6, (cc - 6) % 6));
+          else if (cc < 48) v = double(orr[27 + cc - 42]);   // tau
+          else if (cc == 48) v = hp_to(ohp[0]);
+          else if (cc < 55) v = double(orr[33 + cc - 49]);   // dd
+          else if (cc == 55) v = double(orr[39]);            // gg
+          else v = hp_to(ohp[1]);
+          if (!isfinite(v)) bad = 1;
+          __stcs(P.out + pt * kOutWords + cc, v);
+        }
+        bad = __any_sync(kFull, bad);
+        if (lane == 0) {
+          P.status[pt] = (bad ? 2 : status) | (attempt ? 4 : 0);
+          P.iters[pt] = it + it_total;
+        }
+        if (lane < 8) sout[lane] = lane < 6 ? ebd[lane] : (lane == 6 ? theta : 0.0);
+        for (int i = lane; i < 3 * N; i += 32) __stcs(sout + 8 + i, hp_to(a_s[i]));
+        // the lane's own leaves: parked float-float z of the last pass -> FP64
+#pragma unroll 1
+        for (int j = lane << (K - 5); j < (lane + 1) << (K - 5); ++j) {
+          const int zo = __ldg(P.zoff + j);
+          if (zo < 0) continue;
+          const int nz = (LAW >= 2 && mp[__ldg(P.phase + j)].kind == 2) ? 13 : 7;
+          const HP *zp = reinterpret_cast<const HP *>(sout + zo);
+          for (int q2 = 0; q2 < nz; ++q2) {
+            const HP v = ld_once(zp + q2);
+            sout[zo + q2] = hp_to(v);
+          }
+        }
+        for (int i = P.zend + lane; i < P.SW; i += 32) sout[i] = 0.0;  // padding word
+        active = false;
       }
       __syncwarp();
     }
-
-    // ---- outputs and state (the last pass is at the final a)
-    HP Db = c.Dsum, Xb = c.Xsum;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Db = Db + hp_shfl_down(kFull, Db, o, 32);
-      Xb = Xb + hp_shfl_down(kFull, Xb, o, 32);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int q2 = 0; q2 < 6; ++q2) ohp[q2] = S[q2];
-      ohp[6] = Db;
-      ohp[7] = Xb;
-#pragma unroll
-      for (int q2 = 0; q2 < 21; ++q2) orec[q2] = rec.C[q2];
-#pragma unroll
-      for (int q2 = 0; q2 < 6; ++q2) {
-        orec[21 + q2] = rec.tau[q2];
-        orec[27 + q2] = rec.dd[q2];
-      }
-      orec[33] = rec.gg;
-    }
-    __syncwarp();
-    int bad = 0;
-    for (int cc = lane; cc < kOutWords; cc += 32) {
-      double v;
-      if (cc < 6) v = hp_to(ohp[cc]);
-      else if (cc < 42) v = double(sget(orec, (cc - 6) / 6, (cc - 6) % 6));
-      else if (cc < 48) v = double(orec[21 + cc - 42]);
-      else if (cc == 48) v = hp_to(ohp[6]);
-      else if (cc < 55) v = double(orec[27 + cc - 49]);
-      else if (cc == 55) v = double(orec[33]);
-      else v = hp_to(ohp[7]);
-      if (!isfinite(v)) bad = 1;
-      __stcs(P.out + pt * kOutWords + cc, v);
-    }
-    bad = __any_sync(kFull, bad);
-    if (lane == 0) {
-      P.status[pt] = (bad ? 2 : status) | (attempt ? 4 : 0);
-      P.iters[pt] = it + it_total;
-    }
-    if (lane < 8) sout[lane] = lane < 6 ? ebd[lane] : (lane == 6 ? theta : 0.0);
-    for (int i = lane; i < 3 * N; i += 32) __stcs(sout + 8 + i, hp_to(a_s[i]));
-    // the lane's own leaves: parked float-float z of the last pass -> FP64
-#pragma unroll 1
-    for (int j = lane << (K - 5); j < (lane + 1) << (K - 5); ++j) {
-      const int zo = __ldg(P.zoff + j);
-      if (zo < 0) continue;
-      const int nz = (LAW >= 2 && mp[__ldg(P.phase + j)].kind == 2) ? 13 : 7;
-      const HP *zp = reinterpret_cast<const HP *>(sout + zo);
-      for (int q2 = 0; q2 < nz; ++q2) {
-        const HP v = ld_once(zp + q2);
-        sout[zo + q2] = hp_to(v);
-      }
-    }
-    for (int i = P.zend + lane; i < P.SW; i += 32) sout[i] = 0.0;  // padding word
-    __syncwarp();
   }
 }
 

@@ -79,3 +79,44 @@ def test_autotuner_writes_a_choice(tmp_path):
     e = autotune.tune(K=6, n_points=4096, n_steps=2, warmup=1, path=p)
     assert e["variant"] in autotune.VARIANTS["mixed"]
     assert autotune.lookup(6, "mixed", p) == e["variant"]
+
+
+@pytest.mark.parametrize("variant", [13, 23])
+def test_warm_graph_replay_equals_direct_launches(variant):
+    """The headline increment (network input, four GEMMs, warm-started solve)
+    replayed as a CUDA graph gives the bits of the same launches made
+    directly, over three increments (every rotation phase of the state
+    buffers), for the compact and the warp form of the solve."""
+    from paper_2109_14403_gb300 import DMN
+    from paper_2109_14403_gb300.graph import WarmIncrementGraph
+    from paper_2109_14403_gb300.mlp import MLP
+    dev = _dev()
+    n = 2048
+    w, nrm, ph = syn.tree(8)
+    d = DMN(8, w, nrm, ph, syn.materials(), precision="mixed", tol=1e-12, solve_variant=variant)
+    net = MLP(K=8, hidden=512, n_hidden=3, max_batch=n, seed=0)
+    p = net.params()
+    din, dout = net.layer_dims()[-1]
+    p[-(din * dout + dout):] *= 1e-6  # small predicted increments
+    net.set_params(p)
+    deps, theta = syn.random_walk_k8(n_points=n, n_incr=5)
+    D = torch.tensor(deps * 5, device=dev)
+    T = torch.tensor(theta, device=dev)
+    s0 = d.init_state(torch.full((n,), 293.0, dtype=torch.float64, device=dev))
+    s1, _, _, _ = d.eval(D[0], T[0], 1.0, s0)
+    g = WarmIncrementGraph(d, net, n, s0, s1)
+    prev, cur = s0, s1
+    for k in range(1, 5):
+        g.deps.copy_(D[k])
+        g.theta.copy_(T[k])
+        g.step()
+        x = net.input(D[k], T[k], cur, prev)
+        da = net.predict(x)
+        nxt, out, st, it = d.eval_warm(D[k], T[k], 1.0, cur, da)
+        torch.cuda.synchronize()
+        assert torch.equal(da, g.da)
+        assert torch.equal(out, g.out) and torch.equal(st, g.status) and torch.equal(it, g.iters)
+        assert torch.equal(nxt, g.current_state())
+        prev, cur = cur, nxt
+    net.close()
+    d.close()
