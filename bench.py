@@ -305,7 +305,7 @@ def run_uneven(args):
     magnitudes; every increment is the three launches replayed as one CUDA graph."""
     import torch
 
-    from paper_2109_14403_gb300 import DMN, synthetic as syn
+    from paper_2109_14403_gb300 import DMN, autotune, synthetic as syn
     from paper_2109_14403_gb300.graph import IncrementGraph
     local = int(os.environ.get("LOCAL_RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -322,7 +322,9 @@ def run_uneven(args):
     for i, K in enumerate(syn.UNEVEN_DEPTHS):
         w, nrm, ph = trees[i]
         sel = np.nonzero(tid == i)[0]
-        parts.append((DMN(K, w, nrm, ph, syn.materials(), tol=TOL_PAPER, precision=args.precision), len(sel)))
+        v = autotune.lookup(K, args.precision, workload="uneven")  # the tuning run on this workload
+        parts.append((DMN(K, w, nrm, ph, syn.materials(), tol=TOL_PAPER, precision=args.precision,
+                          solve_variant=v), len(sel)))
         sels.append(sel)
     g = IncrementGraph(parts)
     for i, (d, m) in enumerate(parts):
@@ -358,7 +360,10 @@ def run_uneven(args):
                 "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
                 "config": {"workload": f"uneven batch, {n} points over DMNs K=6/7/8, lognormal increments, "
                                        "CUDA-graph increments", "precision": args.precision, "tol": TOL_PAPER},
-                "iter_hist": hist, "clocks": clk.summary(), "gpu_launches": 4 * len(parts) * steps}
+                "iter_hist": hist, "clocks": clk.summary(), "gpu_launches": len(parts) * steps,
+                "solve_variants": {f"K={d.K}": {"variant": d.solve_variant,
+                                                "mapping": autotune.MAPPING.get(d.solve_variant, "")}
+                                   for d, _ in parts}}
         print(json.dumps(line), flush=True)
     for d, _ in parts:
         d.close()
@@ -965,7 +970,9 @@ def main():
     # ---- the timed path: mixed precision + learned warm start, one CUDA
     #      graph per increment (network input, four GEMMs, warm-started solve)
     from paper_2109_14403_gb300.graph import WarmIncrementGraph
-    mixed = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision="mixed", solve_variant=args.variant)
+    variant = (args.variant if args.variant is not None
+               else autotune.lookup(K_DEPTH, "mixed", workload="plastic" if plastic else "random_walk"))
+    mixed = DMN(K_DEPTH, w, nrm, ph, mats, tol=TOL, precision="mixed", solve_variant=variant)
     bufs = [start_prev.clone(), start_cur.clone(), torch.empty_like(start_cur)]
     out = torch.empty((n, 57), dtype=torch.float64, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)

@@ -3,8 +3,11 @@
 Tolerances (relative, per point, 2-norm):
   FP64 path:  stress 1e-10, tangents and coupling terms 1e-8 (Algorithm 1
               stopped at tol = 1e-12 on both sides);
-  mixed path: stress 1e-8; tangents 1e-4 (they come from the FP32
-              condensation); coupling term and dissipation 1e-8.
+  mixed path: stress 1e-8; tangents 5e-6, the mixed form's stated tangent
+              bound (they are the root record of the FP32 condensation: a few
+              FP32 roundings times the stiffness contrast ~30; the largest
+              seen over this suite is 7.5e-7); coupling term and dissipation
+              1e-8.
 State after each increment, relative to the largest entry of the oracle's:
   jump vectors a and internal variables z: 1e-8 / 1e-9 (FP64), 1e-6 (mixed).
   The residual test bounds stress errors; strains of hardening leaves are
@@ -20,7 +23,7 @@ from paper_2109_14403_gb300 import synthetic as syn
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": dict(sig=1e-10, tan=1e-8, scal=1e-9), "mixed": dict(sig=1e-8, tan=1e-4, scal=1e-8)}
+TOL = {"fp64": dict(sig=1e-10, tan=1e-8, scal=1e-9), "mixed": dict(sig=1e-8, tan=5e-6, scal=1e-8)}
 
 
 def _dev():
@@ -240,7 +243,7 @@ def test_deterministic_bits(prec, variant):
 # solution, so they differ by about tol * N * (stiffness contrast)
 # = 1e-12 * 63 * 29 ~ 2e-9 in the stress (K = 6); compared with an oracle
 # converged to 1e-14, the bounds below leave a factor 2-3.
-TOL_WARM = {"fp64": dict(sig=5e-9, tan=5e-8, scal=5e-9), "mixed": dict(sig=2e-8, tan=1e-4, scal=2e-8)}
+TOL_WARM = {"fp64": dict(sig=5e-9, tan=5e-8, scal=5e-9), "mixed": dict(sig=2e-8, tan=5e-6, scal=2e-8)}
 
 
 @pytest.mark.parametrize("prec,variant", [("fp64", 0), ("mixed", 0)] + COMPACT)
