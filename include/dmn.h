@@ -261,6 +261,24 @@ dmn_status dmn_eval_noalloc(int32_t K, const double *leaf_w, const double *norma
                             const double *d_state_in, double *d_state_out, double *d_out,
                             int32_t *d_status, int32_t *d_iters);
 
+/*
+ * Index-check log of the debug library (no counterpart in the paper).  The
+ * library can be built a second time with bounds checks (libdmn_debug.so,
+ * compile flag DMN_BOUNDS_CHECK): every node, leaf, point, state-offset and
+ * shared-memory slot index of the solve kernels is checked; an index out of
+ * range is counted, replaced by 0 (the access stays inside its array) and
+ * gives the point being evaluated the status bit DMN_PT_BOUNDS -- nothing
+ * traps.  This call copies the log out (synchronous):
+ *   *count  violations since the last clear (summed over the kernels)
+ *   *index, *bound, *line  the first one's index, bound and source line
+ *           (pointers may be NULL)
+ *   clear   nonzero: reset the log afterwards
+ * The release library has no checks and returns DMN_ERR_ARG.
+ */
+enum { DMN_PT_BOUNDS = 16 };
+dmn_status dmn_debug_bounds_log(int64_t *count, int64_t *index, int64_t *bound, int32_t *line,
+                                int32_t clear);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *dmn_last_error(void);
 

@@ -14,6 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libdmn.so")
+LIB_DEBUG = os.path.join(LIBDIR, "libdmn_debug.so")  # with index checks (-DDMN_BOUNDS_CHECK)
 SOURCES = ["dmn_api.cu", "dmn_solve.cu", "dmn_solve_compact.cu", "dmn_solve_compact_vp.cu", "dmn_solve_compact_pa66.cu", "dmn_solve_warp.cu", "dmn_solve_warp8.cu", "dmn_noalloc.cu", "dmn_drive.cu", "dmn_linear.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -29,25 +30,30 @@ def _nvcc():
     return exe
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
         os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(os.path.join(LIBDIR, "obj"), exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile the library; debug=True: the index-checking build
+    libdmn_debug.so (its own object directory)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    objdir = os.path.join(LIBDIR, "obj_debug" if debug else "obj")
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(LIBDIR, "obj", src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-DDMN_BOUNDS_CHECK"] if debug else []), "-c",
+               os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -57,11 +63,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stdout.write(out.decode(errors="replace"))
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

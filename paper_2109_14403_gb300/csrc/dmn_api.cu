@@ -521,3 +521,31 @@ extern "C" dmn_status dmn_eval_mixed(dmn_handle h, dmn_stream stream, int64_t n_
   if (e != cudaSuccess) return cuda_fail(e, "dmn_eval_mixed finish");
   return DMN_OK;
 }
+
+extern "C" dmn_status dmn_debug_bounds_log(int64_t *count, int64_t *index, int64_t *bound, int32_t *line,
+                                           int32_t clear) {
+  g_err[0] = 0;
+  if (!count) return fail(DMN_ERR_ARG, "dmn_debug_bounds_log: count is NULL");
+  cudaError_t (*const logs[])(BoundsLog *, bool) = {bounds_log_owner, bounds_log_compact,
+                                                    bounds_log_compact_vp, bounds_log_compact_pa66,
+                                                    bounds_log_warp, bounds_log_warp8};
+  int64_t n = 0;
+  bool first = true;
+  for (auto f : logs) {
+    BoundsLog b;
+    const cudaError_t e = f(&b, clear != 0);
+    if (e == cudaErrorNotSupported)
+      return fail(DMN_ERR_ARG, "dmn_debug_bounds_log: index checks are compiled into the debug library "
+                               "(libdmn_debug.so) only");
+    if (e != cudaSuccess) return cuda_fail(e, "dmn_debug_bounds_log");
+    if (b.count > 0 && first) {
+      if (index) *index = b.index;
+      if (bound) *bound = b.bound;
+      if (line) *line = b.line;
+      first = false;
+    }
+    n += int64_t(b.count);
+  }
+  *count = n;
+  return DMN_OK;
+}

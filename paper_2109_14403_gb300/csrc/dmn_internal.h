@@ -72,6 +72,14 @@ cudaError_t mixed_update(cudaStream_t s, int64_t n, int sw, int n3, const uint8_
                          const int32_t *status, int32_t *outer, int it, bool last, float *work,
                          unsigned long long *open);
 cudaError_t mixed_finish(cudaStream_t s, int64_t n, int32_t *status, int32_t *outer);
+// debug build: the index-check logs of the translation units with solve
+// kernels (dmn_check.cuh); cudaErrorNotSupported in the release build
+cudaError_t bounds_log_owner(BoundsLog *out, bool clear);
+cudaError_t bounds_log_compact(BoundsLog *out, bool clear);
+cudaError_t bounds_log_compact_vp(BoundsLog *out, bool clear);
+cudaError_t bounds_log_compact_pa66(BoundsLog *out, bool clear);
+cudaError_t bounds_log_warp(BoundsLog *out, bool clear);
+cudaError_t bounds_log_warp8(BoundsLog *out, bool clear);
 // message returned by dmn_last_error() on this thread
 void set_error_message(const char *msg);
 }  // namespace dmn

@@ -31,6 +31,7 @@
 #include <stdint.h>
 
 #include "dfl.cuh"
+#include "dmn_check.cuh"
 
 namespace dmn {
 

@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
   // per-thread constants: laminate t and its leaves 2t, 2t+1
   const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
   const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
-  const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
-  const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
+  int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
+  int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
   for (;;) {
     if (t == 0) {
@@ -157,6 +157,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
     __syncthreads();
     const int64_t pt = int64_t(ctrl->next);
     if (pt >= P.n_points) break;
+    DMN_BOUNDS_CLEAR();
+#ifdef DMN_BOUNDS_CHECK
+    {
+      int hq0 = zq0, hq1 = zq1;  // the shared copy of z uses the state's offsets
+      check_leaf(P, mp_s, ph0, hq0, zq0, ZW);
+      check_leaf(P, mp_s, ph1, hq1, zq1, ZW);
+    }
+#endif
     const double *sin = P.sin + pt * P.SW;
     double *sout = P.sout + pt * P.SW;
     const double theta = P.theta[pt];
@@ -422,8 +430,9 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_kernel(const SolveParams
       P.out[pt * kOutWords + c] = v;
     }
     bad = __syncthreads_or(bad);
+    const int bbad = DMN_BOUNDS_CTA_OR();
     if (t == 0) {
-      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
+      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0) | (bbad ? kPtBounds : 0);
       P.iters[pt] = ctrl->it + it_total;
     }
     for (int c = t; c < 8; c += G)  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
@@ -542,5 +551,8 @@ cudaError_t launch_solve(const SolveParams &P, bool mixed, int variant, int grid
   pick(P.K, mixed, variant, P.law)<<<grid, solve_block_threads(P.K, variant, P.law), smem, s>>>(P);
   return cudaGetLastError();
 }
+
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_owner)
 
 }  // namespace dmn

@@ -23,4 +23,7 @@ KernelFn compact_kernel(int K, bool mixed, int minb) {
   return minb == 3 ? dmn_solve_compact<float, dfl, 128, 3, 1> : dmn_solve_compact<float, dfl, 128, 2, 1>;
 }
 
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_compact)
+
 }  // namespace dmn

@@ -15,4 +15,7 @@ KernelFn compact_kernel_pa66(int K, bool mixed) {
   return mixed ? dmn_solve_compact<float, dfl, 128, 2, 3> : dmn_solve_compact<double, double, 128, 1, 3>;
 }
 
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_compact_pa66)
+
 }  // namespace dmn

@@ -10,4 +10,7 @@ KernelFn compact_kernel_vp(int K, bool mixed) {
   return mixed ? dmn_solve_compact<float, dfl, 256, 1, 2> : dmn_solve_compact<double, double, 256, 1, 2>;
 }
 
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_compact_vp)
+
 }  // namespace dmn

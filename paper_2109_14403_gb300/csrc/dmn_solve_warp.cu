@@ -40,4 +40,7 @@ KernelFn warp_kernel(int K, int minb) {
   return warp_kernel8(minb);
 }
 
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_warp)
+
 }  // namespace dmn

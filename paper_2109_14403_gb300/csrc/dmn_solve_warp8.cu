@@ -11,4 +11,7 @@ KernelFn warp_kernel8(int minb) {
   return dmn_solve_warp<8, 4, 4, 1>;
 }
 
+// the index-check log of this translation unit (debug build; dmn_check.cuh)
+DMN_BOUNDS_TU(bounds_log_warp8)
+
 }  // namespace dmn

@@ -73,6 +73,7 @@ struct NodeHP {
   HP n[3], ns[3], c1, c2;  // normal, normal / sqrt2, volume fractions
 };
 __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<double> &o) {
+  p = DMN_IDX(p, P.N);
   const double *r = P.node + kNodeWords * p;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -83,6 +84,7 @@ __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<do
   o.c2 = ld_keep(r + 4);
 }
 __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<dfl> &o) {
+  p = DMN_IDX(p, P.N);
   const float4 *r = reinterpret_cast<const float4 *>(P.node_df + kNodeDfl * p);
   const float4 a = ld_keep(r), b = ld_keep(r + 1), c = ld_keep(r + 2), d = ld_keep(r + 3);
   o.n[0] = {a.x, a.y};
@@ -97,6 +99,7 @@ __device__ __forceinline__ void load_node(const SolveParams &P, int p, NodeHP<df
 // normal, c1, c2, 1/(w c1 c2), w c1 c2 in the condensation precision
 __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, double n[3], double &c1,
                                              double &c2, double &iwcc, double &wcc) {
+  p = DMN_IDX(p, P.N);
   const double *r = P.node + kNodeWords * p;
   n[0] = ld_keep(r);
   n[1] = ld_keep(r + 1);
@@ -108,6 +111,7 @@ __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, double
 }
 __device__ __forceinline__ void load_node_tf(const SolveParams &P, int p, float n[3], float &c1,
                                              float &c2, float &iwcc, float &wcc) {
+  p = DMN_IDX(p, P.N);
   const float *r = P.node_df + kNodeDfl * p;
   n[0] = ld_keep(r);
   n[1] = ld_keep(r + 2);
@@ -136,6 +140,28 @@ __device__ __forceinline__ void btvec_hp(const NodeHP<HP> &nd, const HP s[6], HP
   out[0] = s[0] * nd.n[0] + s[5] * nd.ns[1] + s[4] * nd.ns[2];
   out[1] = s[1] * nd.n[1] + s[5] * nd.ns[0] + s[3] * nd.ns[2];
   out[2] = s[2] * nd.n[2] + s[4] * nd.ns[0] + s[3] * nd.ns[1];
+}
+
+// Debug build: a leaf's phase row, and the offsets of its internal variables
+// in shared memory (hq: their copy, or the PA66 history) and in the state
+// block (zq, from the end of the jumps), inside their arrays; violations are
+// recorded and replaced by 0 (dmn_check.cuh).  The release build leaves the
+// values as they are.
+template <typename M>
+__device__ __forceinline__ void check_leaf(const SolveParams &P, const M *mp, int &ph, int &hq, int &zq,
+                                           int ZW) {
+#ifdef DMN_BOUNDS_CHECK
+  ph = DMN_IDX(ph, P.n_mats);
+  const int kind = mp[ph].kind;
+  if (zq >= 0) {
+    const int nh = kind == 3 ? kPaHist : (kind == 2 ? 13 : 7);
+    const int nz = kind == 3 ? kPaZ : (kind == 2 ? 13 : 7);
+    hq = DMN_IDX(hq, ZW - nh + 1);
+    zq = DMN_IDX(zq, P.zend - (8 + 3 * P.N) - nz + 1);
+  }
+#else
+  (void)P, (void)mp, (void)ph, (void)hq, (void)zq, (void)ZW;
+#endif
 }
 
 template <typename T>

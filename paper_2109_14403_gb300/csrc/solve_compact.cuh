@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   const TF tol = TF(P.tol), res_floor = TF(P.res_floor), gamma = TF(P.gamma);
 
   const HP wL = hp_from(__ldg(P.leafw + 2 * t), tag), wR = hp_from(__ldg(P.leafw + 2 * t + 1), tag);
-  const int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
-  const int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
-  const int hq0 = LAW == 3 ? P.hoff[2 * t] : zq0, hq1 = LAW == 3 ? P.hoff[2 * t + 1] : zq1;
-  const int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
+  int zo0 = P.zoff[2 * t], zo1 = P.zoff[2 * t + 1];
+  int zq0 = zo0 >= 0 ? zo0 - (8 + 3 * N) : -1, zq1 = zo1 >= 0 ? zo1 - (8 + 3 * N) : -1;
+  int hq0 = LAW == 3 ? P.hoff[2 * t] : zq0, hq1 = LAW == 3 ? P.hoff[2 * t + 1] : zq1;
+  int ph0 = P.phase[2 * t], ph1 = P.phase[2 * t + 1];
 
   // Strains of the bottom laminates by ancestor sums (eq. DMN kinematics):
   // laminate t's strain is the root strain plus, for every ancestor p on its
@@ -253,6 +253,13 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     __syncthreads();
     const int64_t pt = int64_t(ctrl->next);
     if (pt >= P.n_points) break;
+    DMN_BOUNDS_CLEAR();
+#ifdef DMN_BOUNDS_CHECK
+    check_leaf(P, mp_s, ph0, hq0, zq0, ZW);
+    check_leaf(P, mp_s, ph1, hq1, zq1, ZW);
+    zo0 = zq0 >= 0 ? zq0 + 8 + 3 * N : -1;
+    zo1 = zq1 >= 0 ? zq1 + 8 + 3 * N : -1;
+#endif
     const double *sin = P.sin + pt * P.SW;
     double *sout = P.sout + pt * P.SW;
     HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
@@ -463,8 +470,12 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         const int j = node_at(k);
         if (j >= 0) {
           const int p = (1 << K) - (1 << k) + j;
-          const TF *rc = recbuf(k + 1) + RS * (2 * j);
-          const HP *sc = sbuf(k + 1) + 12 * j;
+          // children: slots 2j, 2j + 1 of level k + 1's buffer (debug build: checked)
+          const int cap = ((K - 1 - (k + 1)) & 1) ? sc_.GY : sc_.GX;
+          const int jc = DMN_IDX(2 * j, cap - 1) >> 1;
+          (void)cap;
+          const TF *rc = recbuf(k + 1) + RS * (2 * jc);
+          const HP *sc = sbuf(k + 1) + 12 * jc;
           Rec<TF> other;
           rec_get(rec, rc);
           rec_get(other, rc + RS);
@@ -487,9 +498,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
           combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p, full);
           if (k > 1) {
-            rec_put(recbuf(k) + RS * j, rec);
+            const int js = DMN_IDX(j, ((K - 1 - k) & 1) ? sc_.GY : sc_.GX);
+            rec_put(recbuf(k) + RS * js, rec);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) sbuf(k)[6 * j + c] = S[c];
+            for (int c = 0; c < 6; ++c) sbuf(k)[6 * js + c] = S[c];
           }
         }
       }
@@ -571,13 +583,13 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
         for (int k = 1; k <= K; ++k) {
           const int j = node_at(k);  // level K: j = t
           if (j >= 0) {
-            const int p = (1 << K) - (1 << k) + j;
+            const int p = DMN_IDX((1 << K) - (1 << k) + j, N);
             TF de[6];
             if (k == 1) {
 #pragma unroll
               for (int c = 0; c < 6; ++c) de[c] = TF(0);
             } else {
-              const TF *src = tbuf(k) + 6 * j;
+              const TF *src = tbuf(k) + DMN_IDX(6 * j, 6 * G - 5);
 #pragma unroll
               for (int c = 0; c < 6; ++c) de[c] = src[c];
             }
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
               load_node_tf(P, p, n, c1, c2, iwcc, wcc);
               TF J[6];
               bvec(n, da, J);
-              TF *dst = tbuf(k + 1) + 12 * j;
+              TF *dst = tbuf(k + 1) + DMN_IDX(12 * j, 6 * G - 11);
 #pragma unroll
               for (int c = 0; c < 6; ++c) {
                 dst[c] = de[c] + c2 * J[c];
@@ -669,8 +681,9 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       __stcs(P.out + pt * kOutWords + c, v);
     }
     bad = __syncthreads_or(bad);
+    const int bbad = DMN_BOUNDS_CTA_OR();
     if (t == 0) {
-      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0);
+      P.status[pt] = (bad ? 2 : ctrl->status) | (attempt ? 4 : 0) | (bbad ? kPtBounds : 0);
       P.iters[pt] = ctrl->it + it_total;
     }
     for (int c = t; c < 8; c += G) sout[c] = c < 6 ? ebd[c] : (c == 6 ? theta : 0.0);

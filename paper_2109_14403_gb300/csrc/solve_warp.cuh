@@ -100,13 +100,16 @@ template <typename TF, typename HP, int LAW>
 __device__ __forceinline__ void leaf_at(WCtx<TF, HP> &c, int j, const HP e[6], HP sig[6], HP &D, HP &X,
                                         Rec<TF> &rec) {
   const SolveParams &P = *c.P;
-  const int ph = __ldg(P.phase + j), zo = __ldg(P.zoff + j);
+  j = DMN_IDX(j, 1 << P.K);
+  const int ph = DMN_IDX(int(__ldg(P.phase + j)), P.n_mats);
+  int zo = __ldg(P.zoff + j);
   const MatPt<TF, HP> &m = c.mp[ph];
   HP zn[LAW >= 2 ? 13 : 7];
   HP *znew = nullptr;
   HP *tag = nullptr;
   if (zo >= 0) {
     const int nz = (LAW >= 2 && m.kind == 2) ? 13 : 7;
+    zo = DMN_IDX(zo, P.zend - nz + 1);
 #pragma unroll
     for (int q = 0; q < (LAW >= 2 ? 13 : 7); ++q)
       zn[q] = q < nz ? hp_load(ld_stream(c.sin + zo + q), tag) : hp_zero(tag);
@@ -228,7 +231,7 @@ __device__ __forceinline__ void lane_condense(WCtx<TF, HP> &c, const HP e6[6], R
     }
     TF gh[21];
     laminate<TF, HP, LAW>(c, lane * M + q, e, rec, S, gh);
-    store_gh(c.ghw + ((M - 1) + q) * 21 * 32, lane, gh);
+    store_gh(c.ghw + DMN_IDX((M - 1) + q, 2 * M - 1) * 21 * 32, lane, gh);
     // merge with waiting left siblings while this record is a right child
     int lev = K, idx = q;
 #pragma unroll 1
@@ -248,7 +251,7 @@ __device__ __forceinline__ void lane_condense(WCtx<TF, HP> &c, const HP e6[6], R
       lev -= 1;
       const int p = (1 << K) - (1 << lev) + (lane << (lev - 6)) + idx;
       combine_node<TF, HP>(P, p, L, rec, SL, S, c.r2, c.full, gh);
-      store_gh(c.ghw + (((1 << (lev - 6)) - 1) + idx) * 21 * 32, lane, gh);
+      store_gh(c.ghw + DMN_IDX(((1 << (lev - 6)) - 1) + idx, 2 * M - 1) * 21 * 32, lane, gh);
       rec = L;
 #pragma unroll
       for (int c6 = 0; c6 < 6; ++c6) S[c6] = SL[c6];
@@ -272,8 +275,8 @@ __device__ __forceinline__ void lane_condense(WCtx<TF, HP> &c, const HP e6[6], R
 template <int K, int LEV, typename TF, typename HP>
 __device__ __forceinline__ void subtree_back(WCtx<TF, HP> &c, int i, const TF de[6]) {
   const SolveParams &P = *c.P;
-  const int p = (1 << K) - (1 << LEV) + i;
-  const int slot = ((1 << (LEV - 6)) - 1) + (i - (c.lane << (LEV - 6)));
+  const int p = DMN_IDX((1 << K) - (1 << LEV) + i, (1 << K) - 1);
+  const int slot = DMN_IDX(((1 << (LEV - 6)) - 1) + (i - (c.lane << (LEV - 6))), (1 << (K - 5)) - 1);
   const float *g = c.ghw + slot * 21 * 32 + c.lane;
   TF gh[21];
 #pragma unroll
@@ -500,6 +503,7 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
       } else {
         active = true;
         pt = int64_t(q);
+        DMN_BOUNDS_CLEAR();
         const double *sin = P.sin + pt * P.SW;
         c.sin = sin;
         c.sout = P.sout + pt * P.SW;
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
       for (int q2 = 0; q2 < 6; ++q2) So[q2] = hp_shfl_down(kFull, S[q2], 1, 32);
       if ((lane & 1) == 0) {
         const int j = lane >> 1, p = pu0 + j;
-        combine_node<TF, HP>(P, p, rec, other, S, So, c.r2, c.full, ghu + 21 * (p - pu0));
+        combine_node<TF, HP>(P, p, rec, other, S, So, c.r2, c.full, ghu + 21 * DMN_IDX(p - pu0, kUpNodes));
         rec_to_smem(rec5 + RSW * (warp * 16 + j), rec);
 #pragma unroll
         for (int q2 = 0; q2 < 6; ++q2) s5[6 * (warp * 16 + j) + q2] = S[q2];
@@ -586,31 +590,33 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
           const bool from5 = ((k + 1) & 1) != 0;
           const TF *rb = from5 ? rec5 + RSW * (pw * 16) : rec4 + RSW * (pw * 8);
           const HP *sb = from5 ? s5 + 6 * (pw * 16) : s4 + 6 * (pw * 8);
+          const int jl = DMN_IDX(2 * j, from5 ? 15 : 7);  // both children inside the buffer
           Rec<TF> L, R;
-          rec_from_smem(L, rb + RSW * (2 * j));
-          rec_from_smem(R, rb + RSW * (2 * j + 1));
+          rec_from_smem(L, rb + RSW * jl);
+          rec_from_smem(R, rb + RSW * (jl + 1));
           HP SL[6], SR[6];
 #pragma unroll
           for (int q2 = 0; q2 < 6; ++q2) {
-            SL[q2] = sb[6 * (2 * j) + q2];
-            SR[q2] = sb[6 * (2 * j + 1) + q2];
+            SL[q2] = sb[6 * jl + q2];
+            SR[q2] = sb[6 * (jl + 1) + q2];
           }
           const int p = (1 << K) - (1 << k) + j;
           TF *ghu_pw = reinterpret_cast<TF *>(wbase0 + pw * wbytes + wlay_ghu(K));
           TF r2n = TF(0);
-          combine_node<TF, HP>(P, p, L, R, SL, SR, r2n, (pflag[pw] & 2) != 0, ghu_pw + 21 * (p - pu0));
-          r2up[pw * 16 + 16 - (1 << k) + j] = r2n;
+          combine_node<TF, HP>(P, p, L, R, SL, SR, r2n, (pflag[pw] & 2) != 0,
+                               ghu_pw + 21 * DMN_IDX(p - pu0, kUpNodes));
+          r2up[pw * 16 + DMN_IDX(16 - (1 << k) + j, 15)] = r2n;
           TF *rd;
           HP *sd;
           if (k == 1) {
             rd = rootr + RSW * pw;
             sd = sroot + 6 * pw;
           } else if (k & 1) {  // levels 3: the level-5 slots are free again
-            rd = rec5 + RSW * (pw * 16 + j);
-            sd = s5 + 6 * (pw * 16 + j);
+            rd = rec5 + RSW * (pw * 16 + DMN_IDX(j, 16));
+            sd = s5 + 6 * (pw * 16 + DMN_IDX(j, 16));
           } else {
-            rd = rec4 + RSW * (pw * 8 + j);
-            sd = s4 + 6 * (pw * 8 + j);
+            rd = rec4 + RSW * (pw * 8 + DMN_IDX(j, 8));
+            sd = s4 + 6 * (pw * 8 + DMN_IDX(j, 8));
           }
           rec_to_smem(rd, L);
 #pragma unroll
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
           HP hr[6];
           if ((lane & (stride - 1)) == 0) {
             const int j = lane >> (6 - k), p = (1 << K) - (1 << k) + j;
-            const TF *g = ghu + 21 * (p - pu0);
+            const TF *g = ghu + 21 * DMN_IDX(p - pu0, kUpNodes);
             TF da[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -774,8 +780,9 @@ __global__ void __launch_bounds__(32 * W, MINB) dmn_solve_warp(const SolveParams
           __stcs(P.out + pt * kOutWords + cc, v);
         }
         bad = __any_sync(kFull, bad);
+        const int bbad = DMN_BOUNDS_GET();
         if (lane == 0) {
-          P.status[pt] = (bad ? 2 : status) | (attempt ? 4 : 0);
+          P.status[pt] = (bad ? 2 : status) | (attempt ? 4 : 0) | (bbad ? kPtBounds : 0);
           P.iters[pt] = it + it_total;
         }
         if (lane < 8) sout[lane] = lane < 6 ? ebd[lane] : (lane == 6 ? theta : 0.0);

@@ -16,6 +16,7 @@ from . import _build
 DMN_OK, DMN_ERR_ARG = 0, 1
 PT_OK, PT_NOT_CONVERGED, PT_NONFINITE, PT_FALLBACK_USED = 0, 1, 2, 4
 PT_OUTER_NOT_CONVERGED = 8
+PT_BOUNDS = 16  # debug library: an index check failed at the point
 MIXED_ADIABATIC = 1 << 6  # dmn_eval_mixed mask bit: theta from the heat balance
 MIXED_PREDICT = 1  # dmn_eval_mixed flag: start from the previous outputs' linear model
 PREC_FP64, PREC_MIXED = 0, 1
@@ -54,6 +55,7 @@ SIGNATURES = {
     "dmn_last_error": (ctypes.c_char_p, []),
     "dmn_eval_noalloc": (_I32, [_I32, _P, _P, _P, _P, _I32, _P, _P, _I64, _P, _P, _D, _P, _P, _P,
                                 _P, _P]),
+    "dmn_debug_bounds_log": (_I32, [_P, _P, _P, _P, _I32]),
     # include/dmn_mlp.h
     "dmn_mlp_create": (_I32, [_P, _I32, _I32, _I32, _I64, ctypes.c_uint64]),
     "dmn_mlp_destroy": (_I32, [_P]),
@@ -85,19 +87,25 @@ SIGNATURES = {
 }
 
 
+def _debug() -> bool:
+    """DMN_LIBRARY=debug selects the bounds-checking build of the library."""
+    return os.environ.get("DMN_LIBRARY", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if _debug() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load ``libdmn.so`` (building it with nvcc if it is missing)."""
+    """Load ``libdmn.so`` (or, with DMN_LIBRARY=debug, ``libdmn_debug.so``),
+    building it with nvcc if it is missing."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = library_path()
         if not os.path.exists(path):
             if not build_if_missing:
                 raise ImportError(f"DMN CUDA library not built: {path}")
-            _build.build()
+            _build.build(debug=_debug())
         lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(lib, name)
@@ -297,3 +305,13 @@ class DMN:
                                   _dev(iters, torch.int32, (n,), "iters"),
                                   _dev(da, torch.float32, (n, 3 * self.nnode), "da")), "dmn_eval_warm")
         return state_out, out, status, iters
+
+
+def bounds_log(clear=True):
+    """The debug library's index-check log: (count, index, bound, line)."""
+    lib = load()
+    c, i, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    ln = ctypes.c_int32()
+    _check(lib.dmn_debug_bounds_log(ctypes.byref(c), ctypes.byref(i), ctypes.byref(b), ctypes.byref(ln),
+                                    1 if clear else 0), "dmn_debug_bounds_log")
+    return c.value, i.value, b.value, ln.value

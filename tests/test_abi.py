@@ -76,3 +76,13 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     bp[0] = 7
     assert create(3, w, n, bp) == 1
     assert create(3, w, n, ph, nm=0) == 1
+
+
+def test_release_library_has_no_bounds_log():
+    """The index-check log exists only in the debug build; the release
+    library says so (no CUDA call is made)."""
+    from paper_2109_14403_gb300 import dmn
+    if dmn.library_path().endswith("libdmn_debug.so"):
+        pytest.skip("debug library selected in this process")
+    with pytest.raises(RuntimeError, match="debug library"):
+        dmn.bounds_log()
