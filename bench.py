@@ -1054,12 +1054,17 @@ def main():
     ref = DMN(K_DEPTH, w, nrm, ph, mats, tol=1e-13, precision="fp64")
     bufs[0], bufs[1] = snap_prev.clone(), snap_cur.clone()
     kev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(steps)]
-    acc, tan_max, tan_med, fb, iters = [], [], [], 0, []
+    acc, tan_max, tan_med, fb, iters, it64 = [], [], [], 0, [], []
     for j in range(steps):
         _, oref, _, _ = ref.eval(D[first + j], T[first + j], 1.0, bufs[1])
         it = torch.empty(n, dtype=torch.int32, device=dev)
+        cur = bufs[1]
         warm_step(first + j, it, kev[j])
         iters.append(it)
+        # the FP64 path from the same state and the same predicted start:
+        # how many of the iterations the start leaves are the mixed path's
+        _, _, _, itf = fp64.eval_warm(D[first + j], T[first + j], 1.0, cur, da)
+        it64.append(itf)
         sig, sref = out[:, :6], oref[:, :6]
         acc.append(((sig - sref).norm(dim=1) / sref.norm(dim=1)).max().item())
         tan_rel = (out[:, 6:42] - oref[:, 6:42]).norm(dim=1) / oref[:, 6:42].norm(dim=1)
@@ -1079,6 +1084,7 @@ def main():
     hist = torch.bincount(itc.cpu().long()).tolist()
     mean_iters = float(itc.float().mean().item())
     iters_per_incr = [round(float(x.float().mean().item()), 4) for x in iters]
+    fp64_warm_iters = float(torch.cat(it64).float().mean().item())
 
     # ---- the same increments without the network, mixed and FP64
     variants = {}
@@ -1134,6 +1140,7 @@ def main():
             "config": arm_config(n, first, steps, plastic, world),
             "accuracy": accuracy,
             "iter_hist": hist, "mean_iters": mean_iters, "mean_iters_per_increment": iters_per_incr,
+            "fp64_from_the_same_start_mean_iters": fp64_warm_iters,
             "fallback_rate": fallback_rate,
             "graph": {"captured": "network input, 4 GEMMs, warm-started solve per increment (one CUDA graph "
                                   "per rotation of the 3 state buffers); inputs copied in before each replay",
