@@ -425,10 +425,10 @@ def run_large(args):
     perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
     X, Y = X[perm].contiguous(), Y[perm].contiguous()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    B, epochs = 4096, 12
-    for ep in range(epochs):
+    B, epochs = 4096, args.epochs
+    for ep in range(epochs):  # 1e-3, the last third at 2e-4
         for i in range(0, X.shape[0] - B + 1, B):
-            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if 3 * ep < 2 * epochs else 2e-4, loss)
     torch.cuda.synchronize()
     train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
                   "gen_and_train_s": time.perf_counter() - t0}
@@ -862,6 +862,7 @@ def main():
                     help="uneven, cyclic and linear (fp64 or fp32 laminates) workloads only")
     ap.add_argument("--matrix", default="perzyna", choices=["perzyna", "pa66"],
                     help="cyclic workload only: the matrix law")
+    ap.add_argument("--epochs", type=int, default=12, help="training epochs of the warm-start network")
     ap.add_argument("--variant", type=int, default=None,
                     help="solve variant of the timed mixed path (default: the tuning table's)")
     ap.add_argument("--workload", default="random_walk",
@@ -954,16 +955,16 @@ def main():
     perm = torch.randperm(X.shape[0], device=dev, generator=torch.Generator(device=dev).manual_seed(0))
     X, Y = X[perm].contiguous(), Y[perm].contiguous()
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    B, epochs = 4096, 12
-    for ep in range(epochs):
+    B, epochs = 4096, args.epochs
+    for ep in range(epochs):  # 1e-3, the last third at 2e-4
         for i in range(0, X.shape[0] - B + 1, B):
-            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if ep < 8 else 2e-4, loss)
+            net.train_step(X[i:i + B], Y[i:i + B], 1e-3 if 3 * ep < 2 * epochs else 2e-4, loss)
     torch.cuda.synchronize()
     train_info = {"pairs": int(X.shape[0]), "epochs": epochs, "batch": B, "final_loss": loss.item(),
                   "gen_and_train_s": time.perf_counter() - t0,
                   "pairs_from": f"FP64 solves: increments 1-{n_gen} of the timed batch; increments "
                                 f"2, 4, .., {2 * (n_incr // 2)} of two more batches drawn with other seeds",
-                  "network": "773 -> 3 x 512 SiLU -> 765, bf16/fp32-accumulate tcgen05, AMSGrad"}
+                  "network": f"{net.n_in} -> 3 x 512 SiLU -> {net.n_out}, bf16/fp32-accumulate tcgen05, AMSGrad"}
     del X, Y
     start_prev, start_cur = s_prev.clone(), s.clone()
 

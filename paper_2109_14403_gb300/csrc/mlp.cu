@@ -76,19 +76,31 @@ unsigned blocks_for(int64_t n, int t = 256) {
 }
 
 // ------------------------------------------------------------------ kernels
+// feature c of a row: deps (6), theta^{n+1}, theta^{n+1} - theta^n,
+// a^n - a^{n-1} (n3), then the load state and the previous increment's load:
+// eps_bar^n (6), eps_bar^n - eps_bar^{n-1} (6), theta^n - theta^{n-1};
+// a = the state block at t^n, ap = at t^{n-1} or NULL (its columns 0)
+constexpr int kExtraFeatures = 13;
+__device__ __forceinline__ double feature(int c, int n3, const double *dep, double th, const double *a,
+                                          const double *ap) {
+  if (c < 6) return dep[c];
+  if (c == 6) return th;
+  if (c == 7) return th - a[6];
+  if (c < 8 + n3) return ap ? a[c] - ap[c] : 0.0;  // a^n - a^{n-1}: state words 8..
+  const int j = c - (8 + n3);
+  if (j < 6) return a[j];
+  if (j < 12) return ap ? a[j - 6] - ap[j - 6] : 0.0;
+  return ap ? a[6] - ap[6] : 0.0;
+}
+
 __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const double *theta,
                            const double *sin, const double *sprev, float *feat) {
-  const int nin = 8 + n3;
+  const int nin = 8 + n3 + kExtraFeatures;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * nin;
        i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i / nin;
     const int c = int(i - r * nin);
-    double v;
-    if (c < 6) v = deps[r * 6 + c];
-    else if (c == 6) v = theta[r];
-    else if (c == 7) v = theta[r] - sin[r * sw + 6];
-    else v = sprev ? sin[r * sw + 8 + (c - 8)] - sprev[r * sw + 8 + (c - 8)] : 0.0;
-    feat[i] = float(v);
+    feat[i] = float(feature(c, n3, deps + r * 6, theta[r], sin + r * sw, sprev ? sprev + r * sw : nullptr));
   }
 }
 
@@ -98,7 +110,7 @@ __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const 
 __global__ void k_features_norm(int64_t n, int n3, int sw, int ld, const double *deps,
                                 const double *theta, const double *sin, const double *sprev,
                                 const float *mean, const float *inv, bf16 *x) {
-  const int nin = 8 + n3;
+  const int nin = 8 + n3 + kExtraFeatures;
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < n; r += nwarp) {
@@ -112,11 +124,7 @@ __global__ void k_features_norm(int64_t n, int n3, int sw, int ld, const double 
         const int c = c0 + u;
         v[u] = 0.0f;
         if (c < nin) {
-          double f;
-          if (c < 6) f = deps[r * 6 + c];
-          else if (c == 6) f = theta[r];
-          else if (c == 7) f = theta[r] - a[6];
-          else f = ap ? a[c] - ap[c] : 0.0;
+          const double f = feature(c, n3, deps + r * 6, theta[r], a, ap);
           v[u] = (float(f) - mean[c]) * inv[c];
         }
       }
@@ -414,7 +422,7 @@ extern "C" dmn_status dmn_mlp_create(dmn_mlp *out, int32_t K, int32_t hidden, in
   dmn_mlp p = new dmn_mlp_s();
   p->K = K;
   p->n3 = 3 * ((1 << K) - 1);
-  p->nin = 8 + p->n3;
+  p->nin = 8 + p->n3 + kExtraFeatures;
   p->kin = int(rup(p->nin, 128));
   p->H = hidden;
   p->nh = n_hidden;
