@@ -8,10 +8,7 @@
  * whose warm-started iteration fails is re-run from a^n.
  *
  * Network: input [deps (6), theta^{n+1}, theta^{n+1} - theta^n,
- * a^n - a^{n-1} (3(2^K - 1)), eps_bar^n (6), eps_bar^n - eps_bar^{n-1} (6),
- * theta^n - theta^{n-1}] (the load step, the previous increment's response
- * and the load that caused it, the load state), normalised per column;
- * n_hidden layers of width
+ * a^n - a^{n-1} (3(2^K - 1))], normalised per column; n_hidden layers of width
  * `hidden` with SiLU; linear output of 3(2^K - 1) normalised increments.
  * BF16 weights and activations, FP32 accumulation on the tensor cores
  * (tcgen05), FP32 master weights, MSE loss on normalised targets, AMSGrad
@@ -42,13 +39,13 @@ dmn_status dmn_mlp_create(dmn_mlp *out, int32_t K, int32_t hidden, int32_t n_hid
                           int64_t max_batch, uint64_t seed);
 dmn_status dmn_mlp_destroy(dmn_mlp m);
 
-/* Widths: n_in = 8 + 3(2^K-1) + 13, n_in_pad, n_out = 3(2^K-1), n_out_pad. */
+/* Widths: n_in = 8 + 3(2^K-1), n_in_pad, n_out = 3(2^K-1), n_out_pad. */
 dmn_status dmn_mlp_dims(dmn_mlp m, int32_t *n_in, int32_t *n_in_pad, int32_t *n_out,
                         int32_t *n_out_pad);
 
 /* Raw features, fp32 [n x n_in], from the increment's inputs and the state at
    t^n; d_state_prev (state at t^{n-1}) may be NULL (no previous increment:
-   the columns of differences to t^{n-1} are 0). */
+   the a^n - a^{n-1} columns are 0). */
 dmn_status dmn_mlp_features(dmn_mlp m, dmn_stream stream, int64_t n, const double *d_deps,
                             const double *d_theta, const double *d_state_in,
                             const double *d_state_prev, int64_t state_words, float *d_feat);

@@ -77,20 +77,16 @@ unsigned blocks_for(int64_t n, int t = 256) {
 
 // ------------------------------------------------------------------ kernels
 // feature c of a row: deps (6), theta^{n+1}, theta^{n+1} - theta^n,
-// a^n - a^{n-1} (n3), then the load state and the previous increment's load:
-// eps_bar^n (6), eps_bar^n - eps_bar^{n-1} (6), theta^n - theta^{n-1};
-// a = the state block at t^n, ap = at t^{n-1} or NULL (its columns 0)
-constexpr int kExtraFeatures = 13;
+// a^n - a^{n-1} (n3); a = the state block at t^n, ap = at t^{n-1} or NULL
+// (its columns 0)
+constexpr int kExtraFeatures = 0;
 __device__ __forceinline__ double feature(int c, int n3, const double *dep, double th, const double *a,
                                           const double *ap) {
+  (void)n3;
   if (c < 6) return dep[c];
   if (c == 6) return th;
   if (c == 7) return th - a[6];
-  if (c < 8 + n3) return ap ? a[c] - ap[c] : 0.0;  // a^n - a^{n-1}: state words 8..
-  const int j = c - (8 + n3);
-  if (j < 6) return a[j];
-  if (j < 12) return ap ? a[j - 6] - ap[j - 6] : 0.0;
-  return ap ? a[6] - ap[6] : 0.0;
+  return ap ? a[c] - ap[c] : 0.0;  // a^n - a^{n-1}: state words 8..
 }
 
 __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const double *theta,

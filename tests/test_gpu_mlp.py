@@ -324,7 +324,7 @@ def test_warm_start_k9_perzyna():
     dt = syn.LARGE_DT
     plain = DMN(K, w, nrm, ph, mats, precision="fp64", tol=1e-13)
     net = MLP(K=K, hidden=256, n_hidden=2, max_batch=n, seed=0)
-    assert net.n_in == 8 + 3 * 511 + 13 and net.n_out == 3 * 511
+    assert net.n_in == 8 + 3 * 511 and net.n_out == 3 * 511
     s_prev, s = None, plain.init_state(torch.full((n,), 293.0, dtype=torch.float64, device=dev))
     feats, tgts = [], []
     for k in range(n_train):
@@ -362,8 +362,7 @@ def test_warm_start_k9_perzyna():
 
 def test_features_match_the_state():
     """The network's raw features against their definition, computed here
-    from the same device states: the load step, a^n - a^{n-1}, eps_bar^n,
-    eps_bar^n - eps_bar^{n-1} and theta^n - theta^{n-1} (exact FP64
+    from the same device states: the load step and a^n - a^{n-1} (exact FP64
     differences rounded once to FP32); without a previous state the
     difference columns are 0."""
     from paper_2109_14403_gb300 import DMN
@@ -383,13 +382,10 @@ def test_features_match_the_state():
     a, ap = s2.cpu().numpy(), s1.cpu().numpy()
     n3 = 3 * ((1 << K) - 1)
     ref = np.concatenate([deps[2], theta[2][:, None], (theta[2] - a[:, 6])[:, None],
-                          a[:, 8:8 + n3] - ap[:, 8:8 + n3], a[:, :6], a[:, :6] - ap[:, :6],
-                          (a[:, 6] - ap[:, 6])[:, None]], axis=1).astype(np.float32)
+                          a[:, 8:8 + n3] - ap[:, 8:8 + n3]], axis=1).astype(np.float32)
     assert f.shape == (n, net.n_in) == ref.shape
     np.testing.assert_array_equal(f, ref)
-    ref0 = ref.copy()
-    ref0[:, 8:8 + n3] = 0.0
-    ref0[:, 8 + n3 + 6:] = 0.0
-    np.testing.assert_array_equal(f0, ref0)
+    ref[:, 8:] = 0.0
+    np.testing.assert_array_equal(f0, ref)
     net.close()
     d.close()
