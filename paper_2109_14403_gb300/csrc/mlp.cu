@@ -36,11 +36,11 @@ cudaError_t get_encode() {
   return cudaSuccess;
 }
 
-// bf16 row-major [rows x cols] read in 128-row x 64-column boxes, 128 B swizzle
-bool make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t cols) {
+// bf16 row-major [rows x cols] read in box_rows x 64-column boxes, 128 B swizzle
+bool make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows = 128) {
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {cols * 2};
-  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t box[2] = {64, box_rows};
   const cuuint32_t es[2] = {1, 1};
   return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -48,8 +48,11 @@ bool make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t cols) {
 }
 
 int g_gemm_configured_dev = -1;
+int g_gemm_sms = 0;
 
-// C = A . B^T with the fused epilogue ep; A [M x K], B [N x K] bf16
+// C = A . B^T with the fused epilogue ep; A [M x K], B [N x K] bf16.  N a
+// multiple of 256: the persistent wide form (one CTA per SM), else the tile
+// form.
 cudaError_t gemm(cudaStream_t s, const void *A, const void *B, int M, int N, int K, EpiArgs ep) {
   if (M % BM || N % BN || K % BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
   if (M / BM > 65535 || N / BN > 65535) return cudaErrorInvalidValue;  // grid limits
@@ -60,10 +63,19 @@ cudaError_t gemm(cudaStream_t s, const void *A, const void *B, int M, int N, int
   cudaGetDevice(&dev);
   if (g_gemm_configured_dev != dev) {
     e = cudaFuncSetAttribute(gemm_bf16_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_bf16_tn_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, WGEMM_SMEM);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_gemm_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     g_gemm_configured_dev = dev;
   }
   CUtensorMap ma, mb;
+  if (N % WBN == 0) {
+    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, WBN)) return cudaErrorInvalidValue;
+    const int tiles = (M / BM) * (N / WBN);
+    gemm_bf16_tn_wide<<<tiles < g_gemm_sms ? tiles : g_gemm_sms, 192, WGEMM_SMEM, s>>>(ma, mb, M, N, K, ep);
+    return cudaGetLastError();
+  }
   if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) return cudaErrorInvalidValue;
   gemm_bf16_tn<<<dim3(N / BN, M / BM), 128, GEMM_SMEM, s>>>(ma, mb, K, ep);
   return cudaGetLastError();

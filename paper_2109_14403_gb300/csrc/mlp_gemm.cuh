@@ -2,8 +2,11 @@
 //   C[M x N] = A[M x K] . B[N x K]^T   (A, B bf16 with K contiguous; FP32
 //   accumulation in tensor memory), followed by a fused epilogue.
 //
-// One CTA of 128 threads computes a 128 x 128 tile (grid: column tiles fastest);
-// two CTAs share an SM, so one's epilogue overlaps the other's MMAs:
+// Two forms.  The persistent wide form (below, gemm_bf16_tn_wide) serves N a
+// multiple of 256; the tile form serves every other shape (N a multiple of
+// 128).  Tile form: one CTA of 128 threads computes a 128 x 128 tile (grid:
+// column tiles fastest); two CTAs share an SM, so one's epilogue overlaps the
+// other's MMAs:
 //   warp 0, lane 0  loads A and B tiles (64 wide in K) with TMA bulk tensor
 //                   copies into a 3-stage ring of 128-byte-swizzled shared
 //                   memory, signalled by mbarriers with transaction counts;
@@ -133,6 +136,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
+// The epilogue of 16 accumulator columns n..n+15 of output row r, every mode
+// but the staged de-normalised prediction (EPI_BIAS_F32 with scale)
+__device__ __forceinline__ void epi_chunk16(const EpiArgs &ep, int r, int n, const float v[16]) {
+  if (ep.mode == EPI_BIAS_SILU) {
+    __align__(16) __nv_bfloat16 zb[16], hb[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float z = v[i] + ep.bias[n + i];
+      zb[i] = __float2bfloat16(z);
+      hb[i] = __float2bfloat16(z * sigmoidf_(z));
+    }
+    if (ep.z_out) {
+      uint4 *zo = reinterpret_cast<uint4 *>(ep.z_out + size_t(r) * ep.ldc + n);
+      zo[0] = reinterpret_cast<uint4 *>(zb)[0];
+      zo[1] = reinterpret_cast<uint4 *>(zb)[1];
+    }
+    uint4 *ho = reinterpret_cast<uint4 *>(ep.h_out + size_t(r) * ep.ldc + n);
+    ho[0] = reinterpret_cast<uint4 *>(hb)[0];
+    ho[1] = reinterpret_cast<uint4 *>(hb)[1];
+    if (ep.t_out) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) ep.t_out[size_t(n + i) * ep.ldt + r] = hb[i];
+    }
+  } else if (ep.mode == EPI_DSILU) {
+    __align__(16) __nv_bfloat16 db[16];
+    const __nv_bfloat16 *zi = ep.z_in + size_t(r) * ep.ldc + n;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float z = __bfloat162float(zi[i]);
+      const float sg = sigmoidf_(z);
+      db[i] = __float2bfloat16(v[i] * sg * (1.0f + z * (1.0f - sg)));
+    }
+    uint4 *dout = reinterpret_cast<uint4 *>(ep.h_out + size_t(r) * ep.ldc + n);
+    dout[0] = reinterpret_cast<uint4 *>(db)[0];
+    dout[1] = reinterpret_cast<uint4 *>(db)[1];
+    if (ep.t_out) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) ep.t_out[size_t(n + i) * ep.ldt + r] = db[i];
+    }
+  } else if (ep.mode == EPI_BIAS_F32) {
+    float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      fo[q] = make_float4(v[4 * q] + ep.bias[n + 4 * q], v[4 * q + 1] + ep.bias[n + 4 * q + 1],
+                          v[4 * q + 2] + ep.bias[n + 4 * q + 2], v[4 * q + 3] + ep.bias[n + 4 * q + 3]);
+  } else {  // EPI_F32
+    float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+}
+
 __global__ void __launch_bounds__(128, 2)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                  int K, const EpiArgs ep) {
@@ -218,59 +273,12 @@ __global__ void __launch_bounds__(128, 2)
       float v[16];
       tmem_ld16(trow + c0, v);
       const int n = n0 + c0;
-      if (ep.mode == EPI_BIAS_SILU) {
-        __align__(16) __nv_bfloat16 zb[16], hb[16];
+      if (ep.mode == EPI_BIAS_F32 && ep.scale) {  // staged: the ring holds no operands once `done` has fired
+        float *srow = reinterpret_cast<float *>(base) + (warp * 32 + lane) * (BN + 1);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float z = v[i] + ep.bias[n + i];
-          zb[i] = __float2bfloat16(z);
-          hb[i] = __float2bfloat16(z * sigmoidf_(z));
-        }
-        if (ep.z_out) {
-          uint4 *zo = reinterpret_cast<uint4 *>(ep.z_out + size_t(r) * ep.ldc + n);
-          zo[0] = reinterpret_cast<uint4 *>(zb)[0];
-          zo[1] = reinterpret_cast<uint4 *>(zb)[1];
-        }
-        uint4 *ho = reinterpret_cast<uint4 *>(ep.h_out + size_t(r) * ep.ldc + n);
-        ho[0] = reinterpret_cast<uint4 *>(hb)[0];
-        ho[1] = reinterpret_cast<uint4 *>(hb)[1];
-        if (ep.t_out) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) ep.t_out[size_t(n + i) * ep.ldt + r] = hb[i];
-        }
-      } else if (ep.mode == EPI_DSILU) {
-        __align__(16) __nv_bfloat16 db[16];
-        const __nv_bfloat16 *zi = ep.z_in + size_t(r) * ep.ldc + n;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float z = __bfloat162float(zi[i]);
-          const float sg = sigmoidf_(z);
-          db[i] = __float2bfloat16(v[i] * sg * (1.0f + z * (1.0f - sg)));
-        }
-        uint4 *dout = reinterpret_cast<uint4 *>(ep.h_out + size_t(r) * ep.ldc + n);
-        dout[0] = reinterpret_cast<uint4 *>(db)[0];
-        dout[1] = reinterpret_cast<uint4 *>(db)[1];
-        if (ep.t_out) {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) ep.t_out[size_t(n + i) * ep.ldt + r] = db[i];
-        }
-      } else if (ep.mode == EPI_BIAS_F32) {
-        if (ep.scale) {  // staged: the ring holds no operands once `done` has fired
-          float *srow = reinterpret_cast<float *>(base) + (warp * 32 + lane) * (BN + 1);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) srow[c0 + i] = v[i];
-        } else {
-          float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            fo[q] = make_float4(v[4 * q] + ep.bias[n + 4 * q], v[4 * q + 1] + ep.bias[n + 4 * q + 1],
-                                v[4 * q + 2] + ep.bias[n + 4 * q + 2],
-                                v[4 * q + 3] + ep.bias[n + 4 * q + 3]);
-        }
-      } else {  // EPI_F32
-        float4 *fo = reinterpret_cast<float4 *>(ep.f_out + size_t(r) * ep.ldc + n);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fo[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int i = 0; i < 16; ++i) srow[c0 + i] = v[i];
+      } else {
+        epi_chunk16(ep, r, n, v);
       }
     }
     if (ep.mode == EPI_BIAS_F32 && ep.scale) {
@@ -303,6 +311,183 @@ __global__ void __launch_bounds__(128, 2)
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+  }
+}
+
+// ---------------------------------------------------------------- wide form
+// Persistent form for N a multiple of 256 (the network's forward layers: N =
+// 512 or 768): one CTA per SM loops over 128 x 256 tiles (column tiles
+// fastest, so the CTAs sharing an A panel run together and read it from L2).
+// Six warps with fixed roles:
+//   warp 0, lane 0  TMA producer: A (128 x 64) and B (256 x 64) of each K step
+//                   into a 4-stage ring (48 KB per stage);
+//   warp 1          allocates all 512 TMEM columns (two 256-column FP32
+//                   accumulators); its lane 0 issues tcgen05.mma (M = 128,
+//                   N = 256, K = 16) and commits each stage to its "empty"
+//                   barrier and each finished tile to its accumulator's
+//                   "full" barrier;
+//   warps 2..5      the epilogue: warp w reads TMEM lanes 32 (w % 4).. with
+//                   tcgen05.ld, applies the fused epilogue and releases the
+//                   accumulator ("empty", one arrival per warp), so the MMAs
+//                   of the next tile run into the other accumulator meanwhile.
+// The de-normalised FP32 prediction is staged per warp (32 rows x 32 columns)
+// and written row by row, the lanes on consecutive columns.  Every wait is
+// bounded as in the form above.
+constexpr int WBN = 256, WST = 4;
+constexpr int WTILE_B = WBN * BK * 2;
+constexpr int WSTAGE = TILE_A + WTILE_B;  // 48 KB, a multiple of 1024
+constexpr int WSTAGE_EPI = 4 * 32 * 33 * 4;  // staging of the prediction: 4 warps x 32 x 33 floats
+constexpr int WGEMM_SMEM = WST * WSTAGE + WSTAGE_EPI + 1024 + 256;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+    gemm_bf16_tn_wide(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      int M, int N, int K, const EpiArgs ep) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(gsm) + 1023) & ~uintptr_t(1023));
+  float *stage_epi = reinterpret_cast<float *>(base + WST * WSTAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + WST * WSTAGE + WSTAGE_EPI);
+  uint64_t *empty = full + WST;
+  uint64_t *accf = empty + WST;  // 2: accumulator full (MMA -> epilogue)
+  uint64_t *acce = accf + 2;     // 2: accumulator empty (epilogue -> MMA)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+  int *fail = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntn = N / WBN, ntiles = (M / BM) * ntn, nk = K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < WST; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---- TMA producer ----
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int m0 = (t / ntn) * BM, n0 = (t % ntn) * WBN;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int st = it % WST;
+          if (it >= WST && !mbar_wait(&empty[st], ((it / WST) - 1) & 1)) {
+            atomicExch(fail, 1);
+            break;
+          }
+          if (*(volatile int *)fail) break;
+          mbar_expect_tx(&full[st], WSTAGE);
+          tma_load_2d(base + st * WSTAGE, &map_a, &full[st], kb * BK, m0);
+          tma_load_2d(base + st * WSTAGE + TILE_A, &map_b, &full[st], kb * BK, n0);
+        }
+        if (*(volatile int *)fail) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16(BM, WBN);
+      int it = 0, j = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait(&acce[b], ((j >> 1) - 1) & 1)) {
+          atomicExch(fail, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + uint32_t(b * WBN);
+        bool bad = false;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int st = it % WST;
+          if (!mbar_wait(&full[st], (it / WST) & 1)) {
+            atomicExch(fail, 1);
+            bad = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ad = sdesc_sw128(base + st * WSTAGE), bd = sdesc_sw128(base + st * WSTAGE + TILE_A);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma(acc, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          umma_commit(&empty[st]);
+        }
+        if (bad) break;
+        umma_commit(&accf[b]);  // arrives once this tile's MMAs have completed
+      }
+    }
+  } else {  // ---- epilogue: warps 2..5 ----
+    const int qd = warp & 3;  // TMEM lane quarter = tile rows 32 qd ..
+    float *stg = stage_epi + (warp - 2) * 32 * 33;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      const bool ok = mbar_wait(&accf[b], (j >> 1) & 1);
+      if (!__all_sync(0xffffffffu, ok) || *(volatile int *)fail) {
+        if (lane == 0) atomicExch(fail, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (t / ntn) * BM, n0 = (t % ntn) * WBN;
+      const int r = m0 + qd * 32 + lane;
+      const uint32_t trow = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * WBN);
+      if (ep.mode == EPI_BIAS_F32 && ep.scale) {
+        for (int c0 = 0; c0 < WBN; c0 += 32) {
+          float v[16], w[16];
+          tmem_ld16(trow + c0, v);
+          tmem_ld16(trow + c0 + 16, w);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            stg[lane * 33 + i] = v[i];
+            stg[lane * 33 + 16 + i] = w[i];
+          }
+          __syncwarp();
+          const int n = n0 + c0 + lane;
+          const bool cv = n < ep.n_valid;
+          const float bb = cv ? ep.bias[n] : 0.0f, sc = cv ? ep.scale[n] : 0.0f, sh = cv ? ep.shift[n] : 0.0f;
+          for (int rr = 0; rr < 32; ++rr) {
+            const int rg = m0 + qd * 32 + rr;
+            if (rg >= ep.m_valid) break;
+            if (cv) ep.f_out[size_t(rg) * ep.ld_f + n] = (stg[rr * 33 + lane] + bb) * sc + sh;
+          }
+          __syncwarp();
+        }
+      } else {
+        for (int c0 = 0; c0 < WBN; c0 += 16) {
+          float v[16];
+          tmem_ld16(trow + c0, v);
+          epi_chunk16(ep, r, n0 + c0, v);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
+  }
+  __syncwarp();  // lanes 1..31 of the producer and MMA warps wait for lane 0 here
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int *)fail && ep.err) atomicExch(ep.err, 1);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
   }
 }
 
