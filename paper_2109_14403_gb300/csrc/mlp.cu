@@ -73,7 +73,8 @@ cudaError_t gemm(cudaStream_t s, const void *A, const void *B, int M, int N, int
   if (N % WBN == 0) {
     if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, WBN)) return cudaErrorInvalidValue;
     const int tiles = (M / BM) * (N / WBN);
-    gemm_bf16_tn_wide<<<tiles < g_gemm_sms ? tiles : g_gemm_sms, 192, WGEMM_SMEM, s>>>(ma, mb, M, N, K, ep);
+    gemm_bf16_tn_wide<<<tiles < g_gemm_sms ? tiles : g_gemm_sms, 64 + 32 * WEPI, WGEMM_SMEM, s>>>(ma, mb, M, N,
+                                                                                              K, ep);
     return cudaGetLastError();
   }
   if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) return cudaErrorInvalidValue;

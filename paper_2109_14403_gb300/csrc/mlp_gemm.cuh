@@ -134,16 +134,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// the logistic function; the quotient with the fast reciprocal (a few FP32
+// ulp), which the bf16 rounding of every result that uses it hides
+__device__ __forceinline__ float sigmoidf_(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+
+// two 16-column accumulator loads in flight, one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr + 16u));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 // The epilogue of 16 accumulator columns n..n+15 of output row r, every mode
 // but the staged de-normalised prediction (EPI_BIAS_F32 with scale)
 __device__ __forceinline__ void epi_chunk16(const EpiArgs &ep, int r, int n, const float v[16]) {
   if (ep.mode == EPI_BIAS_SILU) {
     __align__(16) __nv_bfloat16 zb[16], hb[16];
+    __align__(16) float bb[16];  // the chunk's biases, four vector loads (n is a multiple of 16)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reinterpret_cast<float4 *>(bb)[q] = reinterpret_cast<const float4 *>(ep.bias + n)[q];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const float z = v[i] + ep.bias[n + i];
+      const float z = v[i] + bb[i];
       zb[i] = __float2bfloat16(z);
       hb[i] = __float2bfloat16(z * sigmoidf_(z));
     }
@@ -326,24 +353,29 @@ __global__ void __launch_bounds__(128, 2)
 //                   N = 256, K = 16) and commits each stage to its "empty"
 //                   barrier and each finished tile to its accumulator's
 //                   "full" barrier;
-//   warps 2..5      the epilogue: warp w reads TMEM lanes 32 (w % 4).. with
-//                   tcgen05.ld, applies the fused epilogue and releases the
-//                   accumulator ("empty", one arrival per warp), so the MMAs
-//                   of the next tile run into the other accumulator meanwhile.
-// The de-normalised FP32 prediction is staged per warp (32 rows x 32 columns)
-// and written row by row, the lanes on consecutive columns.  Every wait is
-// bounded as in the form above.
-constexpr int WBN = 256, WST = 4;
+//   warps 2..9      the epilogue, two warps per TMEM lane quarter: warp w
+//                   reads lanes 32 (w % 4).. (tile rows) of one half of the
+//                   columns with tcgen05.ld, applies the fused epilogue and
+//                   releases the accumulator ("empty", one arrival per warp),
+//                   so the MMAs of the next tile run into the other
+//                   accumulator meanwhile.  (One warp per quarter could not
+//                   keep up: the SiLU epilogue of a 128 x 256 tile is longer
+//                   than its MMAs.)
+// The de-normalised FP32 prediction is staged per warp (32 rows x 16 columns)
+// and written two rows at a time, the lanes on consecutive columns.  Every
+// wait is bounded as in the form above.
+constexpr int WBN = 256, WST = 4, WEPI = 8;  // epilogue warps
 constexpr int WTILE_B = WBN * BK * 2;
 constexpr int WSTAGE = TILE_A + WTILE_B;  // 48 KB, a multiple of 1024
-constexpr int WSTAGE_EPI = 4 * 32 * 33 * 4;  // staging of the prediction: 4 warps x 32 x 33 floats
+constexpr int WSTAGE_EPI = WEPI * 32 * 17 * 4;  // staging of the prediction: per warp 32 x 17 floats
 constexpr int WGEMM_SMEM = WST * WSTAGE + WSTAGE_EPI + 1024 + 256;
+static_assert(WGEMM_SMEM <= 232448, "opt-in shared memory per CTA");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(64 + 32 * WEPI, 1)
     gemm_bf16_tn_wide(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                       int M, int N, int K, const EpiArgs ep) {
   extern __shared__ __align__(1024) unsigned char gsm[];
@@ -367,7 +399,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 4);
+      mbar_init(&acce[b], WEPI);
     }
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -433,9 +465,11 @@ __global__ void __launch_bounds__(192, 1)
         umma_commit(&accf[b]);  // arrives once this tile's MMAs have completed
       }
     }
-  } else {  // ---- epilogue: warps 2..5 ----
+  } else {  // ---- epilogue: warps 2..9 ----
     const int qd = warp & 3;  // TMEM lane quarter = tile rows 32 qd ..
-    float *stg = stage_epi + (warp - 2) * 32 * 33;
+    const int ch0 = ((warp - 2) >> 2) * (WBN / (WEPI / 4));  // this warp's columns
+    constexpr int CW = WBN / (WEPI / 4);
+    float *stg = stage_epi + (warp - 2) * 32 * 17;
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int b = j & 1;
@@ -449,31 +483,28 @@ __global__ void __launch_bounds__(192, 1)
       const int r = m0 + qd * 32 + lane;
       const uint32_t trow = tmem + (uint32_t(qd * 32) << 16) + uint32_t(b * WBN);
       if (ep.mode == EPI_BIAS_F32 && ep.scale) {
-        for (int c0 = 0; c0 < WBN; c0 += 32) {
-          float v[16], w[16];
+        for (int c0 = ch0; c0 < ch0 + CW; c0 += 16) {
+          float v[16];
           tmem_ld16(trow + c0, v);
-          tmem_ld16(trow + c0 + 16, w);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            stg[lane * 33 + i] = v[i];
-            stg[lane * 33 + 16 + i] = w[i];
-          }
+          for (int i = 0; i < 16; ++i) stg[lane * 17 + i] = v[i];
           __syncwarp();
-          const int n = n0 + c0 + lane;
+          // lanes 0..15 on row rr, 16..31 on row rr + 1, consecutive columns
+          const int cl = lane & 15, n = n0 + c0 + cl;
           const bool cv = n < ep.n_valid;
           const float bb = cv ? ep.bias[n] : 0.0f, sc = cv ? ep.scale[n] : 0.0f, sh = cv ? ep.shift[n] : 0.0f;
-          for (int rr = 0; rr < 32; ++rr) {
+          for (int rr = lane >> 4; rr < 32; rr += 2) {
             const int rg = m0 + qd * 32 + rr;
-            if (rg >= ep.m_valid) break;
-            if (cv) ep.f_out[size_t(rg) * ep.ld_f + n] = (stg[rr * 33 + lane] + bb) * sc + sh;
+            if (cv && rg < ep.m_valid) ep.f_out[size_t(rg) * ep.ld_f + n] = (stg[rr * 17 + cl] + bb) * sc + sh;
           }
           __syncwarp();
         }
       } else {
-        for (int c0 = 0; c0 < WBN; c0 += 16) {
-          float v[16];
-          tmem_ld16(trow + c0, v);
+        for (int c0 = ch0; c0 < ch0 + CW; c0 += 32) {
+          float v[32];
+          tmem_ld32(trow + c0, v);
           epi_chunk16(ep, r, n0 + c0, v);
+          epi_chunk16(ep, r, n0 + c0 + 16, v + 16);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
