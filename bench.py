@@ -139,8 +139,8 @@ class ClockSampler:
 
 
 # the translation unit of the headline solve kernel and everything it includes
-SOLVE_SOURCES = ("dfl.cuh", "dmn_internal.h", "dmn_kernels.cuh", "dmn_solve_compact.cu", "pa66.cuh",
-                 "solve_common.cuh", "solve_compact.cuh", "solve_warp.cuh", "dmn_solve_warp8.cu")
+SOLVE_SOURCES = ("dfl.cuh", "dmn_check.cuh", "dmn_internal.h", "dmn_kernels.cuh", "dmn_solve_compact.cu",
+                 "pa66.cuh", "solve_common.cuh", "solve_compact.cuh")
 
 
 def _code_only(text):

@@ -139,5 +139,14 @@ __device__ __forceinline__ double hp_shfl_down(unsigned m, double v, int o, int 
 __device__ __forceinline__ dfl hp_shfl_down(unsigned m, dfl v, int o, int w) {
   return {__shfl_down_sync(m, v.hi, o, w), __shfl_down_sync(m, v.lo, o, w)};
 }
+__device__ __forceinline__ float hp_shfl(unsigned m, float v, int src, int w) {
+  return __shfl_sync(m, v, src, w);
+}
+__device__ __forceinline__ double hp_shfl(unsigned m, double v, int src, int w) {
+  return __shfl_sync(m, v, src, w);
+}
+__device__ __forceinline__ dfl hp_shfl(unsigned m, dfl v, int src, int w) {
+  return {__shfl_sync(m, v.hi, src, w), __shfl_sync(m, v.lo, src, w)};
+}
 
 }  // namespace dmn

@@ -9,10 +9,11 @@
 //    formed at once, one node per thread, and summed per laminate after a
 //    single barrier;
 //  * compact levels: the laminates just above the bottom pair neighbouring
-//    lanes by shuffle; every higher level puts node j of the level on one
-//    thread, with the children's condensed records and stress sums in shared
-//    memory, so a level of at most 32 nodes occupies one warp (the CTA's
-//    leader warp, with warp barriers only) while the other warps go ahead;
+//    lanes by shuffle; every higher level condenses node j on eight lanes,
+//    one Mandel row each (combine_rows), with the children's condensed
+//    records and stress sums in shared memory, so a level of at most four
+//    nodes occupies one warp (the CTA's leader warp, with warp barriers
+//    only) while the other warps go ahead;
 //  * the back-substitution of the Newton increment, a chain through the
 //    levels, in the condensation precision TF on the same compact mapping.
 // The leader warp is picked from the CTA's warp slot so that the CTAs resident
@@ -53,6 +54,145 @@ __device__ __forceinline__ void rec_get(Rec<TF> &r, const TF *s) {
     r.dd[c] = s[33 + c];
   }
   r.gg = s[39];
+}
+
+template <typename T>
+__device__ __forceinline__ T pick3(const T v[3], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
+// The condensation of node p (combine() of dmn_kernels.cuh, the same
+// formulas) by an aligned group of eight lanes: lane r < 6 owns Mandel row r
+// of the tangents and component r of the vectors; lanes 6 and 7 repeat row 5
+// and store nothing.  B^T couples traction component e with rows e, ra(e),
+// rb(e) (t_e = s_e n_e + (s_ra n_ia + s_rb n_ib) / sqrt2), so lane e < 3
+// gathers those two rows by shuffles to form row e of K = B^T M B and the
+// components e of the right-hand sides; everything 3-wide is then broadcast.
+// rcL, rcR: the children's records; sL, sR: their stress sums (HP).  With
+// st, writes the node's record (root: the output layout of orec, C, tau at
+// 21, dd at 27, g at 33) into dst, its stress sum into sdst, G_p and h_p
+// into gh, and adds the lane's part of |r_p|^2 to r2.
+template <typename TF, typename HP>
+__device__ __forceinline__ void combine_rows(const SolveParams &P, int p, int r, bool st, unsigned mask,
+                                             const TF *rcL, const TF *rcR, const HP *sL, const HP *sR,
+                                             TF *dst, HP *sdst, TF *gh, TF &r2, bool full, bool root) {
+  const int rw = r < 6 ? r : 5;
+  const int ra = rw == 2 ? 4 : 5, rb = rw == 0 ? 4 : 3;  // rows coupled with component e = rw < 3
+  const int ia = rw == 0 ? 1 : 0, ib = rw == 2 ? 1 : 2;
+  const bool own = st && r < 6;
+  auto sh = [&](TF v, int src) { return __shfl_sync(mask, v, src, 8); };
+  TF n[3], c1, c2, iwcc, wcc;
+  load_node_tf(P, p, n, c1, c2, iwcc, wcc);
+  const TF rs = TF(kRsq2);
+  const TF ne = pick3(n, rw), na = pick3(n, ia), nb = pick3(n, ib);
+  const TF cc = c1 * c2;
+  // traction component e = rw of a Mandel vector whose component rw is v
+  auto bt_e = [&](TF v) { return v * ne + rs * (sh(v, ra) * na + sh(v, rb) * nb); };
+
+  // row rw of M = c2 C_L + c1 C_R and of dC = C_L - C_R
+  const int rbase = rw * (11 - rw) / 2;  // packed index of (rw, rw) minus rw
+  TF M[6], dC[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int q = c >= rw ? rbase + c : c * (11 - c) / 2 + rw;
+    const TF cl = rcL[q], cr = rcR[q];
+    M[c] = c2 * cl + c1 * cr;
+    dC[c] = cl - cr;
+  }
+  // row rw of M B and of U = dC B; row e of K on lane e < 3, then all of K
+  TF MB[3], U[3];
+  btvec(n, M, MB);
+  btvec(n, dC, U);
+  TF Kr[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) Kr[f] = bt_e(MB[f]);
+  const TF k00 = sh(Kr[0], 0), k11 = sh(Kr[1], 1), k22 = sh(Kr[2], 2);
+  const TF k01 = TF(0.5) * (sh(Kr[1], 0) + sh(Kr[0], 1));
+  const TF k02 = TF(0.5) * (sh(Kr[2], 0) + sh(Kr[0], 2));
+  const TF k12 = TF(0.5) * (sh(Kr[2], 1) + sh(Kr[1], 2));
+  const TF a00 = k11 * k22 - k12 * k12, a01 = k02 * k12 - k01 * k22, a02 = k01 * k12 - k02 * k11;
+  const TF a11 = k00 * k22 - k02 * k02, a12 = k01 * k02 - k00 * k12, a22 = k00 * k11 - k01 * k01;
+  const TF idet = TF(1) / (k00 * a00 + k01 * a01 + k02 * a02);
+  const TF Ki[3][3] = {{a00 * idet, a01 * idet, a02 * idet},
+                       {a01 * idet, a11 * idet, a12 * idet},
+                       {a02 * idet, a12 * idet, a22 * idet}};
+  // column rw of G = K^{-1} U^T
+  TF V[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) V[e] = Ki[e][0] * U[0] + Ki[e][1] * U[1] + Ki[e][2] * U[2];
+  if (own) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gh[6 * e + r] = V[e];
+  }
+  // residual r_p = w c1 c2 B^T (c2 S_L - c1 S_R) in HP; component e on lane e
+  HP S;
+  TF rbv_e;
+  {
+    NodeHP<HP> nd;
+    load_node(P, p, nd);
+    const HP SL = sL[rw], SR = sR[rw];
+    S = SL + SR;
+    const HP dh = nd.c2 * SL - nd.c1 * SR;
+    const HP dha = hp_shfl(mask, dh, ra, 8), dhb = hp_shfl(mask, dh, rb, 8);
+    const HP rh = dh * pick3(nd.n, rw) + dha * pick3(nd.ns, ia) + dhb * pick3(nd.ns, ib);
+    const TF rv = tf_of(rh, (TF *)nullptr);
+    if (st && r < 3) r2 += rv * rv;
+    rbv_e = rv * iwcc;
+  }
+  // condensed stress: B^T ds_hat = rb + B^T (ds_L - ds_R)
+  const TF dsL = rcL[21 + rw], dsR = rcR[21 + rw];
+  const TF b3e = rbv_e + bt_e(dsL - dsR);
+  const TF b3[3] = {sh(b3e, 0), sh(b3e, 1), sh(b3e, 2)};
+  TF hs[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) hs[e] = Ki[e][0] * b3[0] + Ki[e][1] * b3[1] + Ki[e][2] * b3[2];
+  if (st && r == 0) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gh[18 + e] = hs[e];
+  }
+  const TF ds = c1 * dsL + c2 * dsR - cc * (U[0] * hs[0] + U[1] * hs[1] + U[2] * hs[2]);
+  TF tau = TF(0), dd = TF(0), gg = TF(0);
+  if (full) {
+    const TF tL = rcL[27 + rw], tR = rcR[27 + rw], dL = rcL[33 + rw], dR = rcR[33 + rw];
+    const TF te = bt_e(tL - tR), de = bt_e(dL - dR);
+    const TF t3[3] = {sh(te, 0), sh(te, 1), sh(te, 2)};
+    const TF bd[3] = {sh(de, 0), sh(de, 1), sh(de, 2)};
+    TF ht[3], hd[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      ht[e] = Ki[e][0] * t3[0] + Ki[e][1] * t3[1] + Ki[e][2] * t3[2];
+      hd[e] = Ki[e][0] * bd[0] + Ki[e][1] * bd[1] + Ki[e][2] * bd[2];
+    }
+    // g_hat = c1 g_L + c2 g_R - c1 c2 (B^T d_diff) . h_tau
+    gg = c1 * rcL[39] + c2 * rcR[39] - cc * (bd[0] * ht[0] + bd[1] * ht[1] + bd[2] * ht[2]);
+    tau = c1 * tL + c2 * tR - cc * (U[0] * ht[0] + U[1] * ht[1] + U[2] * ht[2]);
+    dd = c1 * dL + c2 * dR - cc * (U[0] * hd[0] + U[1] * hd[1] + U[2] * hd[2]);
+  }
+  // row rw of C_hat = c1 C_L + c2 C_R - c1 c2 U G, c1 C_L + c2 C_R = M + (c1 - c2) dC
+  const TF cm = c1 - c2;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const TF g0 = sh(V[0], c), g1 = sh(V[1], c), g2 = sh(V[2], c);
+    const TF v = M[c] + cm * dC[c] - cc * (U[0] * g0 + U[1] * g1 + U[2] * g2);
+    if (own && c >= rw) dst[rbase + c] = v;
+  }
+  if (own) {
+    sdst[r] = S;
+    if (root) {
+      if (full) {
+        dst[21 + r] = tau;
+        dst[27 + r] = dd;
+        if (r == 0) dst[33] = gg;
+      }
+    } else {
+      dst[21 + r] = ds;
+      if (full) {
+        dst[27 + r] = tau;
+        dst[33 + r] = dd;
+        if (r == 0) dst[39] = gg;
+      }
+    }
+  }
 }
 
 // Shared scratch region, in 8-byte words, used in turn by the condensation
@@ -147,9 +287,19 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     if (cnt > 32) return t < cnt ? t : -1;
     return (warp == L && lane < cnt) ? lane : -1;
   };
-  // thread that ends the bottom-up sweep with the root record (level K-1 is
-  // condensed by shuffles, on threads 0, 2, ..)
-  const int root_t = K >= 3 ? 32 * L : 0;
+  // the root's record and stress sum, for the decision and the outputs (the
+  // layout of the output staging row orec: C, tau at 21, dd at 27, g at 33)
+  auto put_root = [&](const Rec<TF> &R, const HP *Sv) {
+#pragma unroll
+    for (int q = 0; q < 21; ++q) orec[q] = R.C[q];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      orec[21 + c] = R.tau[c];
+      orec[27 + c] = R.dd[c];
+      sroot[c] = Sv[c];
+    }
+    orec[33] = R.gg;
+  };
 
   for (int i = t; i < P.n_mats; i += G)
     mat_static<TF, HP>(mp_s[i], *reinterpret_cast<const MatDev *>(P.mat + kMatWords * i), P.dt);
@@ -420,6 +570,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
                            tf_of(rbh[2], (TF *)nullptr)};
         r2 = wcc * wcc * (rbv[0] * rbv[0] + rbv[1] * rbv[1] + rbv[2] * rbv[2]);
         combine<TF>(rec, rr, n, c1, c2, rbv, gh_s + 21 * t, full);
+        if (K == 1) put_root(rec, S);
       }
       // ---- level K-1: neighbouring lanes (2j, 2j+1) ----
       if (K >= 2) {
@@ -452,30 +603,60 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
             rec_put(recX + RS * j, rec);
 #pragma unroll
             for (int c = 0; c < 6; ++c) Sx[6 * j + c] = S[c];
+          } else {
+            put_root(rec, S);
           }
         }
       }
-      // ---- levels K-2 .. 1: node j of the level on one thread.  Once the
-      //      producers of the level below all sit in warp L, warp L goes on
-      //      alone with warp barriers and the other warps move to the
-      //      reduction barrier ----
-      for (int k = K - 2; k >= 1; --k) {
-        const int prod = k + 1 == K - 1 ? G : (1 << k);  // threads that wrote level k+1
-        if (prod > 32) {
-          __syncthreads();
-        } else {
-          if (warp != L) break;
-          __syncwarp(mask);
+      // ---- levels K-2 .. 1, by Mandel rows: node j of level k on the
+      //      eight lanes 8j .. 8j + 7 of the level's tasks (combine_rows).  A
+      //      level of more than 32 tasks runs on all threads between block
+      //      barriers; once the producers of the level below all sit in warp
+      //      L, warp L goes on alone with warp barriers and the other warps
+      //      move to the reduction barrier.  A CTA of fewer than 8 threads
+      //      (K = 3) condenses its root on one thread. ----
+      if (G >= 8) {
+        for (int k = K - 2; k >= 1; --k) {
+          const int ntask = 8 << (k - 1);
+          const bool wide = ntask > 32 && G > 32;
+          const bool prod_wide = k + 1 == K - 1 ? G > 32 : (2 * ntask > 32 && G > 32);
+          if (prod_wide) __syncthreads();
+          if (!wide) {  // this level and the ones above: warp L alone
+            if (warp != L) break;
+            if (!prod_wide) __syncwarp(mask);
+          }
+          const int step = wide ? G : (G < 32 ? G : 32);
+          const int q0 = wide ? t : lane;
+          const int cnt = 1 << (k - 1);
+          for (int qb = 0; qb < ntask; qb += step) {
+            if (qb + (q0 & ~31) >= ntask) break;  // the whole warp is past the level
+            const int q = qb + q0;
+            const bool st = q < ntask;            // else a copy of the last node, not stored
+            const int j = st ? q >> 3 : cnt - 1;
+            const int p = (1 << K) - (1 << k) + j;
+            // children: slots 2j, 2j + 1 of level k + 1's buffer (debug build: checked)
+            const int cap = ((K - 1 - (k + 1)) & 1) ? sc_.GY : sc_.GX;
+            const int jc = DMN_IDX(2 * j, cap - 1) >> 1;
+            (void)cap;
+            const TF *rc = recbuf(k + 1) + RS * (2 * jc);
+            const HP *sc = sbuf(k + 1) + 12 * jc;
+            TF *dst = orec;
+            HP *sd = sroot;
+            if (k > 1) {
+              const int js = DMN_IDX(j, ((K - 1 - k) & 1) ? sc_.GY : sc_.GX);
+              dst = recbuf(k) + RS * js;
+              sd = sbuf(k) + 6 * js;
+            }
+            combine_rows<TF, HP>(P, p, q & 7, st, mask, rc, rc + RS, sc, sc + 6, dst, sd, gh_s + 21 * p, r2,
+                                 full, k == 1);
+          }
         }
-        const int j = node_at(k);
-        if (j >= 0) {
-          const int p = (1 << K) - (1 << k) + j;
-          // children: slots 2j, 2j + 1 of level k + 1's buffer (debug build: checked)
-          const int cap = ((K - 1 - (k + 1)) & 1) ? sc_.GY : sc_.GX;
-          const int jc = DMN_IDX(2 * j, cap - 1) >> 1;
-          (void)cap;
-          const TF *rc = recbuf(k + 1) + RS * (2 * jc);
-          const HP *sc = sbuf(k + 1) + 12 * jc;
+      } else if (K == 3) {
+        __syncwarp(mask);
+        if (t == 0) {
+          const int p = (1 << K) - 2;
+          const TF *rc = recX;
+          const HP *sc = Sx;
           Rec<TF> other;
           rec_get(rec, rc);
           rec_get(other, rc + RS);
@@ -497,17 +678,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
           r2 += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
           const TF rbv[3] = {rv[0] * iwcc, rv[1] * iwcc, rv[2] * iwcc};
           combine<TF>(rec, other, n, c1, c2, rbv, gh_s + 21 * p, full);
-          if (k > 1) {
-            const int js = DMN_IDX(j, ((K - 1 - k) & 1) ? sc_.GY : sc_.GX);
-            rec_put(recbuf(k) + RS * js, rec);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sbuf(k)[6 * js + c] = S[c];
-          }
+          put_root(rec, S);
         }
-      }
-      if (t == root_t) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) sroot[c] = S[c];
       }
       // ---- residual norm, decision (Algorithm 1) ----
       r2 = warp_sum(r2, mask, W);
@@ -649,15 +821,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       }
     }
     __syncthreads();
-    if (t == root_t) {
-#pragma unroll
-      for (int q = 0; q < 21; ++q) orec[q] = rec.C[q];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        orec[21 + c] = rec.tau[c];
-        orec[27 + c] = rec.dd[c];
-      }
-      orec[33] = rec.gg;
+    if (t == 0) {
       HP Db = redD[0], Xb = redX[0];
       for (int w = 1; w < nwarp; ++w) {
         Db = Db + redD[w];
