@@ -65,8 +65,12 @@ enum {
   DMN_PT_NOT_CONVERGED = 1, /* maxit Newton iterations without res < tol   */
   DMN_PT_NONFINITE = 2,     /* a residual or an output was NaN or Inf      */
   DMN_PT_FALLBACK_USED = 4, /* bit: warm start failed, re-run from a^n     */
-  DMN_PT_OUTER_NOT_CONVERGED = 8 /* bit (dmn_eval_mixed): the prescribed
-                                    stresses / heat balance were not met    */
+  DMN_PT_OUTER_NOT_CONVERGED = 8, /* bit (dmn_eval_mixed): the prescribed
+                                     stresses / heat balance were not met    */
+  DMN_PT_STAGING_TIMEOUT = 32 /* the point's state block did not arrive in
+                                 shared memory within the wait limit; the
+                                 point is not evaluated and its CTA stops
+                                 (the other points are taken by the others) */
 };
 
 /* phase laws (Sec. 4) */

@@ -7,6 +7,7 @@
 namespace dmn {
 
 enum { ACT_STEP = 0, ACT_BACK = 1, ACT_DONE = 2 };
+constexpr int kPtStaging = 32;  // per-point status bit (DMN_PT_STAGING_TIMEOUT)
 
 template <typename TF>
 struct Ctrl {

@@ -15,7 +15,9 @@
 //    nodes occupies one warp (the CTA's leader warp, with warp barriers
 //    only) while the other warps go ahead;
 //  * the back-substitution of the Newton increment, a chain through the
-//    levels, in the condensation precision TF on the same compact mapping.
+//    levels, in the condensation precision TF on the same compact mapping;
+//  * the point's state block (jumps, internal variables) brought into shared
+//    memory by the bulk-copy engine and converted in place by short loops.
 // The leader warp is picked from the CTA's warp slot so that the CTAs resident
 // on one SM run their single-warp phases on different SM sub-partitions.
 // The condensation, the residual and the leaf laws are those of
@@ -195,6 +197,36 @@ __device__ __forceinline__ void combine_rows(const SolveParams &P, int p, int r,
   }
 }
 
+// The state block of a point is moved into shared memory by the bulk-copy
+// engine (cp.async.bulk, completion counted on an mbarrier): the jumps a into
+// a_s and, for the kinds that keep their internal variables as stored, z into
+// zn_s; each thread then converts its words in place.  A block has an even
+// number of words and starts on a 16-byte boundary, so a (word 8) starts
+// aligned and goes with the word after it (3N is odd), and z (word 8 + 3N,
+// odd) goes from the word before it into the slot before zn_s, rounded up to
+// an even count.  The extra words stay inside the block and land in slots
+// written before they are read (eK[0], eK[6G - 1], eb[0]).
+constexpr int kWaitLimit = 1 << 22;  // mbarrier polls before a point gives up
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return unsigned(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mb)
+               : "memory");
+}
+// poll the mbarrier's phase with the given parity, at most `limit` times
+__device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity, int limit) {
+  unsigned ok = 0;
+  for (int it = 0; it < limit && !ok; ++it)
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+  return ok != 0;
+}
+
 // Shared scratch region, in 8-byte words, used in turn by the condensation
 // (stress sums and records of the levels K-1, K-2, ..., two parities), by the
 // Newton back-substitution (TF strain increments of two level parities, level
@@ -277,6 +309,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     unsigned wid;
     asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
     ctrl->lead = nwarp > 1 ? int(((wid >> 2) - wid) & unsigned(nwarp - 1)) : 0;
+  }
+  // mbarrier of the state block's bulk copies (one phase per point)
+  __shared__ __align__(8) unsigned long long stage_bar;
+  const unsigned mb = smem_u32(&stage_bar);
+  unsigned stage_par = 0;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   const int L = ctrl->lead;
@@ -381,19 +421,6 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     return tr;
   };
 
-  // n doubles from global memory into HP in shared memory, U loads in flight
-  auto load_hp = [&](HP *dst, const double *src, int n) {
-    constexpr int U = 8;
-    for (int i0 = t; i0 < n; i0 += U * G) {
-      double v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = i0 + u * G < n ? ld_stream(src + i0 + u * G) : 0.0;
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (i0 + u * G < n) dst[i0 + u * G] = hp_load(v[u], tag);
-    }
-  };
-
   for (;;) {
     if (t == 0) {
       unsigned long long q = atomicAdd(P.queue, 1ull);
@@ -415,33 +442,68 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
     HP *zw = reinterpret_cast<HP *>(sout + 8 + 3 * N);  // z of the current pass (8-byte slots)
     const double theta = P.theta[pt];
     {
-      // one wave of loads: jumps (3N < 8G), the first 8G internal variables,
-      // the predicted increment, eps_bar^n and deps
+      // the state block by bulk copies (a, and z unless LAW 3 keeps histories
+      // there), or by plain loads where the caller's state is not 16-byte
+      // aligned; with them the predicted increment, eps_bar^n and deps
       constexpr int U = 8;
-      double va[U], vz[U], ve = 0.0, vd = 0.0;
+      const bool bulk = (reinterpret_cast<uintptr_t>(P.sin) & 15) == 0;
+      if (bulk && t == 0) {
+        const unsigned n1 = unsigned(3 * N + 1) * 8u, n2 = LAW < 3 ? unsigned((ZW + 2) & ~1) * 8u : 0u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(n1 + n2) : "memory");
+        bulk_g2s(smem_u32(a_s), sin + 8, n1, mb);
+        if (LAW < 3) bulk_g2s(smem_u32(zn_s - 1), sin + 7 + 3 * N, n2, mb);
+      }
+      double ve = 0.0, vd = 0.0;
       float vp[U];
       const float *d0 = P.da0 ? P.da0 + pt * (3 * N) : nullptr;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int i = t + u * G;
-        va[u] = i < 3 * N ? ld_stream(sin + 8 + i) : 0.0;
-        vz[u] = LAW < 3 && i < ZW ? ld_stream(sin + 8 + 3 * N + i) : 0.0;
         vp[u] = d0 && i < 3 * N ? ld_stream(d0 + i) : 0.0f;
       }
       if (G >= 8 && t < 6) {
         ve = ld_stream(sin + t);
         vd = ld_stream(P.deps + pt * 6 + t);
       }
+      if (d0) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = t + u * G;
-        if (i < 3 * N) {
-          a_s[i] = hp_load(va[u], tag);
-          if (d0) da_s[i] = TF(vp[u]);
+        for (int u = 0; u < U; ++u) {
+          const int i = t + u * G;
+          if (i < 3 * N) da_s[i] = TF(vp[u]);
         }
-        if (LAW < 3 && i < ZW) zn_s[i] = hp_load(vz[u], tag);
       }
-      if (LAW < 3 && ZW > U * G) load_hp(zn_s + U * G, sin + 8 + 3 * N + U * G, ZW - U * G);
+      if (bulk) {
+        const bool ok = mbar_wait(mb, stage_par, kWaitLimit);
+        if (!__syncthreads_and(ok)) {
+          // the copies did not complete: flag the point, give them time to
+          // land, and stop this CTA (the queue hands its points to the others)
+          mbar_wait(mb, stage_par, kWaitLimit);
+          if (t == 0) {
+            P.status[pt] = kPtStaging;
+            P.iters[pt] = 0;
+          }
+          return;
+        }
+        stage_par ^= 1u;
+        if (sizeof(TF) == 4) {  // mixed: the raw FP64 words into float-float, in place
+          const double *ra = reinterpret_cast<const double *>(a_s);
+          const double *rz = reinterpret_cast<const double *>(zn_s);
+#pragma unroll 1
+          for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(ra[i], tag);
+          if (LAW < 3) {
+#pragma unroll 1
+            for (int i = t; i < ZW; i += G) zn_s[i] = hp_load(rz[i], tag);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int i = t; i < 3 * N; i += G) a_s[i] = hp_load(ld_stream(sin + 8 + i), tag);
+        if (LAW < 3) {
+#pragma unroll 1
+          for (int i = t; i < ZW; i += G) zn_s[i] = hp_load(ld_stream(sin + 8 + 3 * N + i), tag);
+        }
+      }
       if (G >= 8) {
         if (t < 6) {
           ebd[t] = ve + vd;  // eps_bar^{n+1} = eps_bar^n + deps exactly in FP64
