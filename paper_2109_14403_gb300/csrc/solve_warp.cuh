@@ -7,8 +7,9 @@
 // subtree in the lane's registers (a postorder loop over the lane's bottom
 // laminates), then the five levels 5..1 by shuffles (level k node j on lane
 // j 2^(6-k)).  The loops keep one copy of the leaf, laminate and combine
-// code, small enough for the instruction cache.  Nothing waits for another warp: a CTA holds W independent
-// points, one per warp, and its warps meet only once, when the CTA starts.
+// code, small enough for the instruction cache.  A CTA holds W points, one
+// per warp, whose passes run in lockstep: level 5 by lane pairs on every
+// warp, levels 4..1 of all W points batched on one warp (dmn_solve_warp).
 //
 // Strains.  Lane l keeps the strain of its level-6 node (float-float) in
 // shared memory; the strains below it are formed in every pass from the
