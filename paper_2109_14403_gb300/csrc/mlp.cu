@@ -89,17 +89,35 @@ unsigned blocks_for(int64_t n, int t = 256) {
 }
 
 // ------------------------------------------------------------------ kernels
+// A double rounded to the nearest float (ties to even) by integer
+// operations: the FP64 pipe of this GPU runs at 1/64 of the FP32 rate, and
+// the network input converts 768 words per row.  Magnitudes outside the
+// normal float range (and NaN) take the FP64 conversion; zero and double
+// subnormals give a signed zero.
+__device__ __forceinline__ float f32_rn(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned E = unsigned(b >> 52) & 0x7ffu;
+  const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+  if (E == 0u) return __uint_as_float(sign);
+  if (E < 897u || E > 1150u) return __double2float_rn(d);
+  const unsigned long long mant = b & ((1ull << 52) - 1);
+  unsigned r = sign | ((E - 896u) << 23) | unsigned(mant >> 29);
+  const unsigned rem = unsigned(mant & ((1ull << 29) - 1)), half = 1u << 28;
+  if (rem > half || (rem == half && (r & 1u))) r += 1u;  // a carry moves into the exponent
+  return __uint_as_float(r);
+}
+
 // feature c of a row: deps (6), theta^{n+1}, theta^{n+1} - theta^n,
-// a^n - a^{n-1} (n3); a = the state block at t^n, ap = at t^{n-1} or NULL
-// (its columns 0)
+// a^n - a^{n-1} (n3) as the difference of the two words rounded to float;
+// a = the state block at t^n, ap = at t^{n-1} or NULL (its columns 0)
 constexpr int kExtraFeatures = 0;
-__device__ __forceinline__ double feature(int c, int n3, const double *dep, double th, const double *a,
-                                          const double *ap) {
+__device__ __forceinline__ float feature(int c, int n3, const double *dep, double th, const double *a,
+                                         const double *ap) {
   (void)n3;
-  if (c < 6) return dep[c];
-  if (c == 6) return th;
-  if (c == 7) return th - a[6];
-  return ap ? a[c] - ap[c] : 0.0;  // a^n - a^{n-1}: state words 8..
+  if (c < 6) return f32_rn(dep[c]);
+  if (c == 6) return f32_rn(th);
+  if (c == 7) return float(th - a[6]);
+  return ap ? f32_rn(a[c]) - f32_rn(ap[c]) : 0.0f;  // a^n - a^{n-1}: state words 8..
 }
 
 __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const double *theta,
@@ -109,7 +127,7 @@ __global__ void k_features(int64_t n, int n3, int sw, const double *deps, const 
        i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i / nin;
     const int c = int(i - r * nin);
-    feat[i] = float(feature(c, n3, deps + r * 6, theta[r], sin + r * sw, sprev ? sprev + r * sw : nullptr));
+    feat[i] = feature(c, n3, deps + r * 6, theta[r], sin + r * sw, sprev ? sprev + r * sw : nullptr);
   }
 }
 
@@ -133,8 +151,8 @@ __global__ void k_features_norm(int64_t n, int n3, int sw, int ld, const double 
         const int c = c0 + u;
         v[u] = 0.0f;
         if (c < nin) {
-          const double f = feature(c, n3, deps + r * 6, theta[r], a, ap);
-          v[u] = (float(f) - mean[c]) * inv[c];
+          const float f = feature(c, n3, deps + r * 6, theta[r], a, ap);
+          v[u] = (f - mean[c]) * inv[c];
         }
       }
       xr[c0 >> 1] = __floats2bfloat162_rn(v[0], v[1]);

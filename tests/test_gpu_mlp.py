@@ -366,8 +366,9 @@ def test_warm_start_k9_perzyna():
 
 def test_features_match_the_state():
     """The network's raw features against their definition, computed here
-    from the same device states: the load step and a^n - a^{n-1} (exact FP64
-    differences rounded once to FP32); without a previous state the
+    from the same device states: the load step rounded to FP32, and
+    a^n - a^{n-1} as the FP32 difference of the two words rounded to FP32
+    (round to nearest even, as numpy's astype); without a previous state the
     difference columns are 0."""
     from paper_2109_14403_gb300 import DMN
     from paper_2109_14403_gb300.mlp import MLP
@@ -385,8 +386,9 @@ def test_features_match_the_state():
     f0 = net.features(D, T, s2, None).cpu().numpy()
     a, ap = s2.cpu().numpy(), s1.cpu().numpy()
     n3 = 3 * ((1 << K) - 1)
-    ref = np.concatenate([deps[2], theta[2][:, None], (theta[2] - a[:, 6])[:, None],
-                          a[:, 8:8 + n3] - ap[:, 8:8 + n3]], axis=1).astype(np.float32)
+    ref = np.concatenate([np.asarray(deps[2]).astype(np.float32), theta[2][:, None].astype(np.float32),
+                          (theta[2] - a[:, 6])[:, None].astype(np.float32),
+                          a[:, 8:8 + n3].astype(np.float32) - ap[:, 8:8 + n3].astype(np.float32)], axis=1)
     assert f.shape == (n, net.n_in) == ref.shape
     np.testing.assert_array_equal(f, ref)
     ref[:, 8:] = 0.0
