@@ -67,14 +67,19 @@ __device__ __forceinline__ dfl dfl_from(double d) {
 }
 __device__ __forceinline__ double dfl_to(dfl x) { return double(x.hi) + double(x.lo); }
 
+// the FP64 conversion as a call, so that it is a branch that only the lanes
+// needing it take (not an if-converted sequence every lane issues)
+static __device__ __noinline__ dfl dfl_from_call(double d) { return dfl_from(d); }
+
 // The same split by integer operations only (no FP64 pipe): hi keeps the
 // leading 24 significand bits of d (truncated), lo the next 29 bits rounded
-// to a float; a final fast_two renormalises.  Zero, and magnitudes outside
-// [2^-74, 2^127), take the FP64 conversion.
+// to a float; a final fast_two renormalises.  Zero (and double subnormals)
+// give zero; magnitudes outside [2^-74, 2^127) take the FP64 conversion.
 __device__ __forceinline__ dfl dfl_split(double d) {
   const long long b = __double_as_longlong(d);
   const int E = int((b >> 52) & 0x7ff);
-  if (E < 949 || E >= 1150) return E == 0 ? dfl{0.0f, 0.0f} : dfl_from(d);
+  if (E == 0) return dfl{0.0f, 0.0f};
+  if (E < 949 || E >= 1150) return dfl_from_call(d);
   const unsigned sign = unsigned(b >> 32) & 0x80000000u;
   const long long mant = b & ((1ll << 52) - 1);
   const float hi = __uint_as_float(sign | (unsigned(E - 1023 + 127) << 23) | unsigned(mant >> 29));
