@@ -250,9 +250,8 @@ dmn_status dmn_eval(dmn_handle h, dmn_stream stream, int64_t n_points, const dou
  *   per-leaf history offsets a dmn_handle keeps), are rejected with
  *   DMN_ERR_ARG.
  *   The first call on a device looks up the device address of that array
- *   (with the device current); make that first call before any stream
- *   capture.  The host-to-device copies of the tables are ordinary
- *   stream-ordered copies from host memory.
+ *   (with the device current).  The host-to-device copies of the tables are
+ *   ordinary stream-ordered copies from host memory.
  *   All calls share the one array (tables and the work-queue counter, which
  *   each launch zeroes first): calls that overlap on the GPU -- on different
  *   streams, or from different threads -- race; order them on one stream.
