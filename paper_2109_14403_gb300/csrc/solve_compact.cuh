@@ -367,7 +367,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
   //   SW_WARM:  a += da (da_s) on the way; eK as SW_PLAIN at the new a, and
   //             the trace of the strain at (eps_bar^n = tr_root, a^n) of
   //             laminate t is returned (tr B a = a . n)
-  //   SW_STEP:  eK += sum of the B da terms (the Newton increment in da_s)
+  //   SW_STEP:  eK += sum of the B da terms (the Newton increment in da_s),
+  //             and a += da of the non-bottom nodes on the way
   // Ends with a barrier: eK is complete and the scratch region free again.
   enum { SW_PLAIN = 0, SW_WARM = 1, SW_STEP = 2 };
   auto sweep = [&](int mode, HP tr_root) -> HP {
@@ -377,8 +378,17 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
       load_node(P, p, nd);
       HP x[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        x[r] = mode == SW_STEP ? hp_add_tf(hp_zero(tag), da_s[3 * p + r]) : a_s[3 * p + r];
+      for (int r = 0; r < 3; ++r) {
+        if (mode == SW_STEP) {
+          // the step's da of this node: its terms, and a += da (left here by
+          // the back-substitution chain, one node per thread)
+          const TF d = da_s[3 * p + r];
+          x[r] = hp_add_tf(hp_zero(tag), d);
+          a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], d);
+        } else {
+          x[r] = a_s[3 * p + r];
+        }
+      }
       HP *ent = anc + 14 * q;
       if (mode == SW_WARM) {
         const HP trj = x[0] * nd.n[0] + x[1] * nd.n[1] + x[2] * nd.n[2];
@@ -837,9 +847,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dmn_solve_compact(const SolveParam
               da[r] = -sum;
             }
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              da_s[3 * p + r] = da[r];
-              a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
+            for (int r = 0; r < 3; ++r) da_s[3 * p + r] = da[r];
+            if (k == K) {  // the other levels' a += da: in the strain sums that follow
+#pragma unroll
+              for (int r = 0; r < 3; ++r) a_s[3 * p + r] = hp_add_tf(a_s[3 * p + r], da[r]);
             }
             if (k < K) {
               TF n[3], c1, c2, iwcc, wcc;
