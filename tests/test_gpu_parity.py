@@ -144,6 +144,19 @@ def test_compact_kernel_k8_full_batch_sampled(prec, variant):
     run_path(8, prec, deps, theta, n_check=96, variant=variant)
 
 
+@pytest.mark.parametrize("n", [1, 455, 456, 457, 1000])
+@pytest.mark.parametrize("prec,variant", [("fp64", 11), ("mixed", 13)])
+def test_point_counts_around_the_persistent_grid(n, prec, variant):
+    """K = 8 batches of one point and of sizes around the resident CTA count
+    (three per SM on 152 SMs: 456; the persistent CTAs take points from the
+    queue until it runs dry), checked on up to 16 sampled points including the
+    last, over two plastic increments."""
+    rng = np.random.default_rng(7000 + n)
+    deps = rng.normal(0.0, 2e-3, size=(2, n, 6))
+    theta = syn.THETA_START + np.cumsum(rng.uniform(0, 3, size=(2, n)), axis=0)
+    run_path(8, prec, deps, theta, n_check=None if n <= 16 else 16, variant=variant)
+
+
 @pytest.mark.parametrize("prec,variant", [("fp64", 0), ("mixed", 0)] + COMPACT)
 def test_backtracking_walk(prec, variant):
     """K=8 walk scaled by 20: in its second increment the oracle rejects full
